@@ -1,0 +1,257 @@
+/*
+ * b2sr.h -- C ABI of the GB300-native B2SR bit-graph library.
+ *
+ * Implements the hot path of Bit-GraphBLAS (Chen, Sung, Shen, Tallent,
+ * Barker, Li; arXiv 2201.08560): the Bit-Block Compressed Sparse Row (B2SR)
+ * storage of a binary adjacency matrix (Sec. III), bit-level SpMV and SpGEMM
+ * over it (Sec. IV, Tables 2 and 3) and the GraphBLAS algorithms built on
+ * them (Sec. V, Table 4: BFS, SSSP, PageRank, connected components, triangle
+ * counting), plus batched multi-source BFS.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns a b2sr_status; 0 is success.  On failure the
+ *    calling thread's b2sr_last_error() holds a one-line reason.  No C++
+ *    exception crosses this boundary.
+ *  - Array pointers are DEVICE pointers (cudaMalloc / PyTorch CUDA tensors on
+ *    the current device) unless the parameter name ends in _host.  The caller
+ *    owns every input and output buffer and sizes it as documented; a
+ *    b2sr_handle owns the B2SR arrays it was built with.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    stream-ordered: a function returns once its kernels are enqueued, except
+ *    where it must return a host value (named *_host) or size an allocation;
+ *    those synchronise the stream and say so.
+ *  - Temporary device memory is taken from the stream-ordered allocator
+ *    (cudaMallocAsync) and released on the same stream; failures give
+ *    B2SR_ERR_OOM.  A handle is read-only during SpMV/SpGEMM/driver calls, so
+ *    one handle may serve several streams at once.
+ *  - Vertex ids are int32; n < 2^31; nnz < 2^31.
+ *  - Bitsets are LSB-first uint32 words: vertex v is bit v%32 of word v/32.
+ *    A bitset over n vertices has ceil(n/32) words; output bits >= n are 0.
+ *
+ * B2SR layout (Sec. III-A, III-B and Table 1)
+ * -------------------------------------------
+ *  k = tile_dim in {4, 8, 16, 32}; nTileRow = ceil(n/k).
+ *  TileRowPtr int32[nTileRow+1]: tiles of tile-row I are [TileRowPtr[I],
+ *     TileRowPtr[I+1]).
+ *  TileColInd int32[T]: tile column of each non-empty tile, ascending per
+ *     tile-row.
+ *  BitTiles: k row words per tile, a word being uint8 (k=4, low nibble),
+ *     uint8 (k=8), uint16 (k=16) or uint32 (k=32).  Row word r of tile (I,J)
+ *     holds matrix row k*I+r; its bit c (LSB = 0) is entry (k*I+r, k*J+c).
+ *     Bits outside the n x n matrix are 0.
+ *  Storage bytes = 4(nTileRow+1) + 4T + T*k*word_bytes.
+ */
+#ifndef B2SR_H
+#define B2SR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    B2SR_OK = 0,
+    B2SR_ERR_INVALID_ARG = 1,      /* null pointer, bad size, malformed CSR, bad source */
+    B2SR_ERR_UNSUPPORTED_TILE = 2, /* tile_dim not in {4, 8, 16, 32} */
+    B2SR_ERR_OOM = 3,              /* device allocation failed */
+    B2SR_ERR_CUDA = 4,             /* a CUDA runtime call or kernel launch failed */
+    B2SR_ERR_NOT_CONVERGED = 5,    /* an iterative driver hit max_iters */
+    B2SR_ERR_ADMISSION_REFUSED = 6,/* reserved: serving admission */
+    B2SR_ERR_ABORTED = 7           /* reserved: cancelled work */
+} b2sr_status;
+
+typedef struct b2sr_matrix* b2sr_handle;
+
+typedef enum {
+    B2SR_BOOL_OR_AND = 0, /* Boolean semiring ({0,1}, OR, AND), Table 4 */
+    B2SR_PLUS_TIMES = 1,  /* arithmetic semiring (R, +, x), Table 4 */
+    B2SR_MIN_PLUS = 2     /* tropical min-plus (R u {+inf}, min, +), Table 4 */
+} b2sr_semiring;
+
+typedef enum {
+    B2SR_VEC_BITS = 0, /* bitset, ceil(n/32) uint32 words */
+    B2SR_VEC_I32 = 1,  /* int32[n] */
+    B2SR_VEC_F32 = 2   /* float[n] */
+} b2sr_vec;
+
+typedef struct {
+    int32_t n;           /* vertices (rows = columns) */
+    int32_t tile_dim;    /* k */
+    int32_t n_tile_rows; /* ceil(n/k) */
+    int32_t reserved;
+    int64_t n_tiles;     /* T, non-empty tiles */
+    int64_t nnz;         /* set bits = distinct stored entries */
+    int64_t bytes;       /* 4(nTileRow+1) + 4T + T*k*word_bytes (Sec. III-C sizes) */
+} b2sr_info_t;
+
+/* Thread-local text of the last failure on this thread ("" if none). */
+const char* b2sr_last_error(void);
+
+/* Library version string. */
+const char* b2sr_version(void);
+
+/* ---------------------------------------------------------------------- */
+/* Storage (Sec. III)                                                      */
+/* ---------------------------------------------------------------------- */
+
+/* CSR -> B2SR conversion (Sec. III-A "Bit-tile Indexing System", Sec. III-B
+ * "Bit Packing"): nTileRow = ceil(n/k); the distinct tile columns of each
+ * tile-row give TileRowPtr/TileColInd; every entry (i, j) sets bit j%k of row
+ * word i%k of tile (i/k, j/k).
+ *   n        vertices, 0 <= n < 2^31
+ *   rowptr   device int32[n+1], rowptr[0] = 0, non-decreasing, rowptr[n] = nnz
+ *   colind   device int32[nnz], each in [0, n); rows need not be sorted;
+ *            repeated entries are OR-ed (the matrix is binary)
+ *   tile_dim 4, 8, 16 or 32 (else B2SR_ERR_UNSUPPORTED_TILE)
+ *   out      receives a new handle (owned by the caller; b2sr_destroy)
+ * The input is validated on the device (B2SR_ERR_INVALID_ARG if malformed).
+ * Synchronises `stream` once to learn the tile count. */
+b2sr_status b2sr_from_csr(int32_t n, const int32_t* rowptr, const int32_t* colind, int64_t nnz,
+                          int tile_dim, void* stream, b2sr_handle* out);
+
+/* B2SR -> CSR (sorted, duplicate-free rows): the inverse of b2sr_from_csr.
+ *   rowptr   device int32[n+1] (written)
+ *   colind   device int32[nnz] (written) or NULL to query only
+ *   nnz_host receives nnz (host int64).  Synchronises `stream`. */
+b2sr_status b2sr_to_csr(b2sr_handle h, int32_t* rowptr, int32_t* colind, int64_t* nnz_host,
+                        void* stream);
+
+/* Sizes of a handle (host struct). */
+b2sr_status b2sr_info(b2sr_handle h, b2sr_info_t* info);
+
+/* Device pointers to the handle's three arrays (owned by the handle; valid
+ * until b2sr_destroy).  BitTiles is returned as bytes. */
+b2sr_status b2sr_arrays(b2sr_handle h, const int32_t** tile_rowptr, const int32_t** tile_colind,
+                        const void** bit_tiles);
+
+/* Copies the three arrays, unpadded, into caller buffers (stream-ordered):
+ *   tile_rowptr device int32[nTileRow+1], tile_colind device int32[T],
+ *   bit_tiles device bytes[T*k*word_bytes]; any may be NULL to skip it. */
+b2sr_status b2sr_export(b2sr_handle h, int32_t* tile_rowptr, int32_t* tile_colind, void* bit_tiles,
+                        void* stream);
+
+/* Release a handle (waits for the device to finish with it). NULL is a no-op. */
+b2sr_status b2sr_destroy(b2sr_handle h);
+
+/* Strictly lower triangle L of the matrix (entries (i, j) with j < i) as a new
+ * B2SR handle with the same tile_dim: the L used by triangle counting
+ * (Sec. V, TC).  Synchronises `stream` once. */
+b2sr_status b2sr_lower(b2sr_handle h, void* stream, b2sr_handle* out);
+
+/* Reorders per-entry fp32 weights given in CSR order (the CSR that built h,
+ * any row order, no repeated entries) into set-bit order: tile by tile, row
+ * word by row word, bit by bit.  That is the `weights` layout b2sr_spmv and
+ * b2sr_sssp take.  Weighted graphs are outside the paper's binary B2SR (it
+ * names short-bit-width weights as future work, Sec. VII); the side array is
+ * this library's addition.
+ *   w_csr  device float[nnz] (CSR order);  w_bits  device float[nnz] (written) */
+b2sr_status b2sr_weights_from_csr(b2sr_handle h, const int32_t* rowptr, const int32_t* colind,
+                                  const float* w_csr, float* w_bits, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* SpMV: the BMV schemes of Table 2 over the semirings of Table 4          */
+/* ---------------------------------------------------------------------- */
+
+/* y = A (+).(x) x, overwriting y, with an optional output mask applied just
+ * before the store (Sec. V, BFS: masked schemes).  Supported combinations:
+ *   BOOL_OR_AND, BITS -> BITS  bmv_bin_bin_bin:  y_i = OR_j A_ij AND x_j
+ *   PLUS_TIMES,  BITS -> I32   bmv_bin_bin_full: y_i = sum_J popc(A_IJ[r] & x_J)
+ *                              (the popc formula of Sec. IV), i.e. the number
+ *                              of neighbours j of i with x_j = 1
+ *   PLUS_TIMES,  F32  -> F32   bmv_bin_full_full: y_i = sum_{j: A_ij=1} x_j
+ *   MIN_PLUS,    F32  -> F32   y_i = min(x_i, min_{j: A_ij=1} x_j + w_ij)
+ *                              (Sec. V, SSSP: zeros are +inf off the diagonal
+ *                              and 0 on it, so x_i always takes part);
+ *                              weights NULL means w = 1
+ *   MIN_PLUS,    I32  -> I32   y_i = min(x_i, min_{j: A_ij=1} x_j): every
+ *                              weight 0, the CC min step (Sec. V, CC);
+ *                              weights must be NULL
+ *   x       device; bitset (ceil(n/32) words), int32[n] or float[n]
+ *   y       device; same shapes; must not alias x or mask
+ *   mask    device bitset or NULL; if given, y_i is kept where the mask bit
+ *           is 1 (mask_complement = 0) or 0 (mask_complement = 1); excluded
+ *           outputs get the semiring's additive identity (0 / false / +inf /
+ *           INT32_MAX)
+ *   weights device float[nnz] in set-bit order (b2sr_weights_from_csr) or NULL
+ * Floating-point sums use a fixed order, so results are bitwise reproducible
+ * run to run.  B2SR_ERR_INVALID_ARG for other combinations. */
+b2sr_status b2sr_spmv(b2sr_handle h, b2sr_semiring semiring, b2sr_vec in_kind, const void* x,
+                      b2sr_vec out_kind, void* y, const uint32_t* mask, int mask_complement,
+                      const float* weights, void* stream);
+
+/* Boolean SpMM with 64 frontiers packed per vertex (multi-source BFS step; a
+ * batched form of bmv_bin_bin_bin_masked, Table 2, with the complemented
+ * visited mask of Sec. V BFS):
+ *   Y_i = OR_{j: A_ij=1} X_j, then Y_i &= M_i (complement = 0) or ~M_i (1).
+ *   X, Y device uint64[n]; M device uint64[n] or NULL. */
+b2sr_status b2sr_spmm_bits64(b2sr_handle h, const uint64_t* X, uint64_t* Y, const uint64_t* M,
+                             int complement, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* SpGEMM: the BMM schemes of Table 3 and the Boolean product              */
+/* ---------------------------------------------------------------------- */
+
+/* bmm_bin_bin_sum_masked (Table 3, Listing 2): the sum over the entries (i,j)
+ * of M of (A B^T)_ij = |row_i(A) AND row_j(B)|, reduced into one int64 with
+ * the reduction fused (Sec. V, TC).  Rows of B are used directly, as
+ * Listing 2's popc(r0 & shfl(r1)) does, so triangle counting passes
+ * A = B = M = L.  All three handles need the same n and tile_dim.
+ *   count  device int64[1] (written, not accumulated). */
+b2sr_status b2sr_spgemm_masked_count(b2sr_handle A, b2sr_handle B, b2sr_handle M, int64_t* count,
+                                     void* stream);
+
+/* Boolean SpGEMM C = A (x) B over OR-AND, output in B2SR with the same
+ * tile_dim (not in the paper's Table 3; built from the same tile products):
+ * C_IJ[r] = OR_K OR_{m: bit m of A_IK[r]} B_KJ[m].  Synchronises `stream`. */
+b2sr_status b2sr_spgemm_bool(b2sr_handle A, b2sr_handle B, void* stream, b2sr_handle* C);
+
+/* ---------------------------------------------------------------------- */
+/* Graph algorithms (Sec. V)                                               */
+/* ---------------------------------------------------------------------- */
+
+/* BFS levels from `src` (Sec. V BFS: Boolean semiring, the visited set as a
+ * complemented mask).  levels device int32[n]: 0 at src, -1 if unreachable.
+ * At most max_iters levels (<= 0: n); B2SR_ERR_NOT_CONVERGED if exceeded.
+ * Synchronises `stream` once per batch of levels. */
+b2sr_status b2sr_bfs(b2sr_handle h, int32_t src, int32_t* levels, int max_iters, void* stream);
+
+/* Multi-source BFS: up to 64 BFS runs of Sec. V advance together, their
+ * frontiers packed as one uint64 per vertex (b2sr_spmm_bits64).
+ *   srcs_host host int32[nsrc], 1 <= nsrc <= 64
+ *   levels    device int32[nsrc * n]: row s holds the levels of srcs_host[s] */
+b2sr_status b2sr_bfs_multi(b2sr_handle h, const int32_t* srcs_host, int nsrc, int32_t* levels,
+                           int max_iters, void* stream);
+
+/* Single-source shortest paths (Sec. V SSSP): rounds of min-plus SpMV
+ * relaxation, d <- min(d, A min.+ d), until no distance changes (the fixed
+ * point delta-stepping also reaches).  weights in set-bit order
+ * (b2sr_weights_from_csr), non-negative, or NULL for unit weights.
+ * dist device float[n]: 0 at src, +inf if unreachable. */
+b2sr_status b2sr_sssp(b2sr_handle h, const float* weights, int32_t src, float* dist, int max_iters,
+                      void* stream);
+
+/* PageRank (Sec. V PR): x^0 = 1/n, then `iters` steps of
+ *   x_i <- (1-d) t_i + d * sum_{j: A_ij=1} x_j / outdeg(j)
+ * with outdeg(j) the number of ones in column j (the column-stochastic
+ * matrix); vertices without out-edges pass nothing on.
+ *   teleport device float[n] or NULL for uniform 1/n;  pr device float[n]. */
+b2sr_status b2sr_pagerank(b2sr_handle h, float d, int iters, const float* teleport, float* pr,
+                          void* stream);
+
+/* Connected components (Sec. V CC, FastSV hooking and shortcutting with the
+ * min step of b2sr_spmv).  labels device int32[n]: the smallest vertex id in
+ * each vertex's component.  Undirected (symmetric) matrices. */
+b2sr_status b2sr_cc(b2sr_handle h, int32_t* labels, int max_iters, void* stream);
+
+/* Triangle count (Sec. V TC): sum(L .* (L L^T)) for L = b2sr_lower(h), by
+ * b2sr_spgemm_masked_count.  Symmetric matrices.  count device int64[1]. */
+b2sr_status b2sr_tc(b2sr_handle h, int64_t* count, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* B2SR_H */

@@ -1,0 +1,277 @@
+"""Thin ctypes binding of libb2sr.so (the C ABI in include/b2sr.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+PyTorch supplies device memory and the current CUDA stream.  The functions
+keep the C names; a failed call raises B2SRError with the library's message.
+Importing this module loads the library and fails loudly if it has not been
+built (``python -c "import __graft_entry__ as g; g.build()"``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libb2sr.so")
+
+BOOL_OR_AND, PLUS_TIMES, MIN_PLUS = 0, 1, 2
+VEC_BITS, VEC_I32, VEC_F32 = 0, 1, 2
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_TILE", 3: "OOM", 4: "CUDA", 5: "NOT_CONVERGED",
+          6: "ADMISSION_REFUSED", 7: "ABORTED"}
+WORD_BYTES = {4: 1, 8: 1, 16: 2, 32: 4}
+
+
+class B2SRError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("tile_dim", ctypes.c_int32), ("n_tile_rows", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("n_tiles", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("bytes", ctypes.c_int64)]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"the CUDA library {LIB_PATH} is not built; run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    p, i32, i64, c_int, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int, ctypes.c_float
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sigs = {
+        "b2sr_last_error": (ctypes.c_char_p, []),
+        "b2sr_version": (ctypes.c_char_p, []),
+        "b2sr_from_csr": (c_int, [i32, p, p, i64, c_int, p, pp]),
+        "b2sr_to_csr": (c_int, [p, p, p, ctypes.POINTER(i64), p]),
+        "b2sr_info": (c_int, [p, ctypes.POINTER(Info)]),
+        "b2sr_arrays": (c_int, [p, pp, pp, pp]),
+        "b2sr_export": (c_int, [p, p, p, p, p]),
+        "b2sr_destroy": (c_int, [p]),
+        "b2sr_lower": (c_int, [p, p, pp]),
+        "b2sr_weights_from_csr": (c_int, [p, p, p, p, p, p]),
+        "b2sr_spmv": (c_int, [p, c_int, c_int, p, c_int, p, p, c_int, p, p]),
+        "b2sr_spmm_bits64": (c_int, [p, p, p, p, c_int, p]),
+        "b2sr_spgemm_masked_count": (c_int, [p, p, p, p, p]),
+        "b2sr_spgemm_bool": (c_int, [p, p, p, pp]),
+        "b2sr_bfs": (c_int, [p, i32, p, c_int, p]),
+        "b2sr_bfs_multi": (c_int, [p, p, c_int, p, c_int, p]),
+        "b2sr_sssp": (c_int, [p, p, i32, p, c_int, p]),
+        "b2sr_pagerank": (c_int, [p, f32, c_int, p, p, p]),
+        "b2sr_cc": (c_int, [p, p, c_int, p]),
+        "b2sr_tc": (c_int, [p, p, p]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(status: int):
+    if status != 0:
+        raise B2SRError(status, lib.b2sr_last_error().decode())
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def bitset_words(n: int) -> int:
+    return (n + 31) // 32
+
+
+class Matrix:
+    """Owner of a b2sr_handle; released by close() or garbage collection."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        inf = Info()
+        _check(lib.b2sr_info(self._h, ctypes.byref(inf)))
+        self.n = inf.n
+        self.tile_dim = inf.tile_dim
+        self.n_tile_rows = inf.n_tile_rows
+        self.n_tiles = inf.n_tiles
+        self.nnz = inf.nnz
+        self.bytes = inf.bytes
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("matrix is closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _check(lib.b2sr_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# ---------------------------------------------------------------------------
+# storage
+# ---------------------------------------------------------------------------
+
+def b2sr_from_csr(n: int, rowptr: torch.Tensor, colind: torch.Tensor, tile_dim: int, stream=None) -> Matrix:
+    h = ctypes.c_void_p()
+    _check(lib.b2sr_from_csr(int(n), _ptr(rowptr), _ptr(colind), int(colind.numel()), int(tile_dim),
+                             _stream(stream), ctypes.byref(h)))
+    return Matrix(h)
+
+
+def b2sr_to_csr(m: Matrix, stream=None):
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rowptr = torch.empty(m.n + 1, dtype=torch.int32, device=dev)
+    nnz = ctypes.c_int64()
+    _check(lib.b2sr_to_csr(m.handle, _ptr(rowptr), None, ctypes.byref(nnz), _stream(stream)))
+    colind = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=dev)
+    _check(lib.b2sr_to_csr(m.handle, _ptr(rowptr), _ptr(colind), ctypes.byref(nnz), _stream(stream)))
+    return rowptr, colind[: nnz.value]
+
+
+def b2sr_export(m: Matrix, stream=None):
+    """(TileRowPtr int32, TileColInd int32, BitTiles uint8 bytes) as new CUDA tensors."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    trp = torch.empty(m.n_tile_rows + 1, dtype=torch.int32, device=dev)
+    tci = torch.empty(max(m.n_tiles, 1), dtype=torch.int32, device=dev)
+    tiles = torch.empty(max(m.n_tiles * m.tile_dim * WORD_BYTES[m.tile_dim], 1), dtype=torch.uint8, device=dev)
+    _check(lib.b2sr_export(m.handle, _ptr(trp), _ptr(tci), _ptr(tiles), _stream(stream)))
+    return trp, tci[: m.n_tiles], tiles[: m.n_tiles * m.tile_dim * WORD_BYTES[m.tile_dim]]
+
+
+def b2sr_lower(m: Matrix, stream=None) -> Matrix:
+    h = ctypes.c_void_p()
+    _check(lib.b2sr_lower(m.handle, _stream(stream), ctypes.byref(h)))
+    return Matrix(h)
+
+
+def b2sr_weights_from_csr(m: Matrix, rowptr: torch.Tensor, colind: torch.Tensor, w_csr: torch.Tensor,
+                          stream=None) -> torch.Tensor:
+    out = torch.empty(max(m.nnz, 1), dtype=torch.float32, device=w_csr.device)
+    _check(lib.b2sr_weights_from_csr(m.handle, _ptr(rowptr), _ptr(colind), _ptr(w_csr), _ptr(out),
+                                     _stream(stream)))
+    return out[: m.nnz]
+
+
+# ---------------------------------------------------------------------------
+# SpMV / SpMM
+# ---------------------------------------------------------------------------
+
+def b2sr_spmv(m: Matrix, semiring: int, in_kind: int, x: torch.Tensor, out_kind: int, y: torch.Tensor,
+              mask: Optional[torch.Tensor] = None, mask_complement: bool = False,
+              weights: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    _check(lib.b2sr_spmv(m.handle, int(semiring), int(in_kind), _ptr(x), int(out_kind), _ptr(y), _ptr(mask),
+                         int(bool(mask_complement)), _ptr(weights), _stream(stream)))
+    return y
+
+
+def b2sr_spmm_bits64(m: Matrix, X: torch.Tensor, Y: torch.Tensor, M: Optional[torch.Tensor] = None,
+                     complement: bool = False, stream=None) -> torch.Tensor:
+    _check(lib.b2sr_spmm_bits64(m.handle, _ptr(X), _ptr(Y), _ptr(M), int(bool(complement)), _stream(stream)))
+    return Y
+
+
+# ---------------------------------------------------------------------------
+# SpGEMM
+# ---------------------------------------------------------------------------
+
+def b2sr_spgemm_masked_count(A: Matrix, B: Matrix, M: Matrix, count: Optional[torch.Tensor] = None,
+                             stream=None) -> torch.Tensor:
+    if count is None:
+        count = torch.empty(1, dtype=torch.int64, device=torch.device("cuda", torch.cuda.current_device()))
+    _check(lib.b2sr_spgemm_masked_count(A.handle, B.handle, M.handle, _ptr(count), _stream(stream)))
+    return count
+
+
+def b2sr_spgemm_bool(A: Matrix, B: Matrix, stream=None) -> Matrix:
+    h = ctypes.c_void_p()
+    _check(lib.b2sr_spgemm_bool(A.handle, B.handle, _stream(stream), ctypes.byref(h)))
+    return Matrix(h)
+
+
+# ---------------------------------------------------------------------------
+# graph algorithms
+# ---------------------------------------------------------------------------
+
+def _dev():
+    return torch.device("cuda", torch.cuda.current_device())
+
+
+def b2sr_bfs(m: Matrix, src: int, levels: Optional[torch.Tensor] = None, max_iters: int = 0,
+             stream=None) -> torch.Tensor:
+    if levels is None:
+        levels = torch.empty(max(m.n, 1), dtype=torch.int32, device=_dev())
+    _check(lib.b2sr_bfs(m.handle, int(src), _ptr(levels), int(max_iters), _stream(stream)))
+    return levels[: m.n]
+
+
+def b2sr_bfs_multi(m: Matrix, srcs: Sequence[int], levels: Optional[torch.Tensor] = None, max_iters: int = 0,
+                   stream=None) -> torch.Tensor:
+    srcs = [int(s) for s in srcs]
+    arr = (ctypes.c_int32 * len(srcs))(*srcs)
+    if levels is None:
+        levels = torch.empty((len(srcs), max(m.n, 1)), dtype=torch.int32, device=_dev())
+    _check(lib.b2sr_bfs_multi(m.handle, arr, len(srcs), _ptr(levels), int(max_iters), _stream(stream)))
+    return levels
+
+
+def b2sr_sssp(m: Matrix, src: int, weights: Optional[torch.Tensor] = None, dist: Optional[torch.Tensor] = None,
+              max_iters: int = 0, stream=None) -> torch.Tensor:
+    if dist is None:
+        dist = torch.empty(max(m.n, 1), dtype=torch.float32, device=_dev())
+    _check(lib.b2sr_sssp(m.handle, _ptr(weights), int(src), _ptr(dist), int(max_iters), _stream(stream)))
+    return dist[: m.n]
+
+
+def b2sr_pagerank(m: Matrix, d: float = 0.85, iters: int = 20, teleport: Optional[torch.Tensor] = None,
+                  pr: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    if pr is None:
+        pr = torch.empty(max(m.n, 1), dtype=torch.float32, device=_dev())
+    _check(lib.b2sr_pagerank(m.handle, float(d), int(iters), _ptr(teleport), _ptr(pr), _stream(stream)))
+    return pr[: m.n]
+
+
+def b2sr_cc(m: Matrix, labels: Optional[torch.Tensor] = None, max_iters: int = 0, stream=None) -> torch.Tensor:
+    if labels is None:
+        labels = torch.empty(max(m.n, 1), dtype=torch.int32, device=_dev())
+    _check(lib.b2sr_cc(m.handle, _ptr(labels), int(max_iters), _stream(stream)))
+    return labels[: m.n]
+
+
+def b2sr_tc(m: Matrix, count: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    if count is None:
+        count = torch.empty(1, dtype=torch.int64, device=_dev())
+    _check(lib.b2sr_tc(m.handle, _ptr(count), _stream(stream)))
+    return count
+
+
+def version() -> str:
+    return lib.b2sr_version().decode()

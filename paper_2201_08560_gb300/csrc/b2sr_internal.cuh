@@ -1,0 +1,152 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "b2sr.h"
+
+#define B2SR_VERSION "0.1.0"
+
+namespace b2sr {
+
+// ---------------------------------------------------------------------------
+// error reporting
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+void clear_error();
+b2sr_status fail(b2sr_status st, const std::string& msg);
+b2sr_status cuda_fail(cudaError_t e, const char* what);
+
+#define B2SR_CUDA_TRY(expr)                                                 \
+    do {                                                                    \
+        cudaError_t _e = (expr);                                            \
+        if (_e != cudaSuccess) return ::b2sr::cuda_fail(_e, #expr);         \
+    } while (0)
+
+#define B2SR_LAUNCH_CHECK(name)                                             \
+    do {                                                                    \
+        cudaError_t _e = cudaGetLastError();                                \
+        if (_e != cudaSuccess) return ::b2sr::cuda_fail(_e, name);          \
+    } while (0)
+
+#define B2SR_TRY(expr)                                                      \
+    do {                                                                    \
+        b2sr_status _s = (expr);                                            \
+        if (_s != B2SR_OK) return _s;                                       \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// geometry
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int word_bytes(int k) { return k <= 8 ? 1 : (k == 16 ? 2 : 4); }
+__host__ __device__ inline int tile_bytes(int k) { return k * word_bytes(k); }
+inline bool valid_tile(int k) { return k == 4 || k == 8 || k == 16 || k == 32; }
+
+// Tiles per warp-chunk of the SpMV kernels: 32 lanes x P tiles, P = 512/(32 k)
+// rounded so one chunk holds 2-8 KB of tile data.
+__host__ __device__ constexpr int tiles_per_lane(int k) {
+    return k == 4 ? 16 : (k == 8 ? 8 : (k == 16 ? 4 : 2));
+}
+__host__ __device__ constexpr int chunk_tiles(int k) { return 32 * tiles_per_lane(k); }
+// Arrays are padded (zero-filled) to a multiple of this many tiles so a chunk
+// can always be copied whole.
+constexpr int64_t kTilePad = 512;
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---------------------------------------------------------------------------
+// device memory through the stream-ordered allocator
+// ---------------------------------------------------------------------------
+b2sr_status dmalloc(void** p, size_t bytes, cudaStream_t s);
+void dfree(void* p, cudaStream_t s);
+
+template <class T>
+b2sr_status dalloc(T** p, size_t count, cudaStream_t s) {
+    return dmalloc(reinterpret_cast<void**>(p), count * sizeof(T), s);
+}
+
+// RAII owner for temporaries freed on a stream.
+struct DevBuf {
+    void* p = nullptr;
+    cudaStream_t s = nullptr;
+    DevBuf() = default;
+    explicit DevBuf(cudaStream_t st) : s(st) {}
+    ~DevBuf() { if (p) dfree(p, s); }
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    b2sr_status alloc(size_t bytes) { return dmalloc(&p, bytes, s); }
+    template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+int sm_count();
+
+}  // namespace b2sr
+
+// ---------------------------------------------------------------------------
+// the handle
+// ---------------------------------------------------------------------------
+struct b2sr_matrix {
+    int32_t n = 0;
+    int32_t k = 0;
+    int32_t ntr = 0;       // nTileRow
+    int64_t T = 0;         // non-empty tiles
+    int64_t nnz = 0;       // set bits
+    int64_t cap = 0;       // allocated tiles (T rounded up to kTilePad, >= kTilePad)
+    int32_t* rowptr = nullptr;   // [ntr+1]
+    int32_t* colind = nullptr;   // [cap], zero padding after T
+    uint8_t* tiles = nullptr;    // [cap * k * word_bytes], zero padding after T
+    // SpMV schedule: chunk_row[c] = tile-row holding tile min(c*CT, T-1), c in [0, nchunks]
+    int32_t* chunk_row = nullptr;
+    int64_t nchunks = 0;
+    int32_t first_row = 0;       // tile-row of tile 0 (ntr if T == 0)
+    int32_t last_row = -1;       // tile-row of tile T-1 (-1 if T == 0)
+    // lazily built, cached derived arrays (built under the handle's mutex)
+    int32_t* voff = nullptr;     // [T+1] set bits before each tile (weights offsets)
+    int32_t* outdeg = nullptr;   // [n] ones per column
+    int device = 0;
+    void* mtx = nullptr;         // std::mutex*
+};
+
+namespace b2sr {
+b2sr_status check_handle(const b2sr_matrix* h);
+b2sr_status ensure_voff(b2sr_matrix* h, cudaStream_t s);
+b2sr_status ensure_outdeg(b2sr_matrix* h, cudaStream_t s);
+b2sr_status build_schedule(b2sr_matrix* h, cudaStream_t s);
+b2sr_status new_handle_from_tiles(int32_t n, int k, int64_t T, int32_t* rowptr, int32_t* colind,
+                                  uint8_t* tiles, int64_t cap, cudaStream_t s, b2sr_matrix** out);
+
+// primitives (primitives.cu)
+b2sr_status exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+b2sr_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+// Stable LSD radix sort of keys[0..N) by bits [lo_bit, hi_bit); tmp has N entries.
+// Returns in *result which buffer (keys or tmp) holds the sorted keys.
+b2sr_status radix_sort_u64(uint64_t* keys, uint64_t* tmp, int64_t N, int lo_bit, int hi_bit,
+                           cudaStream_t s, uint64_t** result);
+// Same, carrying a uint32 payload alongside each key.
+b2sr_status radix_sort_u64_pairs(uint64_t* keys, uint64_t* ktmp, uint32_t* vals, uint32_t* vtmp,
+                                 int64_t N, int lo_bit, int hi_bit, cudaStream_t s,
+                                 uint64_t** kres, uint32_t** vres);
+b2sr_status popcount_bytes(const uint8_t* p, int64_t bytes, int64_t* out_dev, cudaStream_t s);
+b2sr_status fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t s);
+
+inline cudaStream_t to_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace b2sr
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t ld_bits(const uint32_t* __restrict__ bits, int64_t bitoff, int k) {
+    // k consecutive bits starting at bitoff (bitoff % k == 0)
+    const uint8_t* b8 = reinterpret_cast<const uint8_t*>(bits);
+    if (k == 32) return __ldg(bits + (bitoff >> 5));
+    if (k == 16) return __ldg(reinterpret_cast<const uint16_t*>(bits) + (bitoff >> 4));
+    if (k == 8) return __ldg(b8 + (bitoff >> 3));
+    return (__ldg(b8 + (bitoff >> 3)) >> (bitoff & 4)) & 0xFu;
+}

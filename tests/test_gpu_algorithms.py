@@ -1,0 +1,207 @@
+"""GPU parity: SpGEMM (Table 3 and the Boolean product) and the Sec. V graph
+algorithms (BFS, multi-source BFS, SSSP, PageRank, CC, TC) against the oracle.
+Levels, labels and counts are bit-exact; PageRank and continuous-weight SSSP
+are within 1e-5 relative error of the fp64 oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2201_08560_gb300 import graphs
+from tests.gpu_util import GRAPH_IDS, csr_dev, small_graphs, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+KS = [4, 8, 16, 32]
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2201_08560_gb300 import binding
+    return binding
+
+
+def mat(B, g, k):
+    rp, ci = csr_dev(g)
+    return B.b2sr_from_csr(g.n, rp, ci, k)
+
+
+# ---------------------------------------------------------------- SpGEMM ---
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("n,da,db,seed", [(1, 1.0, 1.0, 0), (77, 0.08, 0.1, 1), (300, 0.02, 0.03, 2)])
+def test_masked_count_asymmetric(B, k, n, da, db, seed):
+    A = graphs.random_directed(n, da, seed)
+    Bm = graphs.random_directed(n, db, seed + 50)
+    M = graphs.random_directed(n, 0.3, seed + 99)
+    with mat(B, A, k) as a, mat(B, Bm, k) as b, mat(B, M, k) as mm:
+        got = int(B.b2sr_spgemm_masked_count(a, b, mm).item())
+    assert got == oracle.masked_count(A, Bm, M)
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("gi", [0, 1, 2, 3, 4, 6, 7, 8], ids=["rmat12", "rmat11perm", "star20k", "grid37x41",
+                                                               "gaps", "n1", "empty45", "mycielski9"])
+def test_triangle_count(B, k, gi):
+    g = small_graphs()[gi]
+    with mat(B, g, k) as m:
+        assert int(B.b2sr_tc(m).item()) == oracle.triangle_count(g)
+
+
+@pytest.mark.parametrize("n", [5, 33, 70])
+def test_triangle_count_complete(B, n):
+    g = graphs.complete(n)
+    for k in KS:
+        with mat(B, g, k) as m:
+            assert int(B.b2sr_tc(m).item()) == math.comb(n, 3)
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("n,da,db,seed", [(1, 1.0, 1.0, 0), (90, 0.05, 0.05, 1), (257, 0.01, 0.02, 2)])
+def test_spgemm_bool(B, k, n, da, db, seed):
+    A = graphs.random_directed(n, da, seed)
+    Bm = graphs.random_directed(n, db, seed + 7)
+    C = oracle.spgemm_bool(A, Bm)
+    with mat(B, A, k) as a, mat(B, Bm, k) as b, B.b2sr_spgemm_bool(a, b) as c:
+        rp, ci = B.b2sr_to_csr(c)
+        np.testing.assert_array_equal(to_np(rp), C.rowptr)
+        np.testing.assert_array_equal(to_np(ci), C.colind)
+        trp, tci, tiles = oracle.b2sr(C, k)
+        assert c.n_tiles == len(tci)
+
+
+def test_spgemm_bool_rmat(B):
+    g = graphs.rmat(10, 8, seed=2)
+    C = oracle.spgemm_bool(g, g)
+    for k in KS:
+        with mat(B, g, k) as a, B.b2sr_spgemm_bool(a, a) as c:
+            rp, ci = B.b2sr_to_csr(c)
+            np.testing.assert_array_equal(to_np(ci), C.colind)
+
+
+# ------------------------------------------------------------------- BFS ---
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("gi", range(len(GRAPH_IDS)), ids=GRAPH_IDS)
+def test_bfs(B, k, gi):
+    g = small_graphs()[gi]
+    gc = oracle.canonicalize(g)
+    srcs = [0, g.n - 1, g.n // 2]
+    with mat(B, g, k) as m:
+        for s in srcs:
+            np.testing.assert_array_equal(to_np(B.b2sr_bfs(m, s)), oracle.bfs(gc, s))
+
+
+def test_bfs_closed_forms(B):
+    for k in KS:
+        with mat(B, graphs.path(300), k) as m:
+            np.testing.assert_array_equal(to_np(B.b2sr_bfs(m, 17)), np.abs(np.arange(300) - 17))
+        R, C = 45, 38
+        with mat(B, graphs.grid2d(R, C), k) as m:
+            rr, cc = np.divmod(np.arange(R * C), C)
+            np.testing.assert_array_equal(to_np(B.b2sr_bfs(m, 0)), rr + cc)
+
+
+def test_bfs_errors(B):
+    g = graphs.path(50)
+    with mat(B, g, 8) as m:
+        with pytest.raises(B.B2SRError) as e:
+            B.b2sr_bfs(m, 50)
+        assert e.value.status == 1
+        with pytest.raises(B.B2SRError) as e:
+            B.b2sr_bfs(m, 0, max_iters=10)   # the path needs 49 levels
+        assert e.value.status == 5
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("gi", [0, 1, 3, 4, 5], ids=["rmat12", "rmat11perm", "grid37x41", "gaps", "directed300"])
+def test_bfs_multi(B, k, gi):
+    g = small_graphs()[gi]
+    gc = oracle.canonicalize(g)
+    srcs = list(graphs.sources(g, 64, seed=gi)) if gi != 4 else list(range(0, g.n, max(1, g.n // 40)))[:64]
+    with mat(B, g, k) as m:
+        lv = to_np(B.b2sr_bfs_multi(m, srcs))
+        for s_i, s in enumerate(srcs):
+            np.testing.assert_array_equal(lv[s_i], oracle.bfs(gc, int(s)))
+        # a smaller batch gives the same rows
+        lv3 = to_np(B.b2sr_bfs_multi(m, srcs[:3]))
+        np.testing.assert_array_equal(lv3, lv[:3])
+
+
+# ------------------------------------------------------------------ SSSP ---
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("gi", [0, 3, 4, 5], ids=["rmat12", "grid37x41", "gaps", "directed300"])
+def test_sssp(B, k, gi):
+    g = oracle.canonicalize(small_graphs()[gi])
+    rng = np.random.default_rng(gi)
+    w_grid = (1 + rng.integers(0, 99 * 16, g.colind.size) / 16).astype(np.float32)
+    w_cont = rng.uniform(1.0, 100.0, g.colind.size).astype(np.float32)
+    rp, ci = to_dev(g.rowptr), to_dev(g.colind)
+    with B.b2sr_from_csr(g.n, rp, ci, k) as m:
+        # unit weights: distances equal BFS levels
+        d = to_np(B.b2sr_sssp(m, 0))
+        lv = oracle.bfs(g, 0).astype(np.float64)
+        lv[lv < 0] = np.inf
+        np.testing.assert_array_equal(d.astype(np.float64), lv)
+        for w, exact in ((w_grid, True), (w_cont, False)):
+            wb = B.b2sr_weights_from_csr(m, rp, ci, to_dev(w))
+            d = to_np(B.b2sr_sssp(m, 1, wb)).astype(np.float64)
+            ref = oracle.sssp(g, 1, w)
+            if exact:
+                np.testing.assert_array_equal(d, ref)
+            else:
+                fin = np.isfinite(ref)
+                assert (np.isfinite(d) == fin).all()
+                np.testing.assert_allclose(d[fin], ref[fin], rtol=1e-5)
+
+
+# -------------------------------------------------------------------- PR ---
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("gi", [0, 1, 2, 3, 4, 5, 8], ids=["rmat12", "rmat11perm", "star20k", "grid37x41", "gaps",
+                                                            "directed300", "mycielski9"])
+def test_pagerank(B, k, gi):
+    g = oracle.canonicalize(small_graphs()[gi])
+    rp, ci = to_dev(g.rowptr), to_dev(g.colind)
+    with B.b2sr_from_csr(g.n, rp, ci, k) as m:
+        for iters in (1, 20, 50):
+            pr = to_np(B.b2sr_pagerank(m, 0.85, iters)).astype(np.float64)
+            ref = oracle.pagerank(g, 0.85, iters)
+            np.testing.assert_allclose(pr, ref, rtol=1e-5, atol=0)
+        tele = np.random.default_rng(gi).random(g.n)
+        tele /= tele.sum()
+        pr = to_np(B.b2sr_pagerank(m, 0.85, 20, to_dev(tele.astype(np.float32)))).astype(np.float64)
+        ref = oracle.pagerank(g, 0.85, 20, tele.astype(np.float32).astype(np.float64))
+        np.testing.assert_allclose(pr, ref, rtol=1e-5, atol=0)
+
+
+def test_pagerank_closed_forms(B):
+    for g in (graphs.cycle(1000), graphs.torus2d(30, 40)):
+        for k in KS:
+            with mat(B, g, k) as m:
+                np.testing.assert_allclose(to_np(B.b2sr_pagerank(m, 0.85, 30)), 1.0 / g.n, rtol=1e-6)
+
+
+# -------------------------------------------------------------------- CC ---
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("gi", [0, 1, 2, 3, 4, 6, 7, 8], ids=["rmat12", "rmat11perm", "star20k", "grid37x41",
+                                                               "gaps", "n1", "empty45", "mycielski9"])
+def test_cc(B, k, gi):
+    g = small_graphs()[gi]
+    with mat(B, g, k) as m:
+        np.testing.assert_array_equal(to_np(B.b2sr_cc(m)), oracle.cc(oracle.canonicalize(g)))
+
+
+def test_cc_disjoint_unions(B):
+    parts = [graphs.path(300), graphs.complete(9), graphs.cycle(41), graphs.star(77), graphs.path(1),
+             graphs.grid2d(20, 30)]
+    u = graphs.permute(graphs.disjoint_union(*parts), seed=3)
+    for k in KS:
+        with mat(B, u, k) as m:
+            lab = to_np(B.b2sr_cc(m))
+            np.testing.assert_array_equal(lab, oracle.cc(u))
+            assert len(set(lab.tolist())) == len(parts)
