@@ -84,7 +84,7 @@ __global__ void fill_tiles_kernel(const uint64_t* __restrict__ keys, const int32
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N;
          e += (int64_t)gridDim.x * blockDim.x) {
         uint64_t key = keys[e];
-        int64_t t = tidx[e];
+        int64_t t = tidx[e] + flag[e] - 1;  // tile of this entry's run (tidx counts heads before e)
         int p = (int)(key & 1023u);
         if (flag[e]) {
             colind[t] = (int32_t)((key >> 10) & jmask);

@@ -26,45 +26,56 @@
 namespace b2sr {
 
 // ---------------------------------------------------------------------------
-// tile access (shared memory copy of a chunk)
+// tile words.  A lane holds its P tiles as 32-bit words: TW words per tile
+// (k=4: 1, k=8: 2, k=16: 8, k=32: 32); row r of a tile is byte r (k<=8),
+// half-word r (k=16) or word r (k=32).
 // ---------------------------------------------------------------------------
 template <int K>
-__device__ __forceinline__ uint32_t srow(const uint8_t* tile, int r) {
-    if (K == 32) return reinterpret_cast<const uint32_t*>(tile)[r];
-    if (K == 16) return reinterpret_cast<const uint16_t*>(tile)[r];
-    return tile[r];
+struct ChunkShape {
+    static constexpr int P = tiles_per_lane(K);
+    static constexpr int CT = 32 * P;
+    static constexpr int TB = K * (K <= 8 ? 1 : (K == 16 ? 2 : 4));
+    static constexpr int TW = TB / 4;
+    static constexpr int TILE_V4 = P * TB / 16;   // uint4 loads per lane for its tiles
+};
+
+template <int K>
+__device__ __forceinline__ uint32_t row_word(const uint32_t* w, int r) {
+    if (K == 32) return w[r];
+    if (K == 16) return (w[r >> 1] >> (16 * (r & 1))) & 0xFFFFu;
+    return (w[r >> 2] >> (8 * (r & 3))) & 0xFFu;
 }
 
-// Bit r of the result is set iff row word r of the tile shares a bit with xs
-// (the k-bit segment of the input vector under the tile's column).
+// Bit r of the result is set iff row r of the tile shares a bit with xs (the
+// k-bit segment of the input vector under the tile's column).
 template <int K>
-__device__ __forceinline__ uint32_t rows_hit(const uint8_t* tile, uint32_t xs) {
+__device__ __forceinline__ uint32_t rows_hit(const uint32_t* w, uint32_t xs) {
     if (K == 4 || K == 8) {
-        // four rows per 32-bit word, one per byte: flag the non-zero bytes
-        // (high bit per byte), then gather the four flags with one multiply
+        // four rows per word, one per byte: flag the non-zero bytes (high bit
+        // per byte), then gather the four flags with one multiply
         const uint32_t rep = xs * 0x01010101u;
         uint32_t out = 0;
 #pragma unroll
-        for (int w = 0; w < K / 4; ++w) {
-            uint32_t m = reinterpret_cast<const uint32_t*>(tile)[w] & rep;
+        for (int q = 0; q < K / 4; ++q) {
+            uint32_t m = w[q] & rep;
             uint32_t h = (((m & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | m) & 0x80808080u;
-            out |= (((h >> 7) * 0x00204081u) >> 21 & 0xFu) << (4 * w);
+            out |= (((h >> 7) * 0x00204081u) >> 21 & 0xFu) << (4 * q);
         }
         return out;
     } else if (K == 16) {
         const uint32_t rep = xs | (xs << 16);
         uint32_t out = 0;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) {
-            uint32_t m = reinterpret_cast<const uint32_t*>(tile)[w] & rep;
-            out |= ((m & 0xFFFFu) ? 1u : 0u) << (2 * w);
-            out |= ((m >> 16) ? 1u : 0u) << (2 * w + 1);
+        for (int q = 0; q < 8; ++q) {
+            uint32_t m = w[q] & rep;
+            out |= ((m & 0xFFFFu) ? 1u : 0u) << (2 * q);
+            out |= ((m >> 16) ? 1u : 0u) << (2 * q + 1);
         }
         return out;
     } else {
         uint32_t out = 0;
 #pragma unroll
-        for (int r = 0; r < 32; ++r) out |= ((reinterpret_cast<const uint32_t*>(tile)[r] & xs) ? 1u : 0u) << r;
+        for (int r = 0; r < 32; ++r) out |= ((w[r] & xs) ? 1u : 0u) << r;
         return out;
     }
 }
@@ -76,10 +87,13 @@ __device__ __forceinline__ bool mask_allows(const uint32_t* __restrict__ mask, i
 }
 
 // ---------------------------------------------------------------------------
-// semirings.  Each provides: V (value type), NV (values per accumulator),
-// ident(), comb(a, b) (a earlier in the fixed order), tile(acc, ...) and
-// store(R, acc).  store() applies the self term, the mask and the overwrite
-// rule; empty tile-rows are stored with the identity accumulator.
+// semirings.  Each provides V (accumulator value), NV (values per tile-row
+// accumulator), ident(), comb(a, b) (a earlier in the fixed order) and
+// store(R, acc), which applies the self term, the mask and the overwrite
+// rule (empty tile-rows are stored with the identity accumulator).
+//   bit-vector schemes (kGather = false): xseg(J) and tile(acc, words, xs);
+//   value schemes (kGather = true): one gathered input value per set bit,
+//     src() (the values), weighted and apply(acc, x_j, w_ij).
 // ---------------------------------------------------------------------------
 
 // bmv_bin_bin_bin[_masked]: bitset in, bitset out, acc = k-bit row mask
@@ -87,6 +101,7 @@ template <int K>
 struct SemBool {
     using V = uint32_t;
     static constexpr int NV = 1;
+    static constexpr bool kGather = false;
     const uint32_t* x;
     uint32_t* y;
     const uint32_t* mask;
@@ -94,9 +109,8 @@ struct SemBool {
     int32_t n;
     __device__ V ident() const { return 0u; }
     __device__ V comb(V a, V b) const { return a | b; }
-    __device__ void tile(V (&acc)[NV], const uint8_t* t, int32_t J, int64_t) const {
-        acc[0] |= rows_hit<K>(t, ld_bits(x, (int64_t)J * K, K));
-    }
+    __device__ uint32_t xseg(int32_t J) const { return ld_bits(x, (int64_t)J * K, K); }
+    __device__ void tile(V (&acc)[NV], const uint32_t* w, uint32_t xs) const { acc[0] |= rows_hit<K>(w, xs); }
     __device__ void store(int32_t R, const V (&acc)[NV]) const {
         uint32_t v = acc[0];
         if (mask) {
@@ -123,6 +137,7 @@ template <int K>
 struct SemCount {
     using V = int32_t;
     static constexpr int NV = K;
+    static constexpr bool kGather = false;
     const uint32_t* x;
     int32_t* y;
     const uint32_t* mask;
@@ -130,10 +145,10 @@ struct SemCount {
     int32_t n;
     __device__ V ident() const { return 0; }
     __device__ V comb(V a, V b) const { return a + b; }
-    __device__ void tile(V (&acc)[NV], const uint8_t* t, int32_t J, int64_t) const {
-        uint32_t xs = ld_bits(x, (int64_t)J * K, K);
+    __device__ uint32_t xseg(int32_t J) const { return ld_bits(x, (int64_t)J * K, K); }
+    __device__ void tile(V (&acc)[NV], const uint32_t* w, uint32_t xs) const {
 #pragma unroll
-        for (int r = 0; r < K; ++r) acc[r] += __popc(srow<K>(t, r) & xs);
+        for (int r = 0; r < K; ++r) acc[r] += __popc(row_word<K>(w, r) & xs);
     }
     __device__ void store(int32_t R, const V (&acc)[NV]) const {
 #pragma unroll
@@ -148,26 +163,21 @@ struct SemCount {
 template <int K>
 struct SemPlus {
     using V = float;
+    using G = float;
     static constexpr int NV = K;
+    static constexpr bool kGather = true;
     const float* x;
     float* y;
     const uint32_t* mask;
     int comp;
     int32_t n;
+    static constexpr bool weighted = false;
+    __device__ const float* src() const { return x; }
+    __device__ const float* wts() const { return nullptr; }
+    __device__ const int32_t* voffs() const { return nullptr; }
     __device__ V ident() const { return 0.0f; }
     __device__ V comb(V a, V b) const { return a + b; }
-    __device__ void tile(V (&acc)[NV], const uint8_t* t, int32_t J, int64_t) const {
-        const float* xs = x + (int64_t)J * K;
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-            uint32_t w = srow<K>(t, r);
-            while (w) {
-                int c = __ffs(w) - 1;
-                w &= w - 1;
-                acc[r] += __ldg(xs + c);
-            }
-        }
-    }
+    __device__ V apply(V acc, G xv, float) const { return acc + xv; }
     __device__ void store(int32_t R, const V (&acc)[NV]) const {
 #pragma unroll
         for (int r = 0; r < K; ++r) {
@@ -182,7 +192,9 @@ struct SemPlus {
 template <int K>
 struct SemMinPlus {
     using V = float;
+    using G = float;
     static constexpr int NV = K;
+    static constexpr bool kGather = true;
     const float* x;
     float* y;
     const uint32_t* mask;
@@ -190,35 +202,13 @@ struct SemMinPlus {
     int32_t n;
     const float* w;
     const int32_t* voff;
+    bool weighted;
+    __device__ const float* src() const { return x; }
+    __device__ const float* wts() const { return w; }
+    __device__ const int32_t* voffs() const { return voff; }
     __device__ V ident() const { return INFINITY; }
     __device__ V comb(V a, V b) const { return fminf(a, b); }
-    __device__ void tile(V (&acc)[NV], const uint8_t* t, int32_t J, int64_t ti) const {
-        const float* xs = x + (int64_t)J * K;
-        if (w) {
-            const float* wt = w + __ldg(voff + ti);
-            int q = 0;
-#pragma unroll
-            for (int r = 0; r < K; ++r) {
-                uint32_t b = srow<K>(t, r);
-                while (b) {
-                    int c = __ffs(b) - 1;
-                    b &= b - 1;
-                    acc[r] = fminf(acc[r], __ldg(xs + c) + __ldg(wt + q));
-                    ++q;
-                }
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < K; ++r) {
-                uint32_t b = srow<K>(t, r);
-                while (b) {
-                    int c = __ffs(b) - 1;
-                    b &= b - 1;
-                    acc[r] = fminf(acc[r], __ldg(xs + c) + 1.0f);
-                }
-            }
-        }
-    }
+    __device__ V apply(V acc, G xv, float wv) const { return fminf(acc, xv + wv); }
     __device__ void store(int32_t R, const V (&acc)[NV]) const {
 #pragma unroll
         for (int r = 0; r < K; ++r) {
@@ -232,26 +222,21 @@ struct SemMinPlus {
 template <int K>
 struct SemMinI32 {
     using V = int32_t;
+    using G = int32_t;
     static constexpr int NV = K;
+    static constexpr bool kGather = true;
     const int32_t* x;
     int32_t* y;
     const uint32_t* mask;
     int comp;
     int32_t n;
+    static constexpr bool weighted = false;
+    __device__ const int32_t* src() const { return x; }
+    __device__ const float* wts() const { return nullptr; }
+    __device__ const int32_t* voffs() const { return nullptr; }
     __device__ V ident() const { return INT_MAX; }
     __device__ V comb(V a, V b) const { return min(a, b); }
-    __device__ void tile(V (&acc)[NV], const uint8_t* t, int32_t J, int64_t) const {
-        const int32_t* xs = x + (int64_t)J * K;
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-            uint32_t b = srow<K>(t, r);
-            while (b) {
-                int c = __ffs(b) - 1;
-                b &= b - 1;
-                acc[r] = min(acc[r], __ldg(xs + c));
-            }
-        }
-    }
+    __device__ V apply(V acc, G xv, float) const { return min(acc, xv); }
     __device__ void store(int32_t R, const V (&acc)[NV]) const {
 #pragma unroll
         for (int r = 0; r < K; ++r) {
@@ -265,26 +250,21 @@ struct SemMinI32 {
 template <int K>
 struct SemOr64 {
     using V = unsigned long long;
+    using G = unsigned long long;
     static constexpr int NV = K;
+    static constexpr bool kGather = true;
     const unsigned long long* x;
     unsigned long long* y;
     const unsigned long long* mask;
     int comp;
     int32_t n;
+    static constexpr bool weighted = false;
+    __device__ const unsigned long long* src() const { return x; }
+    __device__ const float* wts() const { return nullptr; }
+    __device__ const int32_t* voffs() const { return nullptr; }
     __device__ V ident() const { return 0ull; }
     __device__ V comb(V a, V b) const { return a | b; }
-    __device__ void tile(V (&acc)[NV], const uint8_t* t, int32_t J, int64_t) const {
-        const unsigned long long* xs = x + (int64_t)J * K;
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-            uint32_t b = srow<K>(t, r);
-            while (b) {
-                int c = __ffs(b) - 1;
-                b &= b - 1;
-                acc[r] |= __ldg(xs + c);
-            }
-        }
-    }
+    __device__ V apply(V acc, G xv, float) const { return acc | xv; }
     __device__ void store(int32_t R, const V (&acc)[NV]) const {
 #pragma unroll
         for (int r = 0; r < K; ++r) {
@@ -313,113 +293,223 @@ struct SpmvGeom {
 
 template <class V>
 struct Partials {
-    int32_t* row_first;  // [nchunks]
-    int32_t* row_last;   // [nchunks]
-    V* val_first;        // [nchunks * NV]
-    V* val_last;         // [nchunks * NV]
+    V* val_first;  // [nchunks * NV]: the chunk's first row, begun in an earlier chunk
+    V* val_last;   // [nchunks * NV]: the chunk's last row, continued in a later chunk
 };
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+template <int BYTES>
+__device__ __forceinline__ void cp_async_gather(void* smem, const void* gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-__device__ __forceinline__ int32_t find_row(const int32_t* __restrict__ rowptr, int32_t lo, int32_t hi,
-                                            int64_t t) {
-    // largest R in [lo, hi] with rowptr[R] <= t
-    while (lo < hi) {
-        int32_t mid = lo + (hi - lo + 1) / 2;
-        if ((int64_t)__ldg(rowptr + mid) <= t) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-template <int K>
-struct ChunkShape {
-    static constexpr int P = tiles_per_lane(K);
-    static constexpr int CT = 32 * P;
-    static constexpr int TB = K * (K <= 8 ? 1 : (K == 16 ? 2 : 4));
-    static constexpr int COL_BYTES = CT * 4;
-    static constexpr int STAGE = COL_BYTES + CT * TB;
-};
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 constexpr int kSpmvThreads = 256;
 constexpr int kSpmvWarps = kSpmvThreads / 32;
+// gathered values staged per warp (set bits of one chunk); the rest are read directly
+template <class G>
+struct GatherSlots {
+    static constexpr int N = sizeof(G) == 8 ? 512 : 1024;
+};
 
-template <int K>
-__device__ __forceinline__ void issue_chunk(uint8_t* dst, const SpmvGeom& g, int64_t c) {
-    using S = ChunkShape<K>;
-    const unsigned lane = lane_id();
-    const uint8_t* col_src = reinterpret_cast<const uint8_t*>(g.colind + c * S::CT);
-    const uint8_t* tile_src = g.tiles + c * S::CT * S::TB;
-#pragma unroll 4
-    for (int i = lane; i < S::COL_BYTES / 16; i += 32) cp_async16(dst + i * 16, col_src + i * 16);
-#pragma unroll 4
-    for (int i = lane; i < S::CT * S::TB / 16; i += 32)
-        cp_async16(dst + S::COL_BYTES + i * 16, tile_src + i * 16);
-}
+template <class SEM, bool GATHER = SEM::kGather>
+struct SmemPerWarp {
+    static constexpr int bytes = 0;
+};
+template <class SEM>
+struct SmemPerWarp<SEM, true> {
+    using G = typename SEM::G;
+    static constexpr int bytes = GatherSlots<G>::N * (int)sizeof(G) + GatherSlots<G>::N * 4;
+};
 
+// One warp per chunk of 32*P consecutive tiles; lane l owns tiles
+// [cs + l*P, cs + l*P + P).
 template <int K, class SEM>
-__device__ __forceinline__ void process_chunk(const uint8_t* buf, const SpmvGeom& g, int64_t c, const SEM& sem,
-                                              Partials<typename SEM::V> part) {
+__global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, SEM sem,
+                                                                   Partials<typename SEM::V> part) {
     using S = ChunkShape<K>;
     using V = typename SEM::V;
     constexpr int NV = SEM::NV;
+    constexpr int P = S::P;
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int warp = threadIdx.x >> 5;
     const int lane = (int)lane_id();
-    const int32_t* scol = reinterpret_cast<const int32_t*>(buf);
-    const uint8_t* stile = buf + S::COL_BYTES;
+    const int64_t c = (int64_t)blockIdx.x * kSpmvWarps + warp;
+    if (c >= g.nchunks) return;
 
     const int64_t cs = c * S::CT;
     const int64_t ce = min(cs + (int64_t)S::CT, g.T);
+    const int64_t tl = cs + (int64_t)lane * P;
+    const int cnt = (int)max((int64_t)0, min((int64_t)P, ce - tl));
+
+    // ---- issue every load of the lane first: tiles, tile columns ----
+    uint4 tv[S::TILE_V4];
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(g.tiles + tl * S::TB);
+#pragma unroll
+        for (int q = 0; q < S::TILE_V4; ++q) tv[q] = __ldg(src + q);
+    }
+    const uint32_t* words = reinterpret_cast<const uint32_t*>(tv);
+    int32_t col[P];
+    if (P % 4 == 0) {
+        const int4* src = reinterpret_cast<const int4*>(g.colind + tl);
+#pragma unroll
+        for (int q = 0; q < P / 4; ++q) {
+            int4 v = __ldg(src + q);
+            col[4 * q] = v.x; col[4 * q + 1] = v.y; col[4 * q + 2] = v.z; col[4 * q + 3] = v.w;
+        }
+    } else {
+        const int2* src = reinterpret_cast<const int2*>(g.colind + tl);
+#pragma unroll
+        for (int q = 0; q < P / 2; ++q) {
+            int2 v = __ldg(src + q);
+            col[2 * q] = v.x; col[2 * q + 1] = v.y;
+        }
+    }
     const int32_t r0 = __ldg(g.chunk_row + c);
     const int32_t r1 = __ldg(g.chunk_row + c + 1);
-    const int64_t tl = cs + (int64_t)lane * S::P;
-    const int64_t te = min(tl + (int64_t)S::P, ce);
-    const bool active = tl < ce;
+
+    // ---- input values: one k-bit segment per tile, or one value per set bit ----
+    uint32_t xs[SEM::kGather ? 1 : P];
+    int gbase = 0;
+    if constexpr (!SEM::kGather) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) xs[i] = sem.xseg(col[i]);
+    } else {
+        using G = typename SEM::G;
+        constexpr int NG = GatherSlots<G>::N;
+        G* sx = reinterpret_cast<G*>(smem + warp * SmemPerWarp<SEM>::bytes);
+        float* sw = reinterpret_cast<float*>(sx + NG);
+        int nb = 0;
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+            if (i < cnt) {
+#pragma unroll
+                for (int q = 0; q < S::TW; ++q) nb += __popc(words[i * S::TW + q]);
+            }
+        int incl = nb;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        gbase = incl - nb;
+        int s = gbase;
+        const G* xsrc = sem.src();
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            if (i < cnt && s < NG) {
+                const G* xt = xsrc + (int64_t)col[i] * K;
+                const float* wt = sem.weighted ? sem.wts() + __ldg(sem.voffs() + tl + i) : nullptr;
+                int qb = 0;
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    uint32_t b = row_word<K>(words + i * S::TW, r);
+                    while (b && s < NG) {
+                        const int cc = __ffs(b) - 1;
+                        b &= b - 1;
+                        cp_async_gather<sizeof(G)>(sx + s, xt + cc);
+                        if (sem.weighted) cp_async_gather<4>(sw + s, wt + qb);
+                        ++s;
+                        ++qb;
+                    }
+                }
+            }
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncwarp();
+    }
+
+    // ---- tile-row of the lane's first tile: rows r0..r1 span the chunk ----
+    int32_t row = r0;
+    if (r1 > r0) {
+        const int32_t span = r1 - r0;
+        int32_t add = 0;
+        for (int32_t base = 0; base < span; base += 32) {
+            const int32_t j = base + lane;
+            const int64_t b = j < span ? (int64_t)__ldg(g.rowptr + r0 + 1 + j) : INT64_MAX;
+            // count of boundaries b_j <= tl (b is sorted across lanes)
+            int pos = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                int64_t v = __shfl_sync(0xffffffffu, b, pos + step - 1);
+                if (v <= tl) pos += step;
+            }
+            pos += (__shfl_sync(0xffffffffu, b, pos) <= tl) ? 1 : 0;
+            add += pos;
+            if (__shfl_sync(0xffffffffu, b, 31) > cs + 32 * P) break;  // later windows start past the chunk
+        }
+        row = r0 + add;
+    }
+
     const bool head_cs = (int64_t)__ldg(g.rowptr + r0) == cs;
-
-    V acc[NV], F[NV];
+    V acc[NV], F[NV], idv[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) { acc[v] = sem.ident(); F[v] = sem.ident(); }
-    V idv[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) idv[v] = sem.ident();
-
-    int32_t row = r1;
-    int32_t first_row = r1;
+    for (int v = 0; v < NV; ++v) { acc[v] = sem.ident(); F[v] = sem.ident(); idv[v] = sem.ident(); }
+    const int32_t first_row = row;
     bool has_end = false;
     bool open = false;
-    if (active) {
-        row = find_row(g.rowptr, r0, r1, tl);
-        first_row = row;
+    if (cnt > 0) {
         // empty tile-rows just before a row that starts at this lane's first tile
         if (tl > 0 && (int64_t)__ldg(g.rowptr + row) == tl)
             for (int32_t R = row - 1; R >= 0 && (int64_t)__ldg(g.rowptr + R) == tl; --R) sem.store(R, idv);
         int64_t next = __ldg(g.rowptr + row + 1);
-        open = true;
-        for (int64_t t = tl; t < te; ++t) {
-            const int li = (int)(t - cs);
-            sem.tile(acc, stile + li * S::TB, scol[li], t);
-            open = true;
-            if (t + 1 == next) {  // tile-row `row` ends with tile t
-                if (!has_end) {
+        int s = gbase;
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) F[v] = acc[v];
-                    has_end = true;
+        for (int i = 0; i < P; ++i) {
+            if (i < cnt) {
+                const int64_t t = tl + i;
+                if constexpr (!SEM::kGather) {
+                    sem.tile(acc, words + i * S::TW, xs[i]);
                 } else {
-                    sem.store(row, acc);
-                }
+                    using G = typename SEM::G;
+                    constexpr int NG = GatherSlots<G>::N;
+                    const G* sx = reinterpret_cast<const G*>(smem + warp * SmemPerWarp<SEM>::bytes);
+                    const float* sw = reinterpret_cast<const float*>(sx + NG);
+                    const G* xt = sem.src() + (int64_t)col[i] * K;
+                    const float* wt = sem.weighted ? sem.wts() + __ldg(sem.voffs() + t) : nullptr;
+                    int qb = 0;
 #pragma unroll
-                for (int v = 0; v < NV; ++v) acc[v] = sem.ident();
-                open = false;
-                if (t + 1 < te) {
-                    int32_t R = row + 1;
-                    while ((int64_t)__ldg(g.rowptr + R + 1) == next) { sem.store(R, idv); ++R; }
-                    row = R;
-                    next = __ldg(g.rowptr + row + 1);
+                    for (int r = 0; r < K; ++r) {
+                        uint32_t b = row_word<K>(words + i * S::TW, r);
+                        while (b) {
+                            const int cc = __ffs(b) - 1;
+                            b &= b - 1;
+                            G xv;
+                            float wv = 1.0f;
+                            if (s < NG) {
+                                xv = sx[s];
+                                if (sem.weighted) wv = sw[s];
+                            } else {
+                                xv = __ldg(xt + cc);
+                                if (sem.weighted) wv = __ldg(wt + qb);
+                            }
+                            acc[r] = sem.apply(acc[r], xv, wv);
+                            ++s;
+                            ++qb;
+                        }
+                    }
+                }
+                open = true;
+                if (t + 1 == next) {  // tile-row `row` ends with tile t
+                    if (!has_end) {
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) F[v] = acc[v];
+                        has_end = true;
+                    } else {
+                        sem.store(row, acc);
+                    }
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) acc[v] = sem.ident();
+                    open = false;
+                    if (i + 1 < cnt) {
+                        int32_t R = row + 1;
+                        while ((int64_t)__ldg(g.rowptr + R + 1) == next) { sem.store(R, idv); ++R; }
+                        row = R;
+                        next = __ldg(g.rowptr + row + 1);
+                    }
                 }
             }
         }
@@ -433,7 +523,7 @@ __device__ __forceinline__ void process_chunk(const uint8_t* buf, const SpmvGeom
     for (int v = 0; v < NV; ++v) inc[v] = acc[v];
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        bool o_r = __shfl_up_sync(0xffffffffu, inc_r, d);
+        const bool o_r = __shfl_up_sync(0xffffffffu, inc_r, d);
         const bool take = lane >= d && !inc_r;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -442,75 +532,38 @@ __device__ __forceinline__ void process_chunk(const uint8_t* buf, const SpmvGeom
         }
         if (take) inc_r = o_r;
     }
-    // exclusive value entering this lane
     bool ex_r = __shfl_up_sync(0xffffffffu, inc_r, 1);
-    V ex[NV];
+    if (lane == 0) ex_r = false;
+    // the value carried into this lane joins its first segment (every lane
+    // takes part in the shuffles; only lanes that close a row use them)
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        V o = __shfl_up_sync(0xffffffffu, inc[v], 1);
-        ex[v] = lane == 0 ? sem.ident() : o;
+        const V o = __shfl_up_sync(0xffffffffu, inc[v], 1);
+        if (has_end && lane > 0) F[v] = sem.comb(o, F[v]);
     }
-    if (lane == 0) ex_r = false;
-
     if (has_end) {
-        // this lane closes the segment of its first row
-#pragma unroll
-        for (int v = 0; v < NV; ++v) F[v] = sem.comb(ex[v], F[v]);
-        const bool started = ex_r || head_cs;
-        if (started) {
+        // this lane closes the tile-row of its first tile
+        if (ex_r || head_cs) {
             sem.store(first_row, F);
         } else {
-            part.row_first[c] = first_row;
 #pragma unroll
             for (int v = 0; v < NV; ++v) part.val_first[c * NV + v] = F[v];
         }
     }
 
     // chunk tail: the segment still open after the last active lane
-    const int la = (int)((ce - 1 - cs) / S::P);
+    const int la = (int)((ce - 1 - cs) / P);
     const bool tail_open = __shfl_sync(0xffffffffu, open, la);
-    const int32_t tail_row = __shfl_sync(0xffffffffu, row, la);
     const bool tail_r = __shfl_sync(0xffffffffu, inc_r, 31);
-    V tail[NV];
+    if (lane == 31 && tail_open) {
+        if (tail_r || head_cs) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) tail[v] = __shfl_sync(0xffffffffu, inc[v], 31);
-    if (lane == 0 && tail_open) {
-        const bool started = tail_r || head_cs;
-        if (started) {
-            part.row_last[c] = tail_row;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) part.val_last[c * NV + v] = tail[v];
+            for (int v = 0; v < NV; ++v) part.val_last[c * NV + v] = inc[v];
         } else {
-            part.row_first[c] = tail_row;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) part.val_first[c * NV + v] = tail[v];
+            for (int v = 0; v < NV; ++v) part.val_first[c * NV + v] = inc[v];
         }
     }
-}
-
-template <int K, class SEM>
-__global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, SEM sem,
-                                                                   Partials<typename SEM::V> part) {
-    using S = ChunkShape<K>;
-    extern __shared__ __align__(16) uint8_t smem[];
-    const int warp = threadIdx.x >> 5;
-    uint8_t* wsm = smem + warp * 2 * S::STAGE;
-    const int64_t nw = (int64_t)gridDim.x * kSpmvWarps;
-    int64_t c = (int64_t)blockIdx.x * kSpmvWarps + warp;
-    int stage = 0;
-    if (c < g.nchunks) issue_chunk<K>(wsm, g, c);
-    cp_async_commit();
-    for (; c < g.nchunks; c += nw) {
-        const int64_t cn = c + nw;
-        if (cn < g.nchunks) issue_chunk<K>(wsm + (stage ^ 1) * S::STAGE, g, cn);
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncwarp();
-        process_chunk<K, SEM>(wsm + stage * S::STAGE, g, c, sem, part);
-        __syncwarp();
-        stage ^= 1;
-    }
-    cp_async_wait<0>();
 }
 
 // Rows that span chunks: the chunk where such a row ends joins the partials
@@ -605,18 +658,11 @@ static b2sr_status launch_edges(const b2sr_matrix* h, const SEM& sem, cudaStream
 template <int K, class SEM>
 static b2sr_status launch_chunks(const b2sr_matrix* h, const SpmvGeom& g, const SEM& sem,
                                  Partials<typename SEM::V> part, cudaStream_t s) {
-    using S = ChunkShape<K>;
-    const int smem = kSpmvWarps * 2 * S::STAGE;
-    static int per_sm = 0;  // one cache per (K, SEM) instantiation
-    B2SR_CUDA_TRY(cudaFuncSetAttribute(spmv_chunks_kernel<K, SEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    if (per_sm == 0) {
-        int v = 0;
-        B2SR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, spmv_chunks_kernel<K, SEM>, kSpmvThreads, smem));
-        per_sm = std::max(v, 1);
-    }
-    int64_t want = ceil_div(h->nchunks, kSpmvWarps);
-    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * per_sm));
-    spmv_chunks_kernel<K, SEM><<<grid, kSpmvThreads, smem, s>>>(g, sem, part);
+    const int smem = kSpmvWarps * SmemPerWarp<SEM>::bytes;
+    if (smem > 48 * 1024)
+        B2SR_CUDA_TRY(cudaFuncSetAttribute(spmv_chunks_kernel<K, SEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int64_t blocks = ceil_div(h->nchunks, kSpmvWarps);
+    spmv_chunks_kernel<K, SEM><<<(unsigned)blocks, kSpmvThreads, smem, s>>>(g, sem, part);
     B2SR_LAUNCH_CHECK("spmv_chunks_kernel");
     return B2SR_OK;
 }
@@ -624,13 +670,10 @@ static b2sr_status launch_chunks(const b2sr_matrix* h, const SpmvGeom& g, const 
 template <class V, int NV>
 static b2sr_status alloc_partials(DevBuf& pbuf, int64_t nchunks, Partials<V>* part) {
     const size_t vbytes = round_up((size_t)nchunks * NV * sizeof(V), 16);
-    const size_t rbytes = round_up((size_t)nchunks * sizeof(int32_t), 16);
-    B2SR_TRY(pbuf.alloc(2 * rbytes + 2 * vbytes));
+    B2SR_TRY(pbuf.alloc(2 * vbytes));
     uint8_t* base = pbuf.as<uint8_t>();
-    part->row_first = reinterpret_cast<int32_t*>(base);
-    part->row_last = reinterpret_cast<int32_t*>(base + rbytes);
-    part->val_first = reinterpret_cast<V*>(base + 2 * rbytes);
-    part->val_last = reinterpret_cast<V*>(base + 2 * rbytes + vbytes);
+    part->val_first = reinterpret_cast<V*>(base);
+    part->val_last = reinterpret_cast<V*>(base + vbytes);
     return B2SR_OK;
 }
 
@@ -713,7 +756,7 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
         return with_k(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
             SemMinPlus<K> sem{static_cast<const float*>(x), static_cast<float*>(y), mask, comp, h->n, weights,
-                              h->voff};
+                              h->voff, weights != nullptr};
             return run_spmv<K>(h, sem, nullptr, s);
         });
     }

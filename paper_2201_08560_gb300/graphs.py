@@ -61,8 +61,12 @@ def from_edges(n: int, src: np.ndarray, dst: np.ndarray, *, symmetric: bool = Tr
     if drop_self_loops:
         keep = src != dst
         src, dst = src[keep], dst[keep]
-    key = src * np.int64(n) + dst
-    key = np.unique(key) if dedup else np.sort(key, kind="stable")
+    key = np.sort(src * np.int64(n) + dst)
+    if dedup and key.size:
+        first = np.empty(key.size, dtype=bool)
+        first[0] = True
+        np.not_equal(key[1:], key[:-1], out=first[1:])
+        key = key[first]
     rows = (key // n).astype(np.int64)
     cols = (key % n).astype(np.int32)
     counts = np.bincount(rows, minlength=n)
@@ -269,12 +273,20 @@ def symmetric_weights(g: CSR, seed: int, lo: float = 1.0, hi: float = 100.0,
     lo_id = np.minimum(rows, cols)
     hi_id = np.maximum(rows, cols)
     key = lo_id * np.int64(g.n) + hi_id
-    uniq, inv = np.unique(key, return_inverse=True)
+    order = np.argsort(key, kind="stable")
+    sk = key[order]
+    first = np.ones(sk.size, dtype=bool)
+    if sk.size:
+        np.not_equal(sk[1:], sk[:-1], out=first[1:])
+    group = np.cumsum(first) - 1          # undirected edge id of each sorted entry
+    nuniq = int(first.sum())
     if grid is None:
-        w = rng.uniform(lo, hi, size=uniq.size).astype(np.float32)
+        w = rng.uniform(lo, hi, size=nuniq).astype(np.float32)
     else:
         steps = int(round((hi - lo) * grid))
-        w = (lo + rng.integers(0, steps, size=uniq.size) / grid).astype(np.float32)
+        w = (lo + rng.integers(0, steps, size=nuniq) / grid).astype(np.float32)
+    inv = np.empty(key.size, dtype=np.int64)
+    inv[order] = group
     return w[inv].astype(np.float32)
 
 
