@@ -28,6 +28,11 @@
  *  - Vertex ids are int32; n < 2^31; nnz < 2^31.
  *  - Bitsets are LSB-first uint32 words: vertex v is bit v%32 of word v/32.
  *    A bitset over n vertices has ceil(n/32) words; output bits >= n are 0.
+ *  - Orientation: entry (i, j) of A is an edge from vertex j to vertex i,
+ *    the direction in which y = A x moves values (Sec. V multiplies PageRank
+ *    by the column-stochastic A, so column j holds the out-edges of j).  BFS
+ *    and SSSP follow edges that way.  For symmetric matrices (undirected
+ *    graphs) both orientations coincide.
  *
  * B2SR layout (Sec. III-A, III-B and Table 1)
  * -------------------------------------------

@@ -373,28 +373,64 @@ int64_t orc_spgemm_bool(int32_t n, const int32_t* a_rowptr, const int32_t* a_col
 /* Graph algorithms (Sec. V)                                                  */
 /* ------------------------------------------------------------------------ */
 
-/* BFS levels by a FIFO queue: level 0 at src, -1 where unreachable. */
+/* Orientation: entry (i, j) of A is an edge from j to i, the direction in
+ * which y = A x moves values (Sec. V PR multiplies by the column-stochastic A,
+ * so column j holds the out-edges of j).  BFS and SSSP follow edges that way;
+ * for symmetric matrices either orientation gives the same result.  The
+ * out-edges of every vertex are the transpose of the CSR, built here. */
+static int transpose_csr(int32_t n, const int32_t* rowptr, const int32_t* colind, const float* w,
+                         int32_t** out_ptr, int32_t** out_ind, float** out_w) {
+    int64_t nnz = rowptr[n];
+    int32_t* tp = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
+    int32_t* ti = (int32_t*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+    float* tw = w ? (float*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(float)) : NULL;
+    int32_t* fill = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!tp || !ti || (w && !tw) || !fill) { free(tp); free(ti); free(tw); free(fill); return ORC_ENOMEM; }
+    for (int64_t e = 0; e < nnz; ++e) tp[colind[e] + 1] += 1;
+    for (int32_t j = 0; j < n; ++j) tp[j + 1] += tp[j];
+    for (int32_t j = 0; j < n; ++j) fill[j] = tp[j];
+    for (int32_t i = 0; i < n; ++i)
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            int32_t j = colind[e];
+            int32_t at = fill[j]++;
+            ti[at] = i;
+            if (tw) tw[at] = w[e];
+        }
+    free(fill);
+    *out_ptr = tp;
+    *out_ind = ti;
+    if (out_w) *out_w = tw;
+    return ORC_OK;
+}
+
+/* BFS levels by a FIFO queue over the edges j -> i of the entries A_ij:
+ * level 0 at src, -1 where unreachable. */
 int orc_bfs(int32_t n, const int32_t* rowptr, const int32_t* colind, int32_t src, int32_t* levels) {
     if (src < 0 || src >= n) return ORC_EINVAL;
+    int32_t *op = NULL, *oi = NULL;
+    if (transpose_csr(n, rowptr, colind, NULL, &op, &oi, NULL) != ORC_OK) return ORC_ENOMEM;
     int32_t* queue = (int32_t*)malloc((size_t)n * sizeof(int32_t));
-    if (!queue) return ORC_ENOMEM;
+    if (!queue) { free(op); free(oi); return ORC_ENOMEM; }
     for (int64_t v = 0; v < n; ++v) levels[v] = -1;
     int64_t head = 0, tail = 0;
     levels[src] = 0;
     queue[tail++] = src;
     while (head < tail) {
         int32_t u = queue[head++];
-        for (int64_t e = rowptr[u]; e < rowptr[u + 1]; ++e) {
-            int32_t v = colind[e];
+        for (int64_t e = op[u]; e < op[u + 1]; ++e) {
+            int32_t v = oi[e];
             if (levels[v] < 0) { levels[v] = levels[u] + 1; queue[tail++] = v; }
         }
     }
     free(queue);
+    free(op);
+    free(oi);
     return ORC_OK;
 }
 
 /* Single-source shortest paths by Dijkstra with a binary heap, in fp64 over
- * fp32 weights (w == NULL: unit weights).  Unreachable vertices get +inf.
+ * fp32 weights, following the edges j -> i of the entries A_ij with weight
+ * w_ij (w in CSR order; NULL: unit weights).  Unreachable vertices get +inf.
  * Any SSSP method (delta-stepping, Bellman-Ford) reaches these distances. */
 typedef struct { double d; int32_t v; } heap_item;
 
@@ -427,10 +463,13 @@ static heap_item heap_pop(heap_item* h, int64_t* size) {
 int orc_sssp(int32_t n, const int32_t* rowptr, const int32_t* colind, const float* w, int32_t src,
              double* dist) {
     if (src < 0 || src >= n) return ORC_EINVAL;
+    int32_t *op = NULL, *oi = NULL;
+    float* ow = NULL;
+    if (transpose_csr(n, rowptr, colind, w, &op, &oi, w ? &ow : NULL) != ORC_OK) return ORC_ENOMEM;
     int64_t cap = (int64_t)rowptr[n] + 1;
     heap_item* heap = (heap_item*)malloc((size_t)cap * sizeof(heap_item));
     uint8_t* done = (uint8_t*)calloc((size_t)n, 1);
-    if (!heap || !done) { free(heap); free(done); return ORC_ENOMEM; }
+    if (!heap || !done) { free(heap); free(done); free(op); free(oi); free(ow); return ORC_ENOMEM; }
     for (int64_t v = 0; v < n; ++v) dist[v] = INFINITY;
     int64_t size = 0;
     dist[src] = 0.0;
@@ -440,9 +479,9 @@ int orc_sssp(int32_t n, const int32_t* rowptr, const int32_t* colind, const floa
         heap_item it = heap_pop(heap, &size);
         if (done[it.v]) continue;
         done[it.v] = 1;
-        for (int64_t e = rowptr[it.v]; e < rowptr[it.v + 1]; ++e) {
-            int32_t v = colind[e];
-            double nd = it.d + (w ? (double)w[e] : 1.0);
+        for (int64_t e = op[it.v]; e < op[it.v + 1]; ++e) {
+            int32_t v = oi[e];
+            double nd = it.d + (ow ? (double)ow[e] : 1.0);
             if (nd < dist[v]) {
                 dist[v] = nd;
                 heap_item ni = {nd, v};
@@ -452,6 +491,9 @@ int orc_sssp(int32_t n, const int32_t* rowptr, const int32_t* colind, const floa
     }
     free(heap);
     free(done);
+    free(op);
+    free(oi);
+    free(ow);
     return ORC_OK;
 }
 

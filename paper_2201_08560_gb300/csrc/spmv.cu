@@ -1,25 +1,28 @@
 // B2SR SpMV: the BMV schemes of Table 2 over the semirings of Table 4, and the
 // 64-lane Boolean SpMM used by multi-source BFS.
 //
-// Design (GB300): the paper maps one tile-row to one warp (Listing 1) or 32
+// Design (GB300).  The paper maps one tile-row to one warp (Listing 1) or 32
 // tile-rows to a 1024-thread block (Sec. IV, bmv_bin_full_full).  Power-law
-// graphs make that row mapping badly imbalanced (a scale-20 R-MAT tile-row
-// can hold 10^4 tiles), so here the unit of work is a fixed-size chunk of
-// consecutive tiles instead:
-//   * a warp owns a chunk of 32*P tiles (P tiles per lane); persistent warps
-//     stream chunks, double-buffering them into shared memory with 16-byte
-//     cp.async copies, so the tile stream is read once, fully coalesced;
-//   * each lane walks its P tiles in order, accumulating the k row results
-//     of the current tile-row and storing every row that starts and ends
-//     inside the lane;
-//   * rows that cross lanes are joined with a warp-level segmented scan
-//     (shuffles, fixed order); rows that cross chunks leave per-chunk partials
-//     that a second small kernel joins in chunk order.
+// graphs make any row mapping badly imbalanced (a scale-20 R-MAT tile-row can
+// hold 10^5 tiles), so the unit of work here is a fixed-size chunk of
+// consecutive tiles:
+//   * one warp per chunk of 32*P tiles; lane l owns P consecutive tiles and
+//     issues every load it needs up front (its tiles and tile columns as
+//     16-byte vectors, then the input segments or, for full-precision
+//     vectors, one 4/8-byte cp.async gather per set bit into shared memory),
+//     so each warp keeps several KB in flight;
+//   * the lane walks its tiles in order, accumulating the k row results of
+//     the current tile-row and storing every row that starts and ends inside
+//     the lane (and the identity for empty tile-rows it passes);
+//   * rows that cross lanes are joined with a warp segmented scan (shuffles,
+//     fixed order); rows that cross chunks leave per-chunk partials that a
+//     second kernel joins, one warp per row, in a fixed order.
 // Every reduction order is fixed by the data, so floating-point results are
-// bitwise reproducible and independent of the grid size or stream.
+// bitwise reproducible and independent of launch geometry and stream.
 #include <algorithm>
 #include <cfloat>
 #include <climits>
+#include <type_traits>
 
 #include "b2sr_internal.cuh"
 
@@ -36,7 +39,8 @@ struct ChunkShape {
     static constexpr int CT = 32 * P;
     static constexpr int TB = K * (K <= 8 ? 1 : (K == 16 ? 2 : 4));
     static constexpr int TW = TB / 4;
-    static constexpr int TILE_V4 = P * TB / 16;   // uint4 loads per lane for its tiles
+    static constexpr int TILE_V4 = P * TB / 16;  // uint4 loads per lane for its tiles
+    static constexpr int ROW_BITS = K <= 8 ? 8 : K;  // bits per row slot in a word
 };
 
 template <int K>
@@ -87,19 +91,38 @@ __device__ __forceinline__ bool mask_allows(const uint32_t* __restrict__ mask, i
 }
 
 // ---------------------------------------------------------------------------
+// accumulator storage: registers (static row index) or shared memory (one
+// column per lane, any row index)
+// ---------------------------------------------------------------------------
+template <class V, int NV>
+struct RegAcc {
+    V a[NV];
+    __device__ __forceinline__ V get(int v) const { return a[v]; }
+    __device__ __forceinline__ void set(int v, V x) { a[v] = x; }
+};
+
+template <class V, int NV>
+struct SmemAcc {
+    V* p;  // element v at p[v * 32]
+    __device__ __forceinline__ V get(int v) const { return p[v * 32]; }
+    __device__ __forceinline__ void set(int v, V x) { p[v * 32] = x; }
+};
+
+// ---------------------------------------------------------------------------
 // semirings.  Each provides V (accumulator value), NV (values per tile-row
-// accumulator), ident(), comb(a, b) (a earlier in the fixed order) and
-// store(R, acc), which applies the self term, the mask and the overwrite
-// rule (empty tile-rows are stored with the identity accumulator).
+// accumulator), ident(), comb(a, b) (a earlier in the fixed order),
+// store(R, acc) (self term, mask, overwrite; empty tile-rows are stored with
+// the identity) and a join type J for the cross-chunk join.
 //   bit-vector schemes (kGather = false): xseg(J) and tile(acc, words, xs);
-//   value schemes (kGather = true): one gathered input value per set bit,
-//     src() (the values), weighted and apply(acc, x_j, w_ij).
+//   value schemes (kGather = true): one gathered input per set bit, src(),
+//     weighted, wts(), voffs() and apply(acc, x_j, w_ij).
 // ---------------------------------------------------------------------------
 
 // bmv_bin_bin_bin[_masked]: bitset in, bitset out, acc = k-bit row mask
 template <int K>
 struct SemBool {
     using V = uint32_t;
+    using J = uint32_t;
     static constexpr int NV = 1;
     static constexpr bool kGather = false;
     const uint32_t* x;
@@ -109,10 +132,15 @@ struct SemBool {
     int32_t n;
     __device__ V ident() const { return 0u; }
     __device__ V comb(V a, V b) const { return a | b; }
-    __device__ uint32_t xseg(int32_t J) const { return ld_bits(x, (int64_t)J * K, K); }
-    __device__ void tile(V (&acc)[NV], const uint32_t* w, uint32_t xs) const { acc[0] |= rows_hit<K>(w, xs); }
-    __device__ void store(int32_t R, const V (&acc)[NV]) const {
-        uint32_t v = acc[0];
+    __device__ J jcomb(J a, J b) const { return a | b; }
+    __device__ uint32_t xseg(int32_t Jc) const { return ld_bits(x, (int64_t)Jc * K, K); }
+    template <class A>
+    __device__ void tile(A& acc, const uint32_t* w, uint32_t xs) const {
+        acc.set(0, acc.get(0) | rows_hit<K>(w, xs));
+    }
+    template <class A>
+    __device__ void store(int32_t R, const A& acc) const {
+        uint32_t v = acc.get(0);
         if (mask) {
             uint32_t mb = ld_bits(mask, (int64_t)R * K, K);
             v &= comp ? ~mb : mb;
@@ -136,6 +164,7 @@ struct SemBool {
 template <int K>
 struct SemCount {
     using V = int32_t;
+    using J = int32_t;
     static constexpr int NV = K;
     static constexpr bool kGather = false;
     const uint32_t* x;
@@ -145,44 +174,51 @@ struct SemCount {
     int32_t n;
     __device__ V ident() const { return 0; }
     __device__ V comb(V a, V b) const { return a + b; }
-    __device__ uint32_t xseg(int32_t J) const { return ld_bits(x, (int64_t)J * K, K); }
-    __device__ void tile(V (&acc)[NV], const uint32_t* w, uint32_t xs) const {
+    __device__ J jcomb(J a, J b) const { return a + b; }
+    __device__ uint32_t xseg(int32_t Jc) const { return ld_bits(x, (int64_t)Jc * K, K); }
+    template <class A>
+    __device__ void tile(A& acc, const uint32_t* w, uint32_t xs) const {
 #pragma unroll
-        for (int r = 0; r < K; ++r) acc[r] += __popc(row_word<K>(w, r) & xs);
+        for (int r = 0; r < K; ++r) acc.set(r, acc.get(r) + __popc(row_word<K>(w, r) & xs));
     }
-    __device__ void store(int32_t R, const V (&acc)[NV]) const {
+    template <class A>
+    __device__ void store(int32_t R, const A& acc) const {
 #pragma unroll
         for (int r = 0; r < K; ++r) {
             int64_t i = (int64_t)R * K + r;
-            if (i < n) y[i] = mask_allows(mask, comp, i) ? acc[r] : 0;
+            if (i < n) y[i] = mask_allows(mask, comp, i) ? acc.get(r) : 0;
         }
     }
 };
 
-// bmv_bin_full_full over plus-times: float in, float out
+// bmv_bin_full_full over plus-times: float in, float out; partials of rows
+// that cross chunks are joined in fp64
 template <int K>
 struct SemPlus {
     using V = float;
     using G = float;
+    using J = double;
     static constexpr int NV = K;
     static constexpr bool kGather = true;
+    static constexpr bool weighted = false;
     const float* x;
     float* y;
     const uint32_t* mask;
     int comp;
     int32_t n;
-    static constexpr bool weighted = false;
     __device__ const float* src() const { return x; }
     __device__ const float* wts() const { return nullptr; }
     __device__ const int32_t* voffs() const { return nullptr; }
     __device__ V ident() const { return 0.0f; }
     __device__ V comb(V a, V b) const { return a + b; }
+    __device__ J jcomb(J a, J b) const { return a + b; }
     __device__ V apply(V acc, G xv, float) const { return acc + xv; }
-    __device__ void store(int32_t R, const V (&acc)[NV]) const {
+    template <class A>
+    __device__ void store(int32_t R, const A& acc) const {
 #pragma unroll
         for (int r = 0; r < K; ++r) {
             int64_t i = (int64_t)R * K + r;
-            if (i < n) y[i] = mask_allows(mask, comp, i) ? acc[r] : 0.0f;
+            if (i < n) y[i] = mask_allows(mask, comp, i) ? (float)acc.get(r) : 0.0f;
         }
     }
 };
@@ -193,6 +229,7 @@ template <int K>
 struct SemMinPlus {
     using V = float;
     using G = float;
+    using J = float;
     static constexpr int NV = K;
     static constexpr bool kGather = true;
     const float* x;
@@ -208,12 +245,14 @@ struct SemMinPlus {
     __device__ const int32_t* voffs() const { return voff; }
     __device__ V ident() const { return INFINITY; }
     __device__ V comb(V a, V b) const { return fminf(a, b); }
+    __device__ J jcomb(J a, J b) const { return fminf(a, b); }
     __device__ V apply(V acc, G xv, float wv) const { return fminf(acc, xv + wv); }
-    __device__ void store(int32_t R, const V (&acc)[NV]) const {
+    template <class A>
+    __device__ void store(int32_t R, const A& acc) const {
 #pragma unroll
         for (int r = 0; r < K; ++r) {
             int64_t i = (int64_t)R * K + r;
-            if (i < n) y[i] = mask_allows(mask, comp, i) ? fminf(__ldg(x + i), acc[r]) : INFINITY;
+            if (i < n) y[i] = mask_allows(mask, comp, i) ? fminf(__ldg(x + i), (float)acc.get(r)) : INFINITY;
         }
     }
 };
@@ -223,25 +262,28 @@ template <int K>
 struct SemMinI32 {
     using V = int32_t;
     using G = int32_t;
+    using J = int32_t;
     static constexpr int NV = K;
     static constexpr bool kGather = true;
+    static constexpr bool weighted = false;
     const int32_t* x;
     int32_t* y;
     const uint32_t* mask;
     int comp;
     int32_t n;
-    static constexpr bool weighted = false;
     __device__ const int32_t* src() const { return x; }
     __device__ const float* wts() const { return nullptr; }
     __device__ const int32_t* voffs() const { return nullptr; }
     __device__ V ident() const { return INT_MAX; }
     __device__ V comb(V a, V b) const { return min(a, b); }
+    __device__ J jcomb(J a, J b) const { return min(a, b); }
     __device__ V apply(V acc, G xv, float) const { return min(acc, xv); }
-    __device__ void store(int32_t R, const V (&acc)[NV]) const {
+    template <class A>
+    __device__ void store(int32_t R, const A& acc) const {
 #pragma unroll
         for (int r = 0; r < K; ++r) {
             int64_t i = (int64_t)R * K + r;
-            if (i < n) y[i] = mask_allows(mask, comp, i) ? min(__ldg(x + i), acc[r]) : INT_MAX;
+            if (i < n) y[i] = mask_allows(mask, comp, i) ? min(__ldg(x + i), (int32_t)acc.get(r)) : INT_MAX;
         }
     }
 };
@@ -251,26 +293,29 @@ template <int K>
 struct SemOr64 {
     using V = unsigned long long;
     using G = unsigned long long;
+    using J = unsigned long long;
     static constexpr int NV = K;
     static constexpr bool kGather = true;
+    static constexpr bool weighted = false;
     const unsigned long long* x;
     unsigned long long* y;
     const unsigned long long* mask;
     int comp;
     int32_t n;
-    static constexpr bool weighted = false;
     __device__ const unsigned long long* src() const { return x; }
     __device__ const float* wts() const { return nullptr; }
     __device__ const int32_t* voffs() const { return nullptr; }
     __device__ V ident() const { return 0ull; }
     __device__ V comb(V a, V b) const { return a | b; }
+    __device__ J jcomb(J a, J b) const { return a | b; }
     __device__ V apply(V acc, G xv, float) const { return acc | xv; }
-    __device__ void store(int32_t R, const V (&acc)[NV]) const {
+    template <class A>
+    __device__ void store(int32_t R, const A& acc) const {
 #pragma unroll
         for (int r = 0; r < K; ++r) {
             int64_t i = (int64_t)R * K + r;
             if (i < n) {
-                V v = acc[r];
+                V v = acc.get(r);
                 if (mask) v &= comp ? ~__ldg(mask + i) : __ldg(mask + i);
                 y[i] = v;
             }
@@ -279,7 +324,7 @@ struct SemOr64 {
 };
 
 // ---------------------------------------------------------------------------
-// kernel arguments
+// kernel arguments and shared-memory layout
 // ---------------------------------------------------------------------------
 struct SpmvGeom {
     const int32_t* rowptr;
@@ -307,24 +352,30 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 constexpr int kSpmvThreads = 256;
 constexpr int kSpmvWarps = kSpmvThreads / 32;
-// gathered values staged per warp (set bits of one chunk); the rest are read directly
-template <class G>
-struct GatherSlots {
-    static constexpr int N = sizeof(G) == 8 ? 512 : 1024;
-};
 
+// Shared memory per warp for the gather schemes: NG staged input values
+// (+ NG weights), then the lane accumulators and first-row values
+// (NV x 32 each).  Set bits past NG in one chunk are read directly.
 template <class SEM, bool GATHER = SEM::kGather>
-struct SmemPerWarp {
+struct GatherLayout {
+    static constexpr int NG = 0;
     static constexpr int bytes = 0;
 };
 template <class SEM>
-struct SmemPerWarp<SEM, true> {
+struct GatherLayout<SEM, true> {
     using G = typename SEM::G;
-    static constexpr int bytes = GatherSlots<G>::N * (int)sizeof(G) + GatherSlots<G>::N * 4;
+    using V = typename SEM::V;
+    static constexpr int NG = sizeof(G) == 8 ? 512 : 1024;
+    static constexpr int x_off = 0;
+    static constexpr int w_off = NG * (int)sizeof(G);
+    static constexpr int acc_off = w_off + NG * 4;
+    static constexpr int f_off = acc_off + SEM::NV * 32 * (int)sizeof(V);
+    static constexpr int bytes = f_off + SEM::NV * 32 * (int)sizeof(V);
 };
 
-// One warp per chunk of 32*P consecutive tiles; lane l owns tiles
-// [cs + l*P, cs + l*P + P).
+// ---------------------------------------------------------------------------
+// the chunk kernel
+// ---------------------------------------------------------------------------
 template <int K, class SEM>
 __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, SEM sem,
                                                                    Partials<typename SEM::V> part) {
@@ -332,18 +383,19 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
     using V = typename SEM::V;
     constexpr int NV = SEM::NV;
     constexpr int P = S::P;
+    constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(16) uint8_t smem[];
     const int warp = threadIdx.x >> 5;
     const int lane = (int)lane_id();
     const int64_t c = (int64_t)blockIdx.x * kSpmvWarps + warp;
-    if (c >= g.nchunks) return;
+    if (c >= g.nchunks) return;  // whole warps leave together
 
     const int64_t cs = c * S::CT;
     const int64_t ce = min(cs + (int64_t)S::CT, g.T);
     const int64_t tl = cs + (int64_t)lane * P;
     const int cnt = (int)max((int64_t)0, min((int64_t)P, ce - tl));
 
-    // ---- issue every load of the lane first: tiles, tile columns ----
+    // ---- every load of the lane first: tiles, tile columns, chunk rows ----
     uint4 tv[S::TILE_V4];
     {
         const uint4* src = reinterpret_cast<const uint4*>(g.tiles + tl * S::TB);
@@ -352,7 +404,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
     }
     const uint32_t* words = reinterpret_cast<const uint32_t*>(tv);
     int32_t col[P];
-    if (P % 4 == 0) {
+    if constexpr (P % 4 == 0) {
         const int4* src = reinterpret_cast<const int4*>(g.colind + tl);
 #pragma unroll
         for (int q = 0; q < P / 4; ++q) {
@@ -369,8 +421,11 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
     }
     const int32_t r0 = __ldg(g.chunk_row + c);
     const int32_t r1 = __ldg(g.chunk_row + c + 1);
+    const int32_t span = r1 - r0;
+    // window of row pointers: lane j holds rowptr[r0 + j] for j <= span + 1
+    const int64_t win = lane <= span + 1 ? (int64_t)__ldg(g.rowptr + r0 + lane) : INT64_MAX;
 
-    // ---- input values: one k-bit segment per tile, or one value per set bit ----
+    // ---- input: one k-bit segment per tile, or one value per set bit ----
     uint32_t xs[SEM::kGather ? 1 : P];
     int gbase = 0;
     if constexpr (!SEM::kGather) {
@@ -378,9 +433,10 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
         for (int i = 0; i < P; ++i) xs[i] = sem.xseg(col[i]);
     } else {
         using G = typename SEM::G;
-        constexpr int NG = GatherSlots<G>::N;
-        G* sx = reinterpret_cast<G*>(smem + warp * SmemPerWarp<SEM>::bytes);
-        float* sw = reinterpret_cast<float*>(sx + NG);
+        using L = GatherLayout<SEM>;
+        uint8_t* wsm = smem + warp * L::bytes;
+        G* sx = reinterpret_cast<G*>(wsm + L::x_off);
+        float* sw = reinterpret_cast<float*>(wsm + L::w_off);
         int nb = 0;
 #pragma unroll
         for (int i = 0; i < P; ++i)
@@ -391,7 +447,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
         int incl = nb;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            int o = __shfl_up_sync(0xffffffffu, incl, d);
+            int o = __shfl_up_sync(FULL, incl, d);
             if (lane >= d) incl += o;
         }
         gbase = incl - nb;
@@ -399,16 +455,17 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
         const G* xsrc = sem.src();
 #pragma unroll
         for (int i = 0; i < P; ++i) {
-            if (i < cnt && s < NG) {
+            if (i < cnt && s < L::NG) {
                 const G* xt = xsrc + (int64_t)col[i] * K;
                 const float* wt = sem.weighted ? sem.wts() + __ldg(sem.voffs() + tl + i) : nullptr;
                 int qb = 0;
 #pragma unroll
-                for (int r = 0; r < K; ++r) {
-                    uint32_t b = row_word<K>(words + i * S::TW, r);
-                    while (b && s < NG) {
-                        const int cc = __ffs(b) - 1;
+                for (int q = 0; q < S::TW; ++q) {
+                    uint32_t b = words[i * S::TW + q];
+                    while (b && s < L::NG) {
+                        const int bit = __ffs(b) - 1;
                         b &= b - 1;
+                        const int cc = bit % S::ROW_BITS;
                         cp_async_gather<sizeof(G)>(sx + s, xt + cc);
                         if (sem.weighted) cp_async_gather<4>(sw + s, wt + qb);
                         ++s;
@@ -418,44 +475,76 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
             }
         }
         cp_async_commit();
+    }
+
+    // ---- tile-row of the lane's first tile: count row starts <= tl ----
+    const bool head_cs = __shfl_sync(FULL, win, 0) == cs;
+    int32_t row = r0;
+    if (span > 0) {
+        // first window: the row starts are lanes 1..31 (lane 0 is rowptr[r0])
+        const int64_t b = lane == 0 ? INT64_MIN : win;
+        int pos = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int64_t v = __shfl_sync(FULL, b, pos + step - 1);
+            if (v <= tl) pos += step;
+        }
+        pos += (__shfl_sync(FULL, b, pos) <= tl) ? 1 : 0;
+        int32_t add = pos - 1;  // lane 0 is always counted
+        int64_t last = __shfl_sync(FULL, win, 31);
+        for (int32_t base = 32; base <= span && last < ce; base += 32) {
+            // further windows (rare: many tile-rows in one chunk)
+            const int32_t j = base + lane;
+            const int64_t bb = j <= span ? (int64_t)__ldg(g.rowptr + r0 + j) : INT64_MAX;
+            int p2 = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int64_t v = __shfl_sync(FULL, bb, p2 + step - 1);
+                if (v <= tl) p2 += step;
+            }
+            p2 += (__shfl_sync(FULL, bb, p2) <= tl) ? 1 : 0;
+            add += p2;
+            last = __shfl_sync(FULL, bb, 31);
+        }
+        row = r0 + add;
+    }
+    // rowptr[row] and rowptr[row + 1], from the first window when it holds them
+    int64_t row_start, next;
+    {
+        const int d = row - r0;
+        const int64_t a0 = __shfl_sync(FULL, win, d < 32 ? d : 0);
+        const int64_t a1 = __shfl_sync(FULL, win, d + 1 < 32 ? d + 1 : 0);
+        row_start = d < 32 ? a0 : (int64_t)__ldg(g.rowptr + row);
+        next = d + 1 < 32 ? a1 : (int64_t)__ldg(g.rowptr + row + 1);
+    }
+
+    // ---- accumulators ----
+    using Acc = typename std::conditional<SEM::kGather, SmemAcc<V, NV>, RegAcc<V, NV>>::type;
+    Acc acc, F;
+    if constexpr (SEM::kGather) {
+        using L = GatherLayout<SEM>;
+        uint8_t* wsm = smem + warp * L::bytes;
+        acc.p = reinterpret_cast<V*>(wsm + L::acc_off) + lane;
+        F.p = reinterpret_cast<V*>(wsm + L::f_off) + lane;
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { acc.set(v, sem.ident()); F.set(v, sem.ident()); }
+    RegAcc<V, NV> idv;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) idv.set(v, sem.ident());
+
+    if constexpr (SEM::kGather) {
         cp_async_wait_all();
         __syncwarp();
     }
 
-    // ---- tile-row of the lane's first tile: rows r0..r1 span the chunk ----
-    int32_t row = r0;
-    if (r1 > r0) {
-        const int32_t span = r1 - r0;
-        int32_t add = 0;
-        for (int32_t base = 0; base < span; base += 32) {
-            const int32_t j = base + lane;
-            const int64_t b = j < span ? (int64_t)__ldg(g.rowptr + r0 + 1 + j) : INT64_MAX;
-            // count of boundaries b_j <= tl (b is sorted across lanes)
-            int pos = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                int64_t v = __shfl_sync(0xffffffffu, b, pos + step - 1);
-                if (v <= tl) pos += step;
-            }
-            pos += (__shfl_sync(0xffffffffu, b, pos) <= tl) ? 1 : 0;
-            add += pos;
-            if (__shfl_sync(0xffffffffu, b, 31) > cs + 32 * P) break;  // later windows start past the chunk
-        }
-        row = r0 + add;
-    }
-
-    const bool head_cs = (int64_t)__ldg(g.rowptr + r0) == cs;
-    V acc[NV], F[NV], idv[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) { acc[v] = sem.ident(); F[v] = sem.ident(); idv[v] = sem.ident(); }
     const int32_t first_row = row;
     bool has_end = false;
     bool open = false;
     if (cnt > 0) {
         // empty tile-rows just before a row that starts at this lane's first tile
-        if (tl > 0 && (int64_t)__ldg(g.rowptr + row) == tl)
+        if (tl > 0 && row_start == tl)
             for (int32_t R = row - 1; R >= 0 && (int64_t)__ldg(g.rowptr + R) == tl; --R) sem.store(R, idv);
-        int64_t next = __ldg(g.rowptr + row + 1);
         int s = gbase;
 #pragma unroll
         for (int i = 0; i < P; ++i) {
@@ -465,28 +554,31 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
                     sem.tile(acc, words + i * S::TW, xs[i]);
                 } else {
                     using G = typename SEM::G;
-                    constexpr int NG = GatherSlots<G>::N;
-                    const G* sx = reinterpret_cast<const G*>(smem + warp * SmemPerWarp<SEM>::bytes);
-                    const float* sw = reinterpret_cast<const float*>(sx + NG);
+                    using L = GatherLayout<SEM>;
+                    const uint8_t* wsm = smem + warp * L::bytes;
+                    const G* sx = reinterpret_cast<const G*>(wsm + L::x_off);
+                    const float* sw = reinterpret_cast<const float*>(wsm + L::w_off);
                     const G* xt = sem.src() + (int64_t)col[i] * K;
                     const float* wt = sem.weighted ? sem.wts() + __ldg(sem.voffs() + t) : nullptr;
                     int qb = 0;
 #pragma unroll
-                    for (int r = 0; r < K; ++r) {
-                        uint32_t b = row_word<K>(words + i * S::TW, r);
+                    for (int q = 0; q < S::TW; ++q) {
+                        uint32_t b = words[i * S::TW + q];
                         while (b) {
-                            const int cc = __ffs(b) - 1;
+                            const int bit = __ffs(b) - 1;
                             b &= b - 1;
+                            const int r = q * (32 / S::ROW_BITS) + bit / S::ROW_BITS;
+                            const int cc = bit % S::ROW_BITS;
                             G xv;
                             float wv = 1.0f;
-                            if (s < NG) {
+                            if (s < L::NG) {
                                 xv = sx[s];
                                 if (sem.weighted) wv = sw[s];
                             } else {
                                 xv = __ldg(xt + cc);
                                 if (sem.weighted) wv = __ldg(wt + qb);
                             }
-                            acc[r] = sem.apply(acc[r], xv, wv);
+                            acc.set(r, sem.apply(acc.get(r), xv, wv));
                             ++s;
                             ++qb;
                         }
@@ -496,13 +588,13 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
                 if (t + 1 == next) {  // tile-row `row` ends with tile t
                     if (!has_end) {
 #pragma unroll
-                        for (int v = 0; v < NV; ++v) F[v] = acc[v];
+                        for (int v = 0; v < NV; ++v) F.set(v, acc.get(v));
                         has_end = true;
                     } else {
                         sem.store(row, acc);
                     }
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) acc[v] = sem.ident();
+                    for (int v = 0; v < NV; ++v) acc.set(v, sem.ident());
                     open = false;
                     if (i + 1 < cnt) {
                         int32_t R = row + 1;
@@ -515,126 +607,107 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
         }
     }
 
-    // Warp segmented scan of (reset = has_end, value = acc): the open value
-    // carried into each lane, joined in lane order.
+    // ---- warp segmented scan of (reset = has_end, value = acc) ----
+    // The reset pattern does not depend on the values, so which scan steps
+    // take a neighbour's value is worked out once, then applied per value.
+    bool take[5];
     bool inc_r = has_end;
-    V inc[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) inc[v] = acc[v];
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const bool o_r = __shfl_up_sync(0xffffffffu, inc_r, d);
-        const bool take = lane >= d && !inc_r;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            V o = __shfl_up_sync(0xffffffffu, inc[v], d);
-            if (take) inc[v] = sem.comb(o, inc[v]);
-        }
-        if (take) inc_r = o_r;
+    for (int k = 0; k < 5; ++k) {
+        const int d = 1 << k;
+        const bool o = __shfl_up_sync(FULL, inc_r, d);
+        take[k] = lane >= d && !inc_r;
+        if (take[k]) inc_r = o;
     }
-    bool ex_r = __shfl_up_sync(0xffffffffu, inc_r, 1);
+    bool ex_r = __shfl_up_sync(FULL, inc_r, 1);
     if (lane == 0) ex_r = false;
-    // the value carried into this lane joins its first segment (every lane
-    // takes part in the shuffles; only lanes that close a row use them)
+    const int la = (int)((ce - 1 - cs) / P);
+    const bool tail_open = __shfl_sync(FULL, open, la);
+    const bool tail_r = __shfl_sync(FULL, inc_r, 31);
+    const bool close_here = has_end && (ex_r || head_cs);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        const V o = __shfl_up_sync(0xffffffffu, inc[v], 1);
-        if (has_end && lane > 0) F[v] = sem.comb(o, F[v]);
-    }
-    if (has_end) {
-        // this lane closes the tile-row of its first tile
-        if (ex_r || head_cs) {
-            sem.store(first_row, F);
-        } else {
+        V x = acc.get(v);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) part.val_first[c * NV + v] = F[v];
+        for (int k = 0; k < 5; ++k) {
+            const V o = __shfl_up_sync(FULL, x, 1 << k);
+            if (take[k]) x = sem.comb(o, x);
+        }
+        const V ex = __shfl_up_sync(FULL, x, 1);
+        if (has_end && lane > 0) F.set(v, sem.comb(ex, F.get(v)));
+        if (has_end && !close_here) part.val_first[c * NV + v] = F.get(v);
+        if (lane == 31 && tail_open) {
+            if (tail_r || head_cs) part.val_last[c * NV + v] = x;
+            else part.val_first[c * NV + v] = x;
         }
     }
-
-    // chunk tail: the segment still open after the last active lane
-    const int la = (int)((ce - 1 - cs) / P);
-    const bool tail_open = __shfl_sync(0xffffffffu, open, la);
-    const bool tail_r = __shfl_sync(0xffffffffu, inc_r, 31);
-    if (lane == 31 && tail_open) {
-        if (tail_r || head_cs) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) part.val_last[c * NV + v] = inc[v];
-        } else {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) part.val_first[c * NV + v] = inc[v];
-        }
-    }
+    if (close_here) sem.store(first_row, F);
 }
 
-// Rows that span chunks: the chunk where such a row ends joins the partials
-// of every chunk the row touches, in chunk order, and stores the row.
+// Rows that span chunks: one warp per chunk c >= 1 whose first row began in an
+// earlier chunk and ends in c; the lanes fold the partials (lane l takes every
+// 32nd one, in order) and a fixed butterfly joins the lanes.
 template <int K, class SEM>
 __global__ void spmv_fixup_kernel(SpmvGeom g, SEM sem, Partials<typename SEM::V> part) {
     using S = ChunkShape<K>;
     using V = typename SEM::V;
+    using J = typename SEM::J;
     constexpr int NV = SEM::NV;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; c < g.nchunks;
-         c += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = (int)lane_id();
+    const int64_t wpb = blockDim.x >> 5;
+    for (int64_t c = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5) + 1; c < g.nchunks;
+         c += (int64_t)gridDim.x * wpb) {
         const int64_t cs = c * S::CT;
         const int64_t ce = min(cs + (int64_t)S::CT, g.T);
-        const int32_t R = g.chunk_row[c];
-        const int64_t rs = g.rowptr[R], re = g.rowptr[R + 1];
+        const int32_t R = __ldg(g.chunk_row + c);
+        const int64_t rs = __ldg(g.rowptr + R), re = __ldg(g.rowptr + R + 1);
         if (rs >= cs || re > ce) continue;  // R starts here, or does not end here
         const int64_t ca = rs / S::CT;
-        V acc[NV];
+        const int64_t np = c - ca + 1;
+        J acc[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] = part.val_last[ca * NV + v];
-        for (int64_t q = ca + 1; q <= c; ++q) {
+        for (int v = 0; v < NV; ++v) acc[v] = (J)sem.ident();
+        for (int64_t p = lane; p < np; p += 32) {
+            const V* src = p == 0 ? part.val_last + ca * NV : part.val_first + (ca + p) * NV;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) acc[v] = sem.comb(acc[v], part.val_first[q * NV + v]);
+            for (int v = 0; v < NV; ++v) acc[v] = sem.jcomb(acc[v], (J)src[v]);
         }
-        sem.store(R, acc);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const J other = __shfl_xor_sync(0xffffffffu, acc[v], o);
+                acc[v] = (lane & o) ? sem.jcomb(other, acc[v]) : sem.jcomb(acc[v], other);
+            }
+        }
+        if (lane == 0) {
+            RegAcc<V, NV> out;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) out.set(v, (V)acc[v]);
+            sem.store(R, out);
+        }
     }
 }
 
-// Plus-times specialisation of the join: fp64 accumulation of the partials.
-template <int K>
-__global__ void spmv_fixup_plus_kernel(SpmvGeom g, SemPlus<K> sem, Partials<float> part) {
-    using S = ChunkShape<K>;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; c < g.nchunks;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t cs = c * S::CT;
-        const int64_t ce = min(cs + (int64_t)S::CT, g.T);
-        const int32_t R = g.chunk_row[c];
-        const int64_t rs = g.rowptr[R], re = g.rowptr[R + 1];
-        if (rs >= cs || re > ce) continue;
-        const int64_t ca = rs / S::CT;
-        double acc[K];
-#pragma unroll
-        for (int v = 0; v < K; ++v) acc[v] = (double)part.val_last[ca * K + v];
-        for (int64_t q = ca + 1; q <= c; ++q) {
-#pragma unroll
-            for (int v = 0; v < K; ++v) acc[v] += (double)part.val_first[q * K + v];
-        }
-        float out[K];
-#pragma unroll
-        for (int v = 0; v < K; ++v) out[v] = (float)acc[v];
-        sem.store(R, out);
-    }
-}
-
-// Tile-rows before the first tile and after the last one (and every row when
-// the matrix has no tiles) get the identity; for bitset outputs the words past
-// the last tile-row are cleared.
+// Tile-rows before the first tile and after the last one (every row when the
+// matrix has no tiles) get the identity.
 template <int K, class SEM>
 __global__ void spmv_edges_kernel(SEM sem, int32_t lead_end, int32_t trail_begin, int32_t ntr) {
     using V = typename SEM::V;
-    V idv[SEM::NV];
+    RegAcc<V, SEM::NV> idv;
 #pragma unroll
-    for (int v = 0; v < SEM::NV; ++v) idv[v] = sem.ident();
+    for (int v = 0; v < SEM::NV; ++v) idv.set(v, sem.ident());
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t R = tid; R < lead_end; R += stride) sem.store((int32_t)R, idv);
     for (int64_t R = trail_begin + tid; R < ntr; R += stride) sem.store((int32_t)R, idv);
 }
 
-// Bitset outputs: the bits past the last tile-row (>= nTileRow*k) are never
-// stored by a row, so the word holding them is cleared before the rows land.
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+// Bitset outputs: bits past the last tile-row (>= nTileRow*k) are never
+// stored by a row, so the words holding them are cleared first.
 template <int K>
 static b2sr_status clear_bitset_tail(const b2sr_matrix* h, uint32_t* bits, cudaStream_t s) {
     int64_t words = ceil_div(h->n, 32);
@@ -652,18 +725,6 @@ static b2sr_status launch_edges(const b2sr_matrix* h, const SEM& sem, cudaStream
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), (int64_t)sm_count() * 4));
     spmv_edges_kernel<K, SEM><<<grid, 256, 0, s>>>(sem, lead_end, trail_begin, h->ntr);
     B2SR_LAUNCH_CHECK("spmv_edges_kernel");
-    return B2SR_OK;
-}
-
-template <int K, class SEM>
-static b2sr_status launch_chunks(const b2sr_matrix* h, const SpmvGeom& g, const SEM& sem,
-                                 Partials<typename SEM::V> part, cudaStream_t s) {
-    const int smem = kSpmvWarps * SmemPerWarp<SEM>::bytes;
-    if (smem > 48 * 1024)
-        B2SR_CUDA_TRY(cudaFuncSetAttribute(spmv_chunks_kernel<K, SEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    const int64_t blocks = ceil_div(h->nchunks, kSpmvWarps);
-    spmv_chunks_kernel<K, SEM><<<(unsigned)blocks, kSpmvThreads, smem, s>>>(g, sem, part);
-    B2SR_LAUNCH_CHECK("spmv_chunks_kernel");
     return B2SR_OK;
 }
 
@@ -687,28 +748,16 @@ static b2sr_status run_spmv(const b2sr_matrix* h, const SEM& sem, uint32_t* bits
     DevBuf pbuf(s);
     Partials<V> part;
     B2SR_TRY((alloc_partials<V, SEM::NV>(pbuf, h->nchunks, &part)));
-    B2SR_TRY((launch_chunks<K, SEM>(h, g, sem, part, s)));
+    const int smem = kSpmvWarps * GatherLayout<SEM>::bytes;
+    if (smem > 48 * 1024)
+        B2SR_CUDA_TRY(cudaFuncSetAttribute(spmv_chunks_kernel<K, SEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    spmv_chunks_kernel<K, SEM><<<(unsigned)ceil_div(h->nchunks, kSpmvWarps), kSpmvThreads, smem, s>>>(g, sem, part);
+    B2SR_LAUNCH_CHECK("spmv_chunks_kernel");
     if (h->nchunks > 1) {
-        int fgrid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(h->nchunks, 128), (int64_t)sm_count() * 8));
-        spmv_fixup_kernel<K, SEM><<<fgrid, 128, 0, s>>>(g, sem, part);
+        const int64_t warps = h->nchunks - 1;
+        int fgrid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(warps, 8), (int64_t)sm_count() * 16));
+        spmv_fixup_kernel<K, SEM><<<fgrid, 256, 0, s>>>(g, sem, part);
         B2SR_LAUNCH_CHECK("spmv_fixup_kernel");
-    }
-    return B2SR_OK;
-}
-
-template <int K>
-static b2sr_status run_spmv_plus(const b2sr_matrix* h, const SemPlus<K>& sem, cudaStream_t s) {
-    SpmvGeom g{h->rowptr, h->colind, h->tiles, h->chunk_row, h->T, h->nchunks, h->ntr};
-    B2SR_TRY((launch_edges<K, SemPlus<K>>(h, sem, s)));
-    if (h->nchunks == 0) return B2SR_OK;
-    DevBuf pbuf(s);
-    Partials<float> part;
-    B2SR_TRY((alloc_partials<float, K>(pbuf, h->nchunks, &part)));
-    B2SR_TRY((launch_chunks<K, SemPlus<K>>(h, g, sem, part, s)));
-    if (h->nchunks > 1) {
-        int fgrid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(h->nchunks, 128), (int64_t)sm_count() * 8));
-        spmv_fixup_plus_kernel<K><<<fgrid, 128, 0, s>>>(g, sem, part);
-        B2SR_LAUNCH_CHECK("spmv_fixup_plus_kernel");
     }
     return B2SR_OK;
 }
@@ -748,7 +797,7 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
         return with_k(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
             SemPlus<K> sem{static_cast<const float*>(x), static_cast<float*>(y), mask, comp, h->n};
-            return run_spmv_plus<K>(h, sem, s);
+            return run_spmv<K>(h, sem, nullptr, s);
         });
     }
     if (sr == B2SR_MIN_PLUS && in_kind == B2SR_VEC_F32 && out_kind == B2SR_VEC_F32) {

@@ -183,3 +183,35 @@ def test_sample_profile_full_sample_is_exact(g):
         if g.n % k == 0:
             assert th[q] == pytest.approx(len(tci), rel=1e-12)
             assert est[q] == pytest.approx(oracle.b2sr_bytes(g.n, k, len(tci)) / csr_bytes, rel=1e-12)
+
+
+# ------------------------------------------------------------ orientation ---
+
+def test_directed_orientation_follows_columns():
+    """Entry (i, j) is the edge j -> i, the direction y = A x moves values (Sec. V PR
+    uses the column-stochastic matrix): a chain with A[i+1, i] = 1 is walked forward."""
+    n = 7
+    a = np.zeros((n, n), dtype=np.int64)
+    for i in range(n - 1):
+        a[i + 1, i] = 1
+    fwd = graphs.from_dense(a)
+    np.testing.assert_array_equal(oracle.bfs(fwd, 0), np.arange(n))
+    np.testing.assert_array_equal(oracle.sssp(fwd, 0), np.arange(n, dtype=np.float64))
+    back = graphs.from_dense(a.T)
+    assert (oracle.bfs(back, 0)[1:] == -1).all()
+    # one SpMV step moves a value from j to i: y = A e_0 reaches vertex 1
+    e0 = np.zeros(n)
+    e0[0] = 1.0
+    np.testing.assert_array_equal(oracle.spmv_plus(fwd, e0), a @ e0)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_directed_bfs_sssp_match_scipy_on_transpose(seed):
+    g = graphs.random_directed(90, 0.04, seed, self_loops=False)
+    w = np.random.default_rng(seed).uniform(0.5, 3.0, g.nnz).astype(np.float32)
+    At = sp.csr_matrix((w.astype(np.float64), g.colind, g.rowptr), shape=(g.n, g.n)).T.tocsr()
+    for s in (0, 13, 89):
+        d = csgraph.shortest_path(At, method="D", directed=True, indices=s)
+        np.testing.assert_allclose(oracle.sssp(g, s, w), d, rtol=1e-12)
+        hops = csgraph.shortest_path(At, method="D", directed=True, unweighted=True, indices=s)
+        np.testing.assert_array_equal(oracle.bfs(g, s), np.where(np.isinf(hops), -1, hops).astype(np.int32))
