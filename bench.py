@@ -1,0 +1,412 @@
+#!/usr/bin/env python3
+"""Benchmark of the B2SR hot path on the R-MAT scale-20 workload.
+
+One step is one pass of the hot path over the workload: CSR -> B2SR
+conversion (tile_dim 8), one Boolean SpMV, BFS from 16 seeded sources (one
+batched 64-lane launch sequence), PageRank (fp32, d = 0.85, 50 iterations)
+and connected components.  Throughput is GTEPS: the edges the step's queries
+must touch -- nnz for the SpMV, nnz per BFS source, nnz per PageRank
+iteration and nnz for CC, i.e. 68 * nnz per step -- divided by the step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun, one replica per GPU (the path has no exchange
+step); rank 0 prints one JSON line.  --impl reference times the CPU oracle on
+a bounded sample of the same step (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "B2SR SpMV/BFS GTEPS & % HBM peak; TC edges/s; batched BFS queries/s vs plain"
+SCALE, EDGE_FACTOR, SEED = 20, 16, 1
+TILE = 8
+NSRC, PR_ITERS, DAMP = 16, 50, 0.85
+QUERIES_PER_STEP = 1 + NSRC + PR_ITERS + 1  # edge passes counted per step (x nnz)
+FAMILIES = ["spmv_bool", "spmv_count", "spmv_plus", "spmv_minplus", "spmv_min_i32", "spmm_or64"]
+
+
+def workload_desc(n, nnz):
+    return {
+        "workload": f"R-MAT scale {SCALE} ef{EDGE_FACTOR} a/b/c/d=0.57/0.19/0.19/0.05 seed {SEED}, symmetrised, "
+                    f"no self-loops/duplicates, unpermuted ids; B2SR tile 8x8; step = CSR->B2SR + Boolean SpMV + "
+                    f"BFS from {NSRC} seeded sources (batched) + fp32 PageRank {PR_ITERS} iters + CC",
+        "n": int(n), "nnz": int(nnz), "tile_dim": TILE, "sources": NSRC, "pagerank_iters": PR_ITERS,
+        "edges_per_step": int(QUERIES_PER_STEP * nnz),
+        "cache": "inputs larger than L2 (tile stream 272 MiB vs 129 MB L2); no flush",
+    }
+
+
+def make_graph():
+    from paper_2201_08560_gb300 import graphs
+    g = graphs.rmat(SCALE, EDGE_FACTOR, seed=SEED)
+    srcs = graphs.sources(g, NSRC, seed=7)
+    xbits = graphs.random_bits(g.n, 0.05, seed=3)
+    return g, srcs, xbits
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_step_estimate(g, srcs, xbits, bfs_sources=2, pr_iters=2):
+    """Times the oracle on a bounded sample of one step and extrapolates the
+    full step: conversion, SpMV and CC once, BFS on `bfs_sources` of the 16
+    sources, PageRank for `pr_iters` iterations."""
+    import oracle
+    t = {}
+    t0 = time.perf_counter(); oracle.b2sr(g, TILE); t["convert"] = time.perf_counter() - t0
+    t0 = time.perf_counter(); oracle.spmv_bool(g, xbits); t["spmv"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for s in srcs[:bfs_sources]:
+        oracle.bfs(g, int(s))
+    t["bfs_per_source"] = (time.perf_counter() - t0) / bfs_sources
+    t0 = time.perf_counter(); oracle.pagerank(g, DAMP, pr_iters); t["pr_per_iter"] = (time.perf_counter() - t0) / pr_iters
+    t0 = time.perf_counter(); oracle.cc(g); t["cc"] = time.perf_counter() - t0
+    step = t["convert"] + t["spmv"] + NSRC * t["bfs_per_source"] + PR_ITERS * t["pr_per_iter"] + t["cc"]
+    sample = (f"oracle (plain C, 1 thread) on the same graph: CSR->B2SR k=8, Boolean SpMV and CC once, BFS from "
+              f"{bfs_sources} of the {NSRC} sources, PageRank {pr_iters} iterations; step time extrapolated to "
+              f"{NSRC} sources and {PR_ITERS} iterations")
+    return step, t, sample
+
+
+def run_reference(args):
+    """The CPU oracle on the same step: conversion timed once, then per step a
+    bounded sample (SpMV, one BFS source, one PageRank iteration, CC) from
+    which the full step time is extrapolated."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    g, srcs, xbits = make_graph()
+    import oracle
+    oracle.build()
+    edges = QUERIES_PER_STEP * g.nnz
+    t0 = time.perf_counter()
+    oracle.b2sr(g, TILE)
+    t_conv = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        oracle.spmv_bool(g, xbits)
+    times = []
+    t_all = time.perf_counter()
+    for i in range(args.steps):
+        p = {}
+        a = time.perf_counter(); oracle.spmv_bool(g, xbits); p["spmv"] = time.perf_counter() - a
+        a = time.perf_counter(); oracle.bfs(g, int(srcs[i % NSRC])); p["bfs"] = time.perf_counter() - a
+        a = time.perf_counter(); oracle.pagerank(g, DAMP, 1); p["pr"] = time.perf_counter() - a
+        a = time.perf_counter(); oracle.cc(g); p["cc"] = time.perf_counter() - a
+        times.append(t_conv + p["spmv"] + NSRC * p["bfs"] + PR_ITERS * p["pr"] + p["cc"])
+    wall = time.perf_counter() - t_all
+    step = statistics.median(times)
+    value = edges / step / 1e9
+    sample = (f"oracle (plain C, 1 thread) on the same graph: CSR->B2SR k=8 timed once ({t_conv:.2f} s); each step "
+              f"times the Boolean SpMV, BFS from one of the {NSRC} sources, one PageRank iteration and CC, and "
+              f"extrapolates to {NSRC} sources and {PR_ITERS} iterations")
+    line = {
+        "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": int(args.gpus), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8/f64", "data": "synthetic", "impl": "reference",
+        "config": workload_desc(g.n, g.nnz),
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample,
+                         "wall_s": wall},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", self.gpu_id],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def traffic_for(family):
+    """dram bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2201_08560_gb300", "csrc", "spmv.cu")
+    try:
+        rec = json.load(open(path))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        ent = rec.get(family)
+        if ent and ent.get("kernel_source_sha256") == sha:
+            return float(ent["dram_bytes_per_launch"]), ent
+    except Exception:
+        pass
+    return None, None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    from paper_2201_08560_gb300 import binding as B
+
+    g, srcs, xbits = make_graph()
+    rp_h = torch.from_numpy(g.rowptr).pin_memory()
+    ci_h = torch.from_numpy(g.colind).pin_memory()
+    x_h = torch.from_numpy(xbits.view(np.int32)).pin_memory()
+    rp = rp_h.to(dev)
+    ci = ci_h.to(dev)
+    x = x_h.to(dev)
+    words = B.bitset_words(g.n)
+    y = torch.empty(words, dtype=torch.int32, device=dev)
+    levels = torch.empty((NSRC, g.n), dtype=torch.int32, device=dev)
+    pr = torch.empty(g.n, dtype=torch.float32, device=dev)
+    labels = torch.empty(g.n, dtype=torch.int32, device=dev)
+    srcs_l = [int(s) for s in srcs]
+
+    def step(rp_, ci_, x_):
+        m = B.b2sr_from_csr(g.n, rp_, ci_, TILE)
+        B.b2sr_spmv(m, B.BOOL_OR_AND, B.VEC_BITS, x_, B.VEC_BITS, y)
+        B.b2sr_bfs_multi(m, srcs_l, levels)
+        B.b2sr_pagerank(m, DAMP, PR_ITERS, None, pr)
+        B.b2sr_cc(m, labels)
+        m.close()
+
+    for _ in range(args.warmup):
+        step(rp, ci, x)
+    barrier()
+
+    # ---- device-resident timed region ----
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = str(local)
+    B.b2sr_timing_reset()
+    B.b2sr_timing_enable(True)
+    launches0 = B.b2sr_launch_count()
+    with ClockSampler(uuid) as clk:
+        barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            step(rp, ci, x)
+        ev1.record()
+        barrier()
+    launches = B.b2sr_launch_count() - launches0
+    B.b2sr_timing_enable(False)
+    ms_total = ev0.elapsed_time(ev1)
+    fam = {}
+    for f in FAMILIES:
+        t, n, by = B.b2sr_timing_read(f)
+        if n:
+            fam[f] = {"ms": t, "launches": n, "bytes": by}
+    B.b2sr_timing_reset()
+
+    # ---- end to end through the C ABI with host buffers ----
+    lv_h = torch.empty((NSRC, g.n), dtype=torch.int32).pin_memory()
+    pr_hh = torch.empty(g.n, dtype=torch.float32).pin_memory()
+    lab_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    y_h = torch.empty(words, dtype=torch.int32).pin_memory()
+    h2d = rp_h.numel() * 4 + ci_h.numel() * 4 + x_h.numel() * 4
+    d2h = lv_h.numel() * 4 + pr_hh.numel() * 4 + lab_h.numel() * 4 + y_h.numel() * 4
+    rp_d = torch.empty_like(rp)
+    ci_d = torch.empty_like(ci)
+    x_d = torch.empty_like(x)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        rp_d.copy_(rp_h, non_blocking=True)
+        ci_d.copy_(ci_h, non_blocking=True)
+        x_d.copy_(x_h, non_blocking=True)
+        step(rp_d, ci_d, x_d)
+        lv_h.copy_(levels, non_blocking=True)
+        pr_hh.copy_(pr, non_blocking=True)
+        lab_h.copy_(labels, non_blocking=True)
+        y_h.copy_(y, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e1.record()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+
+    # ---- max over ranks ----
+    t = torch.tensor([ms_total, e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_total, e2e_ms = float(t[0]), float(t[1])
+    edges = QUERIES_PER_STEP * g.nnz
+    ms_step = ms_total / args.steps
+    value = world * edges * args.steps / (ms_total / 1e3) / 1e9
+    e2e_value = world * edges * args.steps / (e2e_ms / 1e3) / 1e9
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- extras: batched vs plain BFS, Boolean SpMV alone ----
+    extra = {}
+    with B.b2sr_from_csr(g.n, rp, ci, TILE) as m:
+        for _ in range(2):
+            B.b2sr_bfs_multi(m, srcs_l, levels)
+            B.b2sr_bfs(m, srcs_l[0], levels[0])
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        a.record(); B.b2sr_bfs_multi(m, srcs_l, levels); b.record(); b.synchronize()
+        t_batched = a.elapsed_time(b)
+        a.record()
+        for i, s in enumerate(srcs_l):
+            B.b2sr_bfs(m, s, levels[i])
+        b.record(); b.synchronize()
+        t_plain = a.elapsed_time(b)
+        extra["bfs_16_sources"] = {"batched_ms": t_batched, "plain_ms": t_plain,
+                                   "batched_queries_per_s": NSRC / (t_batched / 1e3),
+                                   "plain_queries_per_s": NSRC / (t_plain / 1e3),
+                                   "speedup": t_plain / t_batched}
+        B.b2sr_timing_enable(True)
+        for _ in range(10):
+            B.b2sr_spmv(m, B.BOOL_OR_AND, B.VEC_BITS, x, B.VEC_BITS, y)
+        torch.cuda.synchronize()
+        tb, nb, byb = B.b2sr_timing_read("spmv_bool")
+        B.b2sr_timing_enable(False)
+        B.b2sr_timing_reset()
+        extra["spmv_bool_k8"] = {"kernel_us": tb / nb * 1e3, "gteps": g.nnz / (tb / nb / 1e3) / 1e9,
+                                 "gbs": byb / nb / (tb / nb / 1e3) / 1e9}
+
+    # ---- roofline of the dominant kernel ----
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, peak_src = 6800.0, "fallback 6.8 TB/s"
+    try:
+        pk = json.load(open(peaks_path))
+        peak, peak_src = float(pk["hbm_gbs"]), "measured hbm_gbs (MEASURED_PEAKS.json)"
+    except Exception:
+        pass
+    roofline = None
+    if fam:
+        dom = max(fam, key=lambda f: fam[f]["ms"])
+        d = fam[dom]
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        traffic, _ = traffic_for(dom)
+        roofline = {"bound": "hbm", "kernel": f"spmv_chunks_kernel ({dom}, k={TILE})", "achieved": achieved,
+                    "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                    "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+                    "avg_launch_us": d["ms"] / d["launches"] * 1e3, "launches": d["launches"],
+                    "share_of_step": d["ms"] / ms_total,
+                    "traffic": traffic}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            import oracle
+            oracle.build()
+            cstep, parts, sample = oracle_step_estimate(g, srcs, xbits)
+            cpu = {"value": edges / cstep / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample,
+                   "step_s_extrapolated": cstep, "parts_s": parts}
+        except Exception as e:  # the baseline is reported, never required
+            cpu = {"value": None, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8/f32", "data": "synthetic",
+        "config": dict(workload_desc(g.n, g.nnz), parallelism=f"replicas x{world}"),
+        "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": e2e_ms / args.steps},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "kernel_breakdown_ms_per_step": {f: fam[f]["ms"] / args.steps for f in fam},
+        "extra": extra,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -255,6 +255,30 @@ b2sr_status b2sr_cc(b2sr_handle h, int32_t* labels, int max_iters, void* stream)
  * b2sr_spgemm_masked_count.  Symmetric matrices.  count device int64[1]. */
 b2sr_status b2sr_tc(b2sr_handle h, int64_t* count, void* stream);
 
+/* ---------------------------------------------------------------------- */
+/* Measurement support (no counterpart in the paper)                       */
+/* ---------------------------------------------------------------------- */
+
+/* Number of kernels the library has launched in this process so far (no
+ * counterpart in the paper). */
+int64_t b2sr_launch_count(void);
+
+/* Turns CUDA-event timing of the SpMV chunk kernels (no counterpart in the
+ * paper) on (1) or off (0).  While
+ * on, every such launch is bracketed by two events on its own stream and
+ * recorded under its family: "spmv_bool", "spmv_count", "spmv_plus",
+ * "spmv_minplus", "spmv_min_i32" or "spmm_or64". */
+void b2sr_timing_enable(int on);
+
+/* Timing read-out (no counterpart in the paper).
+ * Sum over the recorded launches of `family`: device milliseconds, launch
+ * count and algorithmic bytes (the three B2SR arrays plus each vector read or
+ * written once).  Waits for the recorded events. */
+b2sr_status b2sr_timing_read(const char* family, double* total_ms, int64_t* launches, double* bytes);
+
+/* Drops all recorded launches (no counterpart in the paper). */
+b2sr_status b2sr_timing_reset(void);
+
 #ifdef __cplusplus
 }
 #endif

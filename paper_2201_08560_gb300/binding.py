@@ -63,6 +63,11 @@ def _load() -> ctypes.CDLL:
         "b2sr_pagerank": (c_int, [p, f32, c_int, p, p, p]),
         "b2sr_cc": (c_int, [p, p, c_int, p]),
         "b2sr_tc": (c_int, [p, p, p]),
+        "b2sr_launch_count": (i64, []),
+        "b2sr_timing_enable": (None, [c_int]),
+        "b2sr_timing_read": (c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                     ctypes.POINTER(ctypes.c_double)]),
+        "b2sr_timing_reset": (c_int, []),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -275,3 +280,28 @@ def b2sr_tc(m: Matrix, count: Optional[torch.Tensor] = None, stream=None) -> tor
 
 def version() -> str:
     return lib.b2sr_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# measurement support
+# ---------------------------------------------------------------------------
+
+def b2sr_launch_count() -> int:
+    return int(lib.b2sr_launch_count())
+
+
+def b2sr_timing_enable(on: bool = True):
+    lib.b2sr_timing_enable(1 if on else 0)
+
+
+def b2sr_timing_read(family: str):
+    """(device ms, launches, algorithmic bytes) summed over the recorded launches of `family`."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    by = ctypes.c_double()
+    _check(lib.b2sr_timing_read(family.encode(), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by)))
+    return ms.value, n.value, by.value
+
+
+def b2sr_timing_reset():
+    _check(lib.b2sr_timing_reset())

@@ -20,14 +20,25 @@ void clear_error();
 b2sr_status fail(b2sr_status st, const std::string& msg);
 b2sr_status cuda_fail(cudaError_t e, const char* what);
 
+// telemetry (telemetry.cu): launch counter and optional per-family event timing
+void note_launch();
+bool timing_on();
+// Records events around one launch of `family` moving `bytes` algorithmic bytes;
+// call timing_begin before and timing_end after the launch (no-ops when off).
+void* timing_begin(cudaStream_t s);
+void timing_end(void* tok, const char* family, double bytes, cudaStream_t s);
+
 #define B2SR_CUDA_TRY(expr)                                                 \
     do {                                                                    \
         cudaError_t _e = (expr);                                            \
         if (_e != cudaSuccess) return ::b2sr::cuda_fail(_e, #expr);         \
     } while (0)
 
+// Every kernel launch is followed by this check, which also counts the
+// launch for b2sr_launch_count().
 #define B2SR_LAUNCH_CHECK(name)                                             \
     do {                                                                    \
+        ::b2sr::note_launch();                                              \
         cudaError_t _e = cudaGetLastError();                                \
         if (_e != cudaSuccess) return ::b2sr::cuda_fail(_e, name);          \
     } while (0)

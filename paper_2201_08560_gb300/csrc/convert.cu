@@ -271,6 +271,7 @@ b2sr_status ensure_voff(b2sr_matrix* h, cudaStream_t s) {
     }
     if (st == B2SR_OK) {
         i64_to_i32_kernel<<<grid_for(h->T + 1), 256, 0, s>>>(scan.as<int64_t>(), h->T + 1, voff);
+        note_launch();
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_fail(e, "voff");
@@ -519,10 +520,12 @@ extern "C" b2sr_status b2sr_from_csr(int32_t n, const int32_t* rowptr, const int
             fill_tiles_kernel<<<grid_for(nnz), 256, 0, s>>>(sorted, flag.as<int32_t>(), tidx.as<int64_t>(), nnz, k,
                                                             sbits, o_colind, tilerow.as<int32_t>(),
                                                             reinterpret_cast<uint32_t*>(o_tiles));
+            note_launch();
             e = cudaGetLastError();
             if (e != cudaSuccess) return release(cuda_fail(e, "fill_tiles_kernel"));
         }
         build_rowptr_kernel<<<grid_for(T + 1), 256, 0, s>>>(tilerow.as<int32_t>(), T, ntr, o_rowptr);
+        note_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return release(cuda_fail(e, "build_rowptr_kernel"));
     }

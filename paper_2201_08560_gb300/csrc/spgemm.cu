@@ -316,6 +316,7 @@ b2sr_status spgemm_bool(const b2sr_matrix* A, const b2sr_matrix* B, cudaStream_t
         if (st != B2SR_OK) return release(st);
     }
     build_rowptr_from_rows<<<grid_for(TC + 1), 256, 0, s>>>(ctilerow.as<int32_t>(), TC, ntr, crp);
+    note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return release(cuda_fail(e, "build_rowptr_from_rows"));
     return new_handle_from_tiles(A->n, k, TC, crp, cci, ct, cap, s, out);

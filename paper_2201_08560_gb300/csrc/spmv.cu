@@ -738,8 +738,15 @@ static b2sr_status alloc_partials(DevBuf& pbuf, int64_t nchunks, Partials<V>* pa
     return B2SR_OK;
 }
 
+// Algorithmic bytes of one SpMV: the three B2SR arrays once, plus the
+// vectors each scheme reads and writes once.
+static double spmv_bytes(const b2sr_matrix* h, double vec_bytes) {
+    return 4.0 * ((double)h->ntr + 1.0) + (double)h->T * (4.0 + tile_bytes(h->k)) + vec_bytes;
+}
+
 template <int K, class SEM>
-static b2sr_status run_spmv(const b2sr_matrix* h, const SEM& sem, uint32_t* bits_out, cudaStream_t s) {
+static b2sr_status run_spmv(const b2sr_matrix* h, const SEM& sem, uint32_t* bits_out, cudaStream_t s,
+                            const char* family, double vec_bytes) {
     using V = typename SEM::V;
     SpmvGeom g{h->rowptr, h->colind, h->tiles, h->chunk_row, h->T, h->nchunks, h->ntr};
     if (bits_out) B2SR_TRY(clear_bitset_tail<K>(h, bits_out, s));
@@ -751,7 +758,9 @@ static b2sr_status run_spmv(const b2sr_matrix* h, const SEM& sem, uint32_t* bits
     const int smem = kSpmvWarps * GatherLayout<SEM>::bytes;
     if (smem > 48 * 1024)
         B2SR_CUDA_TRY(cudaFuncSetAttribute(spmv_chunks_kernel<K, SEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    void* tok = timing_begin(s);
     spmv_chunks_kernel<K, SEM><<<(unsigned)ceil_div(h->nchunks, kSpmvWarps), kSpmvThreads, smem, s>>>(g, sem, part);
+    timing_end(tok, family, spmv_bytes(h, vec_bytes), s);
     B2SR_LAUNCH_CHECK("spmv_chunks_kernel");
     if (h->nchunks > 1) {
         const int64_t warps = h->nchunks - 1;
@@ -781,7 +790,7 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
         return with_k(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
             SemBool<K> sem{static_cast<const uint32_t*>(x), static_cast<uint32_t*>(y), mask, comp, h->n};
-            return run_spmv<K>(h, sem, static_cast<uint32_t*>(y), s);
+            return run_spmv<K>(h, sem, static_cast<uint32_t*>(y), s, "spmv_bool", (mask ? 3.0 : 2.0) * h->n / 8.0);
         });
     }
     if (sr == B2SR_PLUS_TIMES && in_kind == B2SR_VEC_BITS && out_kind == B2SR_VEC_I32) {
@@ -789,7 +798,7 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
         return with_k(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
             SemCount<K> sem{static_cast<const uint32_t*>(x), static_cast<int32_t*>(y), mask, comp, h->n};
-            return run_spmv<K>(h, sem, nullptr, s);
+            return run_spmv<K>(h, sem, nullptr, s, "spmv_count", (mask ? 2.0 : 1.0) * h->n / 8.0 + 4.0 * h->n);
         });
     }
     if (sr == B2SR_PLUS_TIMES && in_kind == B2SR_VEC_F32 && out_kind == B2SR_VEC_F32) {
@@ -797,7 +806,7 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
         return with_k(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
             SemPlus<K> sem{static_cast<const float*>(x), static_cast<float*>(y), mask, comp, h->n};
-            return run_spmv<K>(h, sem, nullptr, s);
+            return run_spmv<K>(h, sem, nullptr, s, "spmv_plus", 8.0 * h->n + (mask ? h->n / 8.0 : 0.0));
         });
     }
     if (sr == B2SR_MIN_PLUS && in_kind == B2SR_VEC_F32 && out_kind == B2SR_VEC_F32) {
@@ -806,7 +815,9 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
             constexpr int K = decltype(kc)::value;
             SemMinPlus<K> sem{static_cast<const float*>(x), static_cast<float*>(y), mask, comp, h->n, weights,
                               h->voff, weights != nullptr};
-            return run_spmv<K>(h, sem, nullptr, s);
+            return run_spmv<K>(h, sem, nullptr, s, "spmv_minplus",
+                               8.0 * h->n + (mask ? h->n / 8.0 : 0.0) +
+                                   (weights ? 4.0 * (double)h->nnz + 4.0 * (double)h->T : 0.0));
         });
     }
     if (sr == B2SR_MIN_PLUS && in_kind == B2SR_VEC_I32 && out_kind == B2SR_VEC_I32) {
@@ -814,7 +825,7 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
         return with_k(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
             SemMinI32<K> sem{static_cast<const int32_t*>(x), static_cast<int32_t*>(y), mask, comp, h->n};
-            return run_spmv<K>(h, sem, nullptr, s);
+            return run_spmv<K>(h, sem, nullptr, s, "spmv_min_i32", 8.0 * h->n + (mask ? h->n / 8.0 : 0.0));
         });
     }
     return fail(B2SR_ERR_INVALID_ARG, "unsupported semiring / vector kind combination");
@@ -826,7 +837,7 @@ b2sr_status spmm64_dispatch(b2sr_matrix* h, const uint64_t* X, uint64_t* Y, cons
         constexpr int K = decltype(kc)::value;
         SemOr64<K> sem{reinterpret_cast<const unsigned long long*>(X), reinterpret_cast<unsigned long long*>(Y),
                        reinterpret_cast<const unsigned long long*>(M), comp ? 1 : 0, h->n};
-        return run_spmv<K>(h, sem, nullptr, s);
+        return run_spmv<K>(h, sem, nullptr, s, "spmm_or64", (M ? 24.0 : 16.0) * h->n);
     });
 }
 
