@@ -200,6 +200,7 @@ struct SemPlus {
     using J = double;
     static constexpr int NV = K;
     static constexpr bool kGather = true;
+    static constexpr bool kMayWeight = false;
     static constexpr bool weighted = false;
     const float* x;
     float* y;
@@ -232,6 +233,7 @@ struct SemMinPlus {
     using J = float;
     static constexpr int NV = K;
     static constexpr bool kGather = true;
+    static constexpr bool kMayWeight = true;
     const float* x;
     float* y;
     const uint32_t* mask;
@@ -265,6 +267,7 @@ struct SemMinI32 {
     using J = int32_t;
     static constexpr int NV = K;
     static constexpr bool kGather = true;
+    static constexpr bool kMayWeight = false;
     static constexpr bool weighted = false;
     const int32_t* x;
     int32_t* y;
@@ -296,6 +299,7 @@ struct SemOr64 {
     using J = unsigned long long;
     static constexpr int NV = K;
     static constexpr bool kGather = true;
+    static constexpr bool kMayWeight = false;
     static constexpr bool weighted = false;
     const unsigned long long* x;
     unsigned long long* y;
@@ -353,132 +357,57 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 constexpr int kSpmvThreads = 256;
 constexpr int kSpmvWarps = kSpmvThreads / 32;
 
-// Shared memory per warp for the gather schemes: NG staged input values
-// (+ NG weights), then the lane accumulators and first-row values
-// (NV x 32 each).  Set bits past NG in one chunk are read directly.
-template <class SEM, bool GATHER = SEM::kGather>
+// Shared memory per warp for the gather schemes (k <= 16): the lane's tile
+// words and tile columns (so the walk can index them), NG staged input values
+// (+ NG weights) with a one-byte (tile, row) tag each, and the lane
+// accumulators and first-row values (NV x 32 each).  A chunk with more than
+// NG set bits takes the direct path (values read from global memory).
+template <int K, class SEM, bool GATHER = SEM::kGather>
 struct GatherLayout {
     static constexpr int NG = 0;
     static constexpr int bytes = 0;
 };
-template <class SEM>
-struct GatherLayout<SEM, true> {
+template <int K, class SEM>
+struct GatherLayout<K, SEM, true> {
     using G = typename SEM::G;
     using V = typename SEM::V;
-    static constexpr int NG = sizeof(G) == 8 ? 512 : 1024;
-    static constexpr int x_off = 0;
-    static constexpr int w_off = NG * (int)sizeof(G);
-    static constexpr int acc_off = w_off + NG * 4;
-    static constexpr int f_off = acc_off + SEM::NV * 32 * (int)sizeof(V);
+    using S = ChunkShape<K>;
+    static constexpr int NG = 512;
+    static constexpr int words_off = 0;                                    // [32][P*TW] u32
+    static constexpr int col_off = words_off + S::CT * S::TW * 4;          // [32][P] i32
+    static constexpr int x_off = col_off + S::CT * 4;                      // [NG] G
+    static constexpr int w_off = x_off + NG * (int)sizeof(G);              // [NG] f32 (weighted only)
+    static constexpr int tag_off = w_off + (SEM::kMayWeight ? NG * 4 : 0);  // [NG] u8
+    static constexpr int acc_off = (tag_off + NG + 15) / 16 * 16;          // [NV][32] V
+    static constexpr int f_off = acc_off + SEM::NV * 32 * (int)sizeof(V);  // [NV][32] V
     static constexpr int bytes = f_off + SEM::NV * 32 * (int)sizeof(V);
 };
 
 // ---------------------------------------------------------------------------
-// the chunk kernel
+// pieces shared by the chunk kernels
 // ---------------------------------------------------------------------------
-template <int K, class SEM>
-__global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, SEM sem,
-                                                                   Partials<typename SEM::V> part) {
-    using S = ChunkShape<K>;
-    using V = typename SEM::V;
-    constexpr int NV = SEM::NV;
-    constexpr int P = S::P;
+struct LaneSpan {
+    int64_t cs, ce, tl;
+    int cnt;
+};
+
+// Tile-row of the lane's first tile, and rowptr[row], rowptr[row+1]; the
+// chunk's rows r0..r1 come from the schedule, a window of row pointers from
+// one coalesced load, and the search is a shuffle binary search.
+struct RowCursor {
+    int32_t row;
+    int64_t row_start, next;
+    bool head_cs;
+};
+
+__device__ __forceinline__ RowCursor locate_row(const SpmvGeom& g, int64_t c, const LaneSpan& ls, int lane) {
     constexpr unsigned FULL = 0xffffffffu;
-    extern __shared__ __align__(16) uint8_t smem[];
-    const int warp = threadIdx.x >> 5;
-    const int lane = (int)lane_id();
-    const int64_t c = (int64_t)blockIdx.x * kSpmvWarps + warp;
-    if (c >= g.nchunks) return;  // whole warps leave together
-
-    const int64_t cs = c * S::CT;
-    const int64_t ce = min(cs + (int64_t)S::CT, g.T);
-    const int64_t tl = cs + (int64_t)lane * P;
-    const int cnt = (int)max((int64_t)0, min((int64_t)P, ce - tl));
-
-    // ---- every load of the lane first: tiles, tile columns, chunk rows ----
-    uint4 tv[S::TILE_V4];
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(g.tiles + tl * S::TB);
-#pragma unroll
-        for (int q = 0; q < S::TILE_V4; ++q) tv[q] = __ldg(src + q);
-    }
-    const uint32_t* words = reinterpret_cast<const uint32_t*>(tv);
-    int32_t col[P];
-    if constexpr (P % 4 == 0) {
-        const int4* src = reinterpret_cast<const int4*>(g.colind + tl);
-#pragma unroll
-        for (int q = 0; q < P / 4; ++q) {
-            int4 v = __ldg(src + q);
-            col[4 * q] = v.x; col[4 * q + 1] = v.y; col[4 * q + 2] = v.z; col[4 * q + 3] = v.w;
-        }
-    } else {
-        const int2* src = reinterpret_cast<const int2*>(g.colind + tl);
-#pragma unroll
-        for (int q = 0; q < P / 2; ++q) {
-            int2 v = __ldg(src + q);
-            col[2 * q] = v.x; col[2 * q + 1] = v.y;
-        }
-    }
     const int32_t r0 = __ldg(g.chunk_row + c);
     const int32_t r1 = __ldg(g.chunk_row + c + 1);
     const int32_t span = r1 - r0;
-    // window of row pointers: lane j holds rowptr[r0 + j] for j <= span + 1
     const int64_t win = lane <= span + 1 ? (int64_t)__ldg(g.rowptr + r0 + lane) : INT64_MAX;
-
-    // ---- input: one k-bit segment per tile, or one value per set bit ----
-    uint32_t xs[SEM::kGather ? 1 : P];
-    int gbase = 0;
-    if constexpr (!SEM::kGather) {
-#pragma unroll
-        for (int i = 0; i < P; ++i) xs[i] = sem.xseg(col[i]);
-    } else {
-        using G = typename SEM::G;
-        using L = GatherLayout<SEM>;
-        uint8_t* wsm = smem + warp * L::bytes;
-        G* sx = reinterpret_cast<G*>(wsm + L::x_off);
-        float* sw = reinterpret_cast<float*>(wsm + L::w_off);
-        int nb = 0;
-#pragma unroll
-        for (int i = 0; i < P; ++i)
-            if (i < cnt) {
-#pragma unroll
-                for (int q = 0; q < S::TW; ++q) nb += __popc(words[i * S::TW + q]);
-            }
-        int incl = nb;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            int o = __shfl_up_sync(FULL, incl, d);
-            if (lane >= d) incl += o;
-        }
-        gbase = incl - nb;
-        int s = gbase;
-        const G* xsrc = sem.src();
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-            if (i < cnt && s < L::NG) {
-                const G* xt = xsrc + (int64_t)col[i] * K;
-                const float* wt = sem.weighted ? sem.wts() + __ldg(sem.voffs() + tl + i) : nullptr;
-                int qb = 0;
-#pragma unroll
-                for (int q = 0; q < S::TW; ++q) {
-                    uint32_t b = words[i * S::TW + q];
-                    while (b && s < L::NG) {
-                        const int bit = __ffs(b) - 1;
-                        b &= b - 1;
-                        const int cc = bit % S::ROW_BITS;
-                        cp_async_gather<sizeof(G)>(sx + s, xt + cc);
-                        if (sem.weighted) cp_async_gather<4>(sw + s, wt + qb);
-                        ++s;
-                        ++qb;
-                    }
-                }
-            }
-        }
-        cp_async_commit();
-    }
-
-    // ---- tile-row of the lane's first tile: count row starts <= tl ----
-    const bool head_cs = __shfl_sync(FULL, win, 0) == cs;
+    RowCursor rc;
+    rc.head_cs = __shfl_sync(FULL, win, 0) == ls.cs;
     int32_t row = r0;
     if (span > 0) {
         // first window: the row starts are lanes 1..31 (lane 0 is rowptr[r0])
@@ -487,12 +416,12 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
 #pragma unroll
         for (int step = 16; step >= 1; step >>= 1) {
             const int64_t v = __shfl_sync(FULL, b, pos + step - 1);
-            if (v <= tl) pos += step;
+            if (v <= ls.tl) pos += step;
         }
-        pos += (__shfl_sync(FULL, b, pos) <= tl) ? 1 : 0;
+        pos += (__shfl_sync(FULL, b, pos) <= ls.tl) ? 1 : 0;
         int32_t add = pos - 1;  // lane 0 is always counted
         int64_t last = __shfl_sync(FULL, win, 31);
-        for (int32_t base = 32; base <= span && last < ce; base += 32) {
+        for (int32_t base = 32; base <= span && last < ls.ce; base += 32) {
             // further windows (rare: many tile-rows in one chunk)
             const int32_t j = base + lane;
             const int64_t bb = j <= span ? (int64_t)__ldg(g.rowptr + r0 + j) : INT64_MAX;
@@ -500,114 +429,66 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
 #pragma unroll
             for (int step = 16; step >= 1; step >>= 1) {
                 const int64_t v = __shfl_sync(FULL, bb, p2 + step - 1);
-                if (v <= tl) p2 += step;
+                if (v <= ls.tl) p2 += step;
             }
-            p2 += (__shfl_sync(FULL, bb, p2) <= tl) ? 1 : 0;
+            p2 += (__shfl_sync(FULL, bb, p2) <= ls.tl) ? 1 : 0;
             add += p2;
             last = __shfl_sync(FULL, bb, 31);
         }
         row = r0 + add;
     }
-    // rowptr[row] and rowptr[row + 1], from the first window when it holds them
-    int64_t row_start, next;
-    {
-        const int d = row - r0;
-        const int64_t a0 = __shfl_sync(FULL, win, d < 32 ? d : 0);
-        const int64_t a1 = __shfl_sync(FULL, win, d + 1 < 32 ? d + 1 : 0);
-        row_start = d < 32 ? a0 : (int64_t)__ldg(g.rowptr + row);
-        next = d + 1 < 32 ? a1 : (int64_t)__ldg(g.rowptr + row + 1);
-    }
+    const int d = row - r0;
+    const int64_t a0 = __shfl_sync(FULL, win, d < 32 ? d : 0);
+    const int64_t a1 = __shfl_sync(FULL, win, d + 1 < 32 ? d + 1 : 0);
+    rc.row = row;
+    rc.row_start = d < 32 ? a0 : (int64_t)__ldg(g.rowptr + row);
+    rc.next = d + 1 < 32 ? a1 : (int64_t)__ldg(g.rowptr + row + 1);
+    return rc;
+}
 
-    // ---- accumulators ----
-    using Acc = typename std::conditional<SEM::kGather, SmemAcc<V, NV>, RegAcc<V, NV>>::type;
-    Acc acc, F;
-    if constexpr (SEM::kGather) {
-        using L = GatherLayout<SEM>;
-        uint8_t* wsm = smem + warp * L::bytes;
-        acc.p = reinterpret_cast<V*>(wsm + L::acc_off) + lane;
-        F.p = reinterpret_cast<V*>(wsm + L::f_off) + lane;
-    }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) { acc.set(v, sem.ident()); F.set(v, sem.ident()); }
-    RegAcc<V, NV> idv;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) idv.set(v, sem.ident());
-
-    if constexpr (SEM::kGather) {
-        cp_async_wait_all();
-        __syncwarp();
-    }
-
-    const int32_t first_row = row;
+// Per-lane walk state: the tile-row being accumulated, where it ends, the
+// values of the lane's first tile-row (F) once that row has ended.
+template <class SEM, class Acc>
+struct Walk {
+    int32_t row;
+    int64_t next;
     bool has_end = false;
     bool open = false;
-    if (cnt > 0) {
-        // empty tile-rows just before a row that starts at this lane's first tile
-        if (tl > 0 && row_start == tl)
-            for (int32_t R = row - 1; R >= 0 && (int64_t)__ldg(g.rowptr + R) == tl; --R) sem.store(R, idv);
-        int s = gbase;
+    // called after tile t (the lane's i-th of cnt) has been accumulated
+    __device__ __forceinline__ void end_tile(const SpmvGeom& g, const SEM& sem, Acc& acc, Acc& F, int64_t t, int i,
+                                             int cnt, const RegAcc<typename SEM::V, SEM::NV>& idv) {
+        open = true;
+        if (t + 1 == next) {  // tile-row `row` ends with tile t
+            if (!has_end) {
 #pragma unroll
-        for (int i = 0; i < P; ++i) {
-            if (i < cnt) {
-                const int64_t t = tl + i;
-                if constexpr (!SEM::kGather) {
-                    sem.tile(acc, words + i * S::TW, xs[i]);
-                } else {
-                    using G = typename SEM::G;
-                    using L = GatherLayout<SEM>;
-                    const uint8_t* wsm = smem + warp * L::bytes;
-                    const G* sx = reinterpret_cast<const G*>(wsm + L::x_off);
-                    const float* sw = reinterpret_cast<const float*>(wsm + L::w_off);
-                    const G* xt = sem.src() + (int64_t)col[i] * K;
-                    const float* wt = sem.weighted ? sem.wts() + __ldg(sem.voffs() + t) : nullptr;
-                    int qb = 0;
+                for (int v = 0; v < SEM::NV; ++v) F.set(v, acc.get(v));
+                has_end = true;
+            } else {
+                sem.store(row, acc);
+            }
 #pragma unroll
-                    for (int q = 0; q < S::TW; ++q) {
-                        uint32_t b = words[i * S::TW + q];
-                        while (b) {
-                            const int bit = __ffs(b) - 1;
-                            b &= b - 1;
-                            const int r = q * (32 / S::ROW_BITS) + bit / S::ROW_BITS;
-                            const int cc = bit % S::ROW_BITS;
-                            G xv;
-                            float wv = 1.0f;
-                            if (s < L::NG) {
-                                xv = sx[s];
-                                if (sem.weighted) wv = sw[s];
-                            } else {
-                                xv = __ldg(xt + cc);
-                                if (sem.weighted) wv = __ldg(wt + qb);
-                            }
-                            acc.set(r, sem.apply(acc.get(r), xv, wv));
-                            ++s;
-                            ++qb;
-                        }
-                    }
-                }
-                open = true;
-                if (t + 1 == next) {  // tile-row `row` ends with tile t
-                    if (!has_end) {
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) F.set(v, acc.get(v));
-                        has_end = true;
-                    } else {
-                        sem.store(row, acc);
-                    }
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) acc.set(v, sem.ident());
-                    open = false;
-                    if (i + 1 < cnt) {
-                        int32_t R = row + 1;
-                        while ((int64_t)__ldg(g.rowptr + R + 1) == next) { sem.store(R, idv); ++R; }
-                        row = R;
-                        next = __ldg(g.rowptr + row + 1);
-                    }
-                }
+            for (int v = 0; v < SEM::NV; ++v) acc.set(v, sem.ident());
+            open = false;
+            if (i + 1 < cnt) {
+                int32_t R = row + 1;
+                while ((int64_t)__ldg(g.rowptr + R + 1) == next) { sem.store(R, idv); ++R; }
+                row = R;
+                next = __ldg(g.rowptr + row + 1);
             }
         }
     }
+};
 
-    // ---- warp segmented scan of (reset = has_end, value = acc) ----
+// Warp segmented scan of (reset = has_end, value = acc), then: lanes that end
+// their first tile-row store it (or leave it as the chunk's first partial if
+// it began in an earlier chunk); lane 31 leaves the still-open tail.
+template <class SEM, class Acc>
+__device__ __forceinline__ void close_chunk(const SEM& sem, Partials<typename SEM::V> part, int64_t c,
+                                            const LaneSpan& ls, int lane, bool head_cs, int32_t first_row,
+                                            bool has_end, bool open, Acc& acc, Acc& F, int P) {
+    using V = typename SEM::V;
+    constexpr int NV = SEM::NV;
+    constexpr unsigned FULL = 0xffffffffu;
     // The reset pattern does not depend on the values, so which scan steps
     // take a neighbour's value is worked out once, then applied per value.
     bool take[5];
@@ -621,7 +502,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
     }
     bool ex_r = __shfl_up_sync(FULL, inc_r, 1);
     if (lane == 0) ex_r = false;
-    const int la = (int)((ce - 1 - cs) / P);
+    const int la = (int)((ls.ce - 1 - ls.cs) / P);
     const bool tail_open = __shfl_sync(FULL, open, la);
     const bool tail_r = __shfl_sync(FULL, inc_r, 31);
     const bool close_here = has_end && (ex_r || head_cs);
@@ -642,6 +523,259 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
         }
     }
     if (close_here) sem.store(first_row, F);
+}
+
+template <int K>
+__device__ __forceinline__ void load_lane_tiles(const SpmvGeom& g, int64_t tl, uint4 (&tv)[ChunkShape<K>::TILE_V4],
+                                                int32_t (&col)[ChunkShape<K>::P]) {
+    using S = ChunkShape<K>;
+    constexpr int P = S::P;
+    const uint4* src = reinterpret_cast<const uint4*>(g.tiles + tl * S::TB);
+#pragma unroll
+    for (int q = 0; q < S::TILE_V4; ++q) tv[q] = __ldg(src + q);
+    if constexpr (P % 4 == 0) {
+        const int4* cs = reinterpret_cast<const int4*>(g.colind + tl);
+#pragma unroll
+        for (int q = 0; q < P / 4; ++q) {
+            int4 v = __ldg(cs + q);
+            col[4 * q] = v.x; col[4 * q + 1] = v.y; col[4 * q + 2] = v.z; col[4 * q + 3] = v.w;
+        }
+    } else {
+        const int2* cs = reinterpret_cast<const int2*>(g.colind + tl);
+#pragma unroll
+        for (int q = 0; q < P / 2; ++q) {
+            int2 v = __ldg(cs + q);
+            col[2 * q] = v.x; col[2 * q + 1] = v.y;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// chunk kernel for the bit-vector schemes (all k) and for the value schemes
+// at k = 32: registers hold the accumulators (static row indices)
+// ---------------------------------------------------------------------------
+template <int K, class SEM>
+__global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, SEM sem,
+                                                                   Partials<typename SEM::V> part) {
+    using S = ChunkShape<K>;
+    using V = typename SEM::V;
+    constexpr int NV = SEM::NV;
+    constexpr int P = S::P;
+    const int warp = threadIdx.x >> 5;
+    const int lane = (int)lane_id();
+    const int64_t c = (int64_t)blockIdx.x * kSpmvWarps + warp;
+    if (c >= g.nchunks) return;  // whole warps leave together
+
+    LaneSpan ls;
+    ls.cs = c * S::CT;
+    ls.ce = min(ls.cs + (int64_t)S::CT, g.T);
+    ls.tl = ls.cs + (int64_t)lane * P;
+    ls.cnt = (int)max((int64_t)0, min((int64_t)P, ls.ce - ls.tl));
+
+    uint4 tv[S::TILE_V4];
+    int32_t col[P];
+    load_lane_tiles<K>(g, ls.tl, tv, col);
+    const uint32_t* words = reinterpret_cast<const uint32_t*>(tv);
+    uint32_t xs[SEM::kGather ? 1 : P];
+    if constexpr (!SEM::kGather) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) xs[i] = sem.xseg(col[i]);
+    }
+    const RowCursor rc = locate_row(g, c, ls, lane);
+
+    RegAcc<V, NV> acc, F, idv;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { acc.set(v, sem.ident()); F.set(v, sem.ident()); idv.set(v, sem.ident()); }
+    Walk<SEM, RegAcc<V, NV>> wk;
+    wk.row = rc.row;
+    wk.next = rc.next;
+    if (ls.cnt > 0) {
+        // empty tile-rows just before a row that starts at this lane's first tile
+        if (ls.tl > 0 && rc.row_start == ls.tl)
+            for (int32_t R = rc.row - 1; R >= 0 && (int64_t)__ldg(g.rowptr + R) == ls.tl; --R) sem.store(R, idv);
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            if (i < ls.cnt) {
+                const int64_t t = ls.tl + i;
+                if constexpr (!SEM::kGather) {
+                    sem.tile(acc, words + i * S::TW, xs[i]);
+                } else {
+                    using G = typename SEM::G;
+                    const G* xt = sem.src() + (int64_t)col[i] * K;
+                    const float* wt = sem.weighted ? sem.wts() + __ldg(sem.voffs() + t) : nullptr;
+                    int qb = 0;
+#pragma unroll
+                    for (int q = 0; q < S::TW; ++q) {
+                        uint32_t b = words[i * S::TW + q];
+                        while (b) {
+                            const int bit = __ffs(b) - 1;
+                            b &= b - 1;
+                            const int r = q * (32 / S::ROW_BITS) + bit / S::ROW_BITS;
+                            const float wv = sem.weighted ? __ldg(wt + qb) : 1.0f;
+                            acc.set(r, sem.apply(acc.get(r), __ldg(xt + bit % S::ROW_BITS), wv));
+                            ++qb;
+                        }
+                    }
+                }
+                wk.end_tile(g, sem, acc, F, t, i, ls.cnt, idv);
+            }
+        }
+    }
+    close_chunk(sem, part, c, ls, lane, rc.head_cs, rc.row, wk.has_end, wk.open, acc, F, P);
+}
+
+// ---------------------------------------------------------------------------
+// chunk kernel for the value schemes at k <= 16.  Each lane stages one
+// cp.async gather per set bit of its tiles (values land in shared memory in
+// set-bit order, tagged with their tile and row), then walks its set bits in
+// one flat loop; lanes with fewer bits finish early instead of idling through
+// per-word loops.
+// ---------------------------------------------------------------------------
+template <int K, class SEM>
+__global__ void __launch_bounds__(kSpmvThreads) spmv_gather_kernel(SpmvGeom g, SEM sem,
+                                                                   Partials<typename SEM::V> part) {
+    using S = ChunkShape<K>;
+    using V = typename SEM::V;
+    using G = typename SEM::G;
+    using L = GatherLayout<K, SEM>;
+    constexpr int NV = SEM::NV;
+    constexpr int P = S::P;
+    constexpr int TW = S::TW;
+    constexpr int RB = S::ROW_BITS;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int warp = threadIdx.x >> 5;
+    const int lane = (int)lane_id();
+    const int64_t c = (int64_t)blockIdx.x * kSpmvWarps + warp;
+    if (c >= g.nchunks) return;  // whole warps leave together
+
+    uint8_t* wsm = smem + warp * L::bytes;
+    uint32_t* swords = reinterpret_cast<uint32_t*>(wsm + L::words_off) + lane * (P * TW);
+    int32_t* scol = reinterpret_cast<int32_t*>(wsm + L::col_off) + lane * P;
+    G* sx = reinterpret_cast<G*>(wsm + L::x_off);
+    float* sw = reinterpret_cast<float*>(wsm + L::w_off);
+    uint8_t* stag = wsm + L::tag_off;
+
+    LaneSpan ls;
+    ls.cs = c * S::CT;
+    ls.ce = min(ls.cs + (int64_t)S::CT, g.T);
+    ls.tl = ls.cs + (int64_t)lane * P;
+    ls.cnt = (int)max((int64_t)0, min((int64_t)P, ls.ce - ls.tl));
+
+    uint4 tv[S::TILE_V4];
+    int32_t col[P];
+    load_lane_tiles<K>(g, ls.tl, tv, col);
+    const uint32_t* words = reinterpret_cast<const uint32_t*>(tv);
+
+    // set bits of the lane's tiles, their place in the chunk's staging area
+    int nb = 0;
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+        if (i < ls.cnt) {
+#pragma unroll
+            for (int q = 0; q < TW; ++q) nb += __popc(words[i * TW + q]);
+        }
+    int incl = nb;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += o;
+    }
+    const int gbase = incl - nb;
+    const bool staged = __shfl_sync(FULL, incl, 31) <= L::NG;  // warp-uniform
+
+    const RowCursor rc = locate_row(g, c, ls, lane);
+    RegAcc<V, NV> idv;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) idv.set(v, sem.ident());
+    SmemAcc<V, NV> acc, F;
+    acc.p = reinterpret_cast<V*>(wsm + L::acc_off) + lane;
+    F.p = reinterpret_cast<V*>(wsm + L::f_off) + lane;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { acc.set(v, sem.ident()); F.set(v, sem.ident()); }
+    Walk<SEM, SmemAcc<V, NV>> wk;
+    wk.row = rc.row;
+    wk.next = rc.next;
+
+    if (staged) {
+        // lane-private copies of the tile words and columns (indexed below)
+#pragma unroll
+        for (int q = 0; q < P * TW; ++q) swords[q] = words[q];
+#pragma unroll
+        for (int i = 0; i < P; ++i) scol[i] = col[i];
+        // one gather per set bit, in (tile, row, bit) order
+        {
+            int wi = 0;
+            uint32_t cur = nb > 0 ? swords[0] : 0u;
+            int qb = 0, ti = 0;
+            const float* wt = (sem.weighted && ls.cnt > 0) ? sem.wts() + __ldg(sem.voffs() + ls.tl) : nullptr;
+            for (int j = 0; j < nb; ++j) {
+                while (cur == 0u) cur = swords[++wi];
+                const int bit = __ffs(cur) - 1;
+                cur &= cur - 1;
+                const int i = wi / TW;
+                if (sem.weighted && i != ti) {
+                    ti = i;
+                    qb = 0;
+                    wt = sem.wts() + __ldg(sem.voffs() + ls.tl + i);
+                }
+                const int r = (wi % TW) * (32 / RB) + bit / RB;
+                const int s = gbase + j;
+                cp_async_gather<sizeof(G)>(sx + s, sem.src() + (int64_t)scol[i] * K + bit % RB);
+                if (sem.weighted) cp_async_gather<4>(sw + s, wt + qb);
+                stag[s] = (uint8_t)(i * K + r);
+                ++qb;
+            }
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        // each lane reads back only the slots it wrote itself
+    }
+
+    if (ls.cnt > 0) {
+        // empty tile-rows just before a row that starts at this lane's first tile
+        if (ls.tl > 0 && rc.row_start == ls.tl)
+            for (int32_t R = rc.row - 1; R >= 0 && (int64_t)__ldg(g.rowptr + R) == ls.tl; --R) sem.store(R, idv);
+        if (staged) {
+            int i = 0;
+            for (int j = 0; j < nb; ++j) {
+                const int s = gbase + j;
+                const int tag = stag[s];
+                const int ti = tag / K;
+                while (i < ti) {  // every tile has a set bit, so i advances one tile at a time
+                    wk.end_tile(g, sem, acc, F, ls.tl + i, i, ls.cnt, idv);
+                    ++i;
+                }
+                const int r = tag % K;
+                acc.set(r, sem.apply(acc.get(r), sx[s], sem.weighted ? sw[s] : 1.0f));
+            }
+            for (; i < ls.cnt; ++i) wk.end_tile(g, sem, acc, F, ls.tl + i, i, ls.cnt, idv);
+        } else {
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                if (i < ls.cnt) {
+                    const int64_t t = ls.tl + i;
+                    const G* xt = sem.src() + (int64_t)col[i] * K;
+                    const float* wt = sem.weighted ? sem.wts() + __ldg(sem.voffs() + t) : nullptr;
+                    int qb = 0;
+#pragma unroll
+                    for (int q = 0; q < TW; ++q) {
+                        uint32_t b = words[i * TW + q];
+                        while (b) {
+                            const int bit = __ffs(b) - 1;
+                            b &= b - 1;
+                            const int r = q * (32 / RB) + bit / RB;
+                            const float wv = sem.weighted ? __ldg(wt + qb) : 1.0f;
+                            acc.set(r, sem.apply(acc.get(r), __ldg(xt + bit % RB), wv));
+                            ++qb;
+                        }
+                    }
+                    wk.end_tile(g, sem, acc, F, t, i, ls.cnt, idv);
+                }
+            }
+        }
+    }
+    close_chunk(sem, part, c, ls, lane, rc.head_cs, rc.row, wk.has_end, wk.open, acc, F, P);
 }
 
 // Rows that span chunks: one warp per chunk c >= 1 whose first row began in an
@@ -665,6 +799,22 @@ __global__ void spmv_fixup_kernel(SpmvGeom g, SEM sem, Partials<typename SEM::V>
         const int64_t ca = rs / S::CT;
         const int64_t np = c - ca + 1;
         J acc[NV];
+        if (np <= 16) {
+            // few partials (the usual case): lane 0 joins them in order
+            if (lane == 0) {
+                RegAcc<V, NV> out;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) acc[v] = (J)part.val_last[ca * NV + v];
+                for (int64_t q = ca + 1; q <= c; ++q) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) acc[v] = sem.jcomb(acc[v], (J)part.val_first[q * NV + v]);
+                }
+#pragma unroll
+                for (int v = 0; v < NV; ++v) out.set(v, (V)acc[v]);
+                sem.store(R, out);
+            }
+            continue;
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) acc[v] = (J)sem.ident();
         for (int64_t p = lane; p < np; p += 32) {
@@ -755,13 +905,21 @@ static b2sr_status run_spmv(const b2sr_matrix* h, const SEM& sem, uint32_t* bits
     DevBuf pbuf(s);
     Partials<V> part;
     B2SR_TRY((alloc_partials<V, SEM::NV>(pbuf, h->nchunks, &part)));
-    const int smem = kSpmvWarps * GatherLayout<SEM>::bytes;
-    if (smem > 48 * 1024)
-        B2SR_CUDA_TRY(cudaFuncSetAttribute(spmv_chunks_kernel<K, SEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    void* tok = timing_begin(s);
-    spmv_chunks_kernel<K, SEM><<<(unsigned)ceil_div(h->nchunks, kSpmvWarps), kSpmvThreads, smem, s>>>(g, sem, part);
-    timing_end(tok, family, spmv_bytes(h, vec_bytes), s);
-    B2SR_LAUNCH_CHECK("spmv_chunks_kernel");
+    const unsigned blocks = (unsigned)ceil_div(h->nchunks, kSpmvWarps);
+    if constexpr (SEM::kGather && K <= 16) {
+        const int smem = kSpmvWarps * GatherLayout<K, SEM>::bytes;
+        if (smem > 48 * 1024)
+            B2SR_CUDA_TRY(cudaFuncSetAttribute(spmv_gather_kernel<K, SEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        void* tok = timing_begin(s);
+        spmv_gather_kernel<K, SEM><<<blocks, kSpmvThreads, smem, s>>>(g, sem, part);
+        timing_end(tok, family, spmv_bytes(h, vec_bytes), s);
+        B2SR_LAUNCH_CHECK("spmv_gather_kernel");
+    } else {
+        void* tok = timing_begin(s);
+        spmv_chunks_kernel<K, SEM><<<blocks, kSpmvThreads, 0, s>>>(g, sem, part);
+        timing_end(tok, family, spmv_bytes(h, vec_bytes), s);
+        B2SR_LAUNCH_CHECK("spmv_chunks_kernel");
+    }
     if (h->nchunks > 1) {
         const int64_t warps = h->nchunks - 1;
         int fgrid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(warps, 8), (int64_t)sm_count() * 16));
