@@ -118,12 +118,30 @@ struct SmemAcc {
 //     weighted, wts(), voffs() and apply(acc, x_j, w_ij).
 // ---------------------------------------------------------------------------
 
-// bmv_bin_bin_bin[_masked]: bitset in, bitset out, acc = k-bit row mask
+// Row mask of OR-accumulated, input-masked tile words (k <= 8: a row per
+// byte): bit r is set iff byte r is non-zero.  The non-zero bytes get their
+// high bit, and one multiply gathers the four high bits of a word.
+template <int K>
+__device__ __forceinline__ uint32_t nonzero_rows(const uint32_t* w) {
+    uint32_t out = 0;
+#pragma unroll
+    for (int q = 0; q < K / 4; ++q) {
+        const uint32_t m = w[q];
+        const uint32_t h = (((m & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | m) & 0x80808080u;
+        out |= (((h >> 7) * 0x00204081u) >> 21 & 0xFu) << (4 * q);
+    }
+    return out;
+}
+
+// bmv_bin_bin_bin[_masked]: bitset in, bitset out.  For k <= 8 the
+// accumulator is the OR of the tile words ANDed with the input segment (one
+// word per four rows); OR commutes with "row is non-zero", so the row mask is
+// formed only when a row is stored.  For k >= 16 it is the k-bit row mask.
 template <int K>
 struct SemBool {
     using V = uint32_t;
     using J = uint32_t;
-    static constexpr int NV = 1;
+    static constexpr int NV = K <= 8 ? K / 4 : 1;
     static constexpr bool kGather = false;
     const uint32_t* x;
     uint32_t* y;
@@ -136,11 +154,25 @@ struct SemBool {
     __device__ uint32_t xseg(int32_t Jc) const { return ld_bits(x, (int64_t)Jc * K, K); }
     template <class A>
     __device__ void tile(A& acc, const uint32_t* w, uint32_t xs) const {
-        acc.set(0, acc.get(0) | rows_hit<K>(w, xs));
+        if constexpr (K <= 8) {
+            const uint32_t rep = xs * 0x01010101u;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) acc.set(q, acc.get(q) | (w[q] & rep));
+        } else {
+            acc.set(0, acc.get(0) | rows_hit<K>(w, xs));
+        }
     }
     template <class A>
     __device__ void store(int32_t R, const A& acc) const {
-        uint32_t v = acc.get(0);
+        uint32_t v;
+        if constexpr (K <= 8) {
+            uint32_t w[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) w[q] = acc.get(q);
+            v = nonzero_rows<K>(w);
+        } else {
+            v = acc.get(0);
+        }
         if (mask) {
             uint32_t mb = ld_bits(mask, (int64_t)R * K, K);
             v &= comp ? ~mb : mb;
@@ -357,11 +389,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 constexpr int kSpmvThreads = 256;
 constexpr int kSpmvWarps = kSpmvThreads / 32;
 
-// Shared memory per warp for the gather schemes (k <= 16): the lane's tile
-// words and tile columns (so the walk can index them), NG staged input values
-// (+ NG weights) with a one-byte (tile, row) tag each, and the lane
-// accumulators and first-row values (NV x 32 each).  A chunk with more than
-// NG set bits takes the direct path (values read from global memory).
+// Shared memory per warp for the gather schemes (k <= 16): NG staged input
+// values (+ NG weights for min-plus).  A chunk with more than NG set bits
+// reads its values straight from global memory instead.
 template <int K, class SEM, bool GATHER = SEM::kGather>
 struct GatherLayout {
     static constexpr int NG = 0;
@@ -370,17 +400,10 @@ struct GatherLayout {
 template <int K, class SEM>
 struct GatherLayout<K, SEM, true> {
     using G = typename SEM::G;
-    using V = typename SEM::V;
-    using S = ChunkShape<K>;
     static constexpr int NG = 512;
-    static constexpr int words_off = 0;                                    // [32][P*TW] u32
-    static constexpr int col_off = words_off + S::CT * S::TW * 4;          // [32][P] i32
-    static constexpr int x_off = col_off + S::CT * 4;                      // [NG] G
-    static constexpr int w_off = x_off + NG * (int)sizeof(G);              // [NG] f32 (weighted only)
-    static constexpr int tag_off = w_off + (SEM::kMayWeight ? NG * 4 : 0);  // [NG] u8
-    static constexpr int acc_off = (tag_off + NG + 15) / 16 * 16;          // [NV][32] V
-    static constexpr int f_off = acc_off + SEM::NV * 32 * (int)sizeof(V);  // [NV][32] V
-    static constexpr int bytes = f_off + SEM::NV * 32 * (int)sizeof(V);
+    static constexpr int x_off = 0;                                     // [NG] G
+    static constexpr int w_off = NG * (int)sizeof(G);                   // [NG] f32 (min-plus only)
+    static constexpr int bytes = w_off + (SEM::kMayWeight ? NG * 4 : 0);
 };
 
 // ---------------------------------------------------------------------------
@@ -625,14 +648,15 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
 }
 
 // ---------------------------------------------------------------------------
-// chunk kernel for the value schemes at k <= 16.  Each lane stages one
-// cp.async gather per set bit of its tiles (values land in shared memory in
-// set-bit order, tagged with their tile and row), then walks its set bits in
-// one flat loop; lanes with fewer bits finish early instead of idling through
-// per-word loops.
+// chunk kernel for the value schemes at k <= 16.  Pass 1: each lane issues
+// one cp.async gather per set bit of its tiles, so all of a warp's input
+// values are in flight at once and land in shared memory in set-bit order.
+// Pass 2: the lane walks the same bits again and adds each staged value to its
+// row's register accumulator (a row word holds 32/RB rows; the row is picked
+// by a predicated select, keeping every index static).
 // ---------------------------------------------------------------------------
 template <int K, class SEM>
-__global__ void __launch_bounds__(kSpmvThreads) spmv_gather_kernel(SpmvGeom g, SEM sem,
+__global__ void __launch_bounds__(kSpmvThreads, (K >= 16 ? 2 : 3)) spmv_gather_kernel(SpmvGeom g, SEM sem,
                                                                    Partials<typename SEM::V> part) {
     using S = ChunkShape<K>;
     using V = typename SEM::V;
@@ -642,6 +666,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_gather_kernel(SpmvGeom g, S
     constexpr int P = S::P;
     constexpr int TW = S::TW;
     constexpr int RB = S::ROW_BITS;
+    constexpr int RPW = 32 / RB;  // rows per 32-bit word
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(16) uint8_t smem[];
     const int warp = threadIdx.x >> 5;
@@ -650,11 +675,8 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_gather_kernel(SpmvGeom g, S
     if (c >= g.nchunks) return;  // whole warps leave together
 
     uint8_t* wsm = smem + warp * L::bytes;
-    uint32_t* swords = reinterpret_cast<uint32_t*>(wsm + L::words_off) + lane * (P * TW);
-    int32_t* scol = reinterpret_cast<int32_t*>(wsm + L::col_off) + lane * P;
     G* sx = reinterpret_cast<G*>(wsm + L::x_off);
     float* sw = reinterpret_cast<float*>(wsm + L::w_off);
-    uint8_t* stag = wsm + L::tag_off;
 
     LaneSpan ls;
     ls.cs = c * S::CT;
@@ -667,7 +689,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_gather_kernel(SpmvGeom g, S
     load_lane_tiles<K>(g, ls.tl, tv, col);
     const uint32_t* words = reinterpret_cast<const uint32_t*>(tv);
 
-    // set bits of the lane's tiles, their place in the chunk's staging area
+    // set bits of the lane's tiles and their slots in the warp's staging area
     int nb = 0;
 #pragma unroll
     for (int i = 0; i < P; ++i)
@@ -684,94 +706,74 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_gather_kernel(SpmvGeom g, S
     const int gbase = incl - nb;
     const bool staged = __shfl_sync(FULL, incl, 31) <= L::NG;  // warp-uniform
 
-    const RowCursor rc = locate_row(g, c, ls, lane);
-    RegAcc<V, NV> idv;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) idv.set(v, sem.ident());
-    SmemAcc<V, NV> acc, F;
-    acc.p = reinterpret_cast<V*>(wsm + L::acc_off) + lane;
-    F.p = reinterpret_cast<V*>(wsm + L::f_off) + lane;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) { acc.set(v, sem.ident()); F.set(v, sem.ident()); }
-    Walk<SEM, SmemAcc<V, NV>> wk;
-    wk.row = rc.row;
-    wk.next = rc.next;
-
     if (staged) {
-        // lane-private copies of the tile words and columns (indexed below)
+        int s = gbase;
 #pragma unroll
-        for (int q = 0; q < P * TW; ++q) swords[q] = words[q];
+        for (int i = 0; i < P; ++i) {
+            if (i < ls.cnt) {
+                const G* xt = sem.src() + (int64_t)col[i] * K;
+                const float* wt = sem.weighted ? sem.wts() + __ldg(sem.voffs() + ls.tl + i) : nullptr;
 #pragma unroll
-        for (int i = 0; i < P; ++i) scol[i] = col[i];
-        // one gather per set bit, in (tile, row, bit) order
-        {
-            int wi = 0;
-            uint32_t cur = nb > 0 ? swords[0] : 0u;
-            int qb = 0, ti = 0;
-            const float* wt = (sem.weighted && ls.cnt > 0) ? sem.wts() + __ldg(sem.voffs() + ls.tl) : nullptr;
-            for (int j = 0; j < nb; ++j) {
-                while (cur == 0u) cur = swords[++wi];
-                const int bit = __ffs(cur) - 1;
-                cur &= cur - 1;
-                const int i = wi / TW;
-                if (sem.weighted && i != ti) {
-                    ti = i;
-                    qb = 0;
-                    wt = sem.wts() + __ldg(sem.voffs() + ls.tl + i);
+                for (int q = 0; q < TW; ++q) {
+                    uint32_t b = words[i * TW + q];
+                    while (b) {
+                        const int bit = __ffs(b) - 1;
+                        b &= b - 1;
+                        cp_async_gather<sizeof(G)>(sx + s, xt + bit % RB);
+                        if (sem.weighted) cp_async_gather<4>(sw + s, wt + (s - gbase));
+                        ++s;
+                    }
                 }
-                const int r = (wi % TW) * (32 / RB) + bit / RB;
-                const int s = gbase + j;
-                cp_async_gather<sizeof(G)>(sx + s, sem.src() + (int64_t)scol[i] * K + bit % RB);
-                if (sem.weighted) cp_async_gather<4>(sw + s, wt + qb);
-                stag[s] = (uint8_t)(i * K + r);
-                ++qb;
             }
         }
         cp_async_commit();
-        cp_async_wait_all();
-        // each lane reads back only the slots it wrote itself
     }
+
+    const RowCursor rc = locate_row(g, c, ls, lane);
+    RegAcc<V, NV> acc, F, idv;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { acc.set(v, sem.ident()); F.set(v, sem.ident()); idv.set(v, sem.ident()); }
+    Walk<SEM, RegAcc<V, NV>> wk;
+    wk.row = rc.row;
+    wk.next = rc.next;
+    if (staged) cp_async_wait_all();  // each lane reads back only the slots it filled
 
     if (ls.cnt > 0) {
         // empty tile-rows just before a row that starts at this lane's first tile
         if (ls.tl > 0 && rc.row_start == ls.tl)
             for (int32_t R = rc.row - 1; R >= 0 && (int64_t)__ldg(g.rowptr + R) == ls.tl; --R) sem.store(R, idv);
-        if (staged) {
-            int i = 0;
-            for (int j = 0; j < nb; ++j) {
-                const int s = gbase + j;
-                const int tag = stag[s];
-                const int ti = tag / K;
-                while (i < ti) {  // every tile has a set bit, so i advances one tile at a time
-                    wk.end_tile(g, sem, acc, F, ls.tl + i, i, ls.cnt, idv);
-                    ++i;
-                }
-                const int r = tag % K;
-                acc.set(r, sem.apply(acc.get(r), sx[s], sem.weighted ? sw[s] : 1.0f));
-            }
-            for (; i < ls.cnt; ++i) wk.end_tile(g, sem, acc, F, ls.tl + i, i, ls.cnt, idv);
-        } else {
+        int s = gbase;
 #pragma unroll
-            for (int i = 0; i < P; ++i) {
-                if (i < ls.cnt) {
-                    const int64_t t = ls.tl + i;
-                    const G* xt = sem.src() + (int64_t)col[i] * K;
-                    const float* wt = sem.weighted ? sem.wts() + __ldg(sem.voffs() + t) : nullptr;
-                    int qb = 0;
+        for (int i = 0; i < P; ++i) {
+            if (i < ls.cnt) {
+                const int64_t t = ls.tl + i;
+                const G* xt = sem.src() + (int64_t)col[i] * K;
+                const float* wt = (!staged && sem.weighted) ? sem.wts() + __ldg(sem.voffs() + t) : nullptr;
+                int qb = 0;
 #pragma unroll
-                    for (int q = 0; q < TW; ++q) {
-                        uint32_t b = words[i * TW + q];
-                        while (b) {
-                            const int bit = __ffs(b) - 1;
-                            b &= b - 1;
-                            const int r = q * (32 / RB) + bit / RB;
-                            const float wv = sem.weighted ? __ldg(wt + qb) : 1.0f;
-                            acc.set(r, sem.apply(acc.get(r), __ldg(xt + bit % RB), wv));
-                            ++qb;
+                for (int q = 0; q < TW; ++q) {
+                    uint32_t b = words[i * TW + q];
+                    while (b) {
+                        const int bit = __ffs(b) - 1;
+                        b &= b - 1;
+                        G xv;
+                        float wv = 1.0f;
+                        if (staged) {
+                            xv = sx[s];
+                            if (sem.weighted) wv = sw[s];
+                        } else {
+                            xv = __ldg(xt + bit % RB);
+                            if (sem.weighted) wv = __ldg(wt + qb);
                         }
+                        const int u = bit / RB;
+#pragma unroll
+                        for (int uu = 0; uu < RPW; ++uu)
+                            if (u == uu) acc.set(q * RPW + uu, sem.apply(acc.get(q * RPW + uu), xv, wv));
+                        ++s;
+                        ++qb;
                     }
-                    wk.end_tile(g, sem, acc, F, t, i, ls.cnt, idv);
                 }
+                wk.end_tile(g, sem, acc, F, t, i, ls.cnt, idv);
             }
         }
     }
