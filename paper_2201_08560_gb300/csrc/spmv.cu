@@ -389,9 +389,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 constexpr int kSpmvThreads = 256;
 constexpr int kSpmvWarps = kSpmvThreads / 32;
 
-// Shared memory per warp for the gather schemes (k <= 16): NG staged input
-// values (+ NG weights for min-plus).  A chunk with more than NG set bits
-// reads its values straight from global memory instead.
+// Shared memory per warp for the gather schemes (k <= 16): the lanes' tile
+// words and tile columns (lane-private, so the flat bit walk can index them),
+// NG staged input values (+ NG weights for min-plus) and a one-byte
+// (tile, row) tag per staged value.  A chunk with more than NG set bits reads
+// its values straight from global memory instead.
 template <int K, class SEM, bool GATHER = SEM::kGather>
 struct GatherLayout {
     static constexpr int NG = 0;
@@ -400,10 +402,14 @@ struct GatherLayout {
 template <int K, class SEM>
 struct GatherLayout<K, SEM, true> {
     using G = typename SEM::G;
+    using S = ChunkShape<K>;
     static constexpr int NG = 512;
-    static constexpr int x_off = 0;                                     // [NG] G
-    static constexpr int w_off = NG * (int)sizeof(G);                   // [NG] f32 (min-plus only)
-    static constexpr int bytes = w_off + (SEM::kMayWeight ? NG * 4 : 0);
+    static constexpr int words_off = 0;                                    // [32][P*TW] u32
+    static constexpr int col_off = words_off + S::CT * S::TW * 4;          // [32][P] i32
+    static constexpr int x_off = col_off + S::CT * 4;                      // [NG] G
+    static constexpr int w_off = x_off + NG * (int)sizeof(G);              // [NG] f32 (min-plus)
+    static constexpr int tag_off = w_off + (SEM::kMayWeight ? NG * 4 : 0);  // [NG] u8
+    static constexpr int bytes = (tag_off + NG + 15) / 16 * 16;
 };
 
 // ---------------------------------------------------------------------------
@@ -648,12 +654,15 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
 }
 
 // ---------------------------------------------------------------------------
-// chunk kernel for the value schemes at k <= 16.  Pass 1: each lane issues
-// one cp.async gather per set bit of its tiles, so all of a warp's input
-// values are in flight at once and land in shared memory in set-bit order.
-// Pass 2: the lane walks the same bits again and adds each staged value to its
-// row's register accumulator (a row word holds 32/RB rows; the row is picked
-// by a predicated select, keeping every index static).
+// chunk kernel for the value schemes at k <= 16.  Pass 1: each lane walks
+// the set bits of its tiles in one flat loop (tile words copied to lane-private
+// shared memory so a running word index can address them) and issues one
+// cp.async gather per bit, so a warp's input values are all in flight at once;
+// each staged value is tagged with its (tile, row).  Pass 2: a second flat
+// loop over the tags adds each value to its row's register accumulator (a
+// predicated select over the k rows keeps every register index static) and
+// closes tiles as the walk passes them.  Lanes with fewer set bits finish
+// early instead of idling through per-word loops.
 // ---------------------------------------------------------------------------
 template <int K, class SEM>
 __global__ void __launch_bounds__(kSpmvThreads, (K >= 16 ? 2 : 3)) spmv_gather_kernel(SpmvGeom g, SEM sem,
@@ -675,8 +684,11 @@ __global__ void __launch_bounds__(kSpmvThreads, (K >= 16 ? 2 : 3)) spmv_gather_k
     if (c >= g.nchunks) return;  // whole warps leave together
 
     uint8_t* wsm = smem + warp * L::bytes;
+    uint32_t* swords = reinterpret_cast<uint32_t*>(wsm + L::words_off) + lane * (P * TW);
+    int32_t* scol = reinterpret_cast<int32_t*>(wsm + L::col_off) + lane * P;
     G* sx = reinterpret_cast<G*>(wsm + L::x_off);
     float* sw = reinterpret_cast<float*>(wsm + L::w_off);
+    uint8_t* stag = wsm + L::tag_off;
 
     LaneSpan ls;
     ls.cs = c * S::CT;
@@ -707,24 +719,31 @@ __global__ void __launch_bounds__(kSpmvThreads, (K >= 16 ? 2 : 3)) spmv_gather_k
     const bool staged = __shfl_sync(FULL, incl, 31) <= L::NG;  // warp-uniform
 
     if (staged) {
-        int s = gbase;
 #pragma unroll
-        for (int i = 0; i < P; ++i) {
-            if (i < ls.cnt) {
-                const G* xt = sem.src() + (int64_t)col[i] * K;
-                const float* wt = sem.weighted ? sem.wts() + __ldg(sem.voffs() + ls.tl + i) : nullptr;
+        for (int q = 0; q < P * TW; ++q) swords[q] = words[q];
 #pragma unroll
-                for (int q = 0; q < TW; ++q) {
-                    uint32_t b = words[i * TW + q];
-                    while (b) {
-                        const int bit = __ffs(b) - 1;
-                        b &= b - 1;
-                        cp_async_gather<sizeof(G)>(sx + s, xt + bit % RB);
-                        if (sem.weighted) cp_async_gather<4>(sw + s, wt + (s - gbase));
-                        ++s;
-                    }
-                }
+        for (int i = 0; i < P; ++i) scol[i] = col[i];
+        int wi = 0;
+        uint32_t cur = swords[0];
+        int ti = -1, qb = 0;
+        const G* xt = nullptr;
+        const float* wt = nullptr;
+        for (int j = 0; j < nb; ++j) {
+            while (cur == 0u) cur = swords[++wi];
+            const int bit = __ffs(cur) - 1;
+            cur &= cur - 1;
+            const int i = wi / TW;
+            if (i != ti) {  // first set bit of tile i
+                ti = i;
+                qb = 0;
+                xt = sem.src() + (int64_t)scol[i] * K;
+                if (sem.weighted) wt = sem.wts() + __ldg(sem.voffs() + ls.tl + i);
             }
+            const int s = gbase + j;
+            cp_async_gather<sizeof(G)>(sx + s, xt + bit % RB);
+            if (sem.weighted) cp_async_gather<4>(sw + s, wt + qb);
+            stag[s] = (uint8_t)(i * K + (wi % TW) * RPW + bit / RB);
+            ++qb;
         }
         cp_async_commit();
     }
@@ -742,38 +761,49 @@ __global__ void __launch_bounds__(kSpmvThreads, (K >= 16 ? 2 : 3)) spmv_gather_k
         // empty tile-rows just before a row that starts at this lane's first tile
         if (ls.tl > 0 && rc.row_start == ls.tl)
             for (int32_t R = rc.row - 1; R >= 0 && (int64_t)__ldg(g.rowptr + R) == ls.tl; --R) sem.store(R, idv);
-        int s = gbase;
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-            if (i < ls.cnt) {
-                const int64_t t = ls.tl + i;
-                const G* xt = sem.src() + (int64_t)col[i] * K;
-                const float* wt = (!staged && sem.weighted) ? sem.wts() + __ldg(sem.voffs() + t) : nullptr;
-                int qb = 0;
-#pragma unroll
-                for (int q = 0; q < TW; ++q) {
-                    uint32_t b = words[i * TW + q];
-                    while (b) {
-                        const int bit = __ffs(b) - 1;
-                        b &= b - 1;
-                        G xv;
-                        float wv = 1.0f;
-                        if (staged) {
-                            xv = sx[s];
-                            if (sem.weighted) wv = sw[s];
-                        } else {
-                            xv = __ldg(xt + bit % RB);
-                            if (sem.weighted) wv = __ldg(wt + qb);
-                        }
-                        const int u = bit / RB;
-#pragma unroll
-                        for (int uu = 0; uu < RPW; ++uu)
-                            if (u == uu) acc.set(q * RPW + uu, sem.apply(acc.get(q * RPW + uu), xv, wv));
-                        ++s;
-                        ++qb;
-                    }
+        if (staged) {
+            int i = 0;
+            for (int j = 0; j < nb; ++j) {
+                const int s = gbase + j;
+                const int tag = stag[s];
+                const int ti = tag / K;
+                while (i < ti) {  // every tile has a set bit: the walk passes tile i
+                    wk.end_tile(g, sem, acc, F, ls.tl + i, i, ls.cnt, idv);
+                    ++i;
                 }
-                wk.end_tile(g, sem, acc, F, t, i, ls.cnt, idv);
+                const int r = tag % K;
+                const G xv = sx[s];
+                const float wv = sem.weighted ? sw[s] : 1.0f;
+#pragma unroll
+                for (int u = 0; u < K; ++u)
+                    if (r == u) acc.set(u, sem.apply(acc.get(u), xv, wv));
+            }
+            for (; i < ls.cnt; ++i) wk.end_tile(g, sem, acc, F, ls.tl + i, i, ls.cnt, idv);
+        } else {
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                if (i < ls.cnt) {
+                    const int64_t t = ls.tl + i;
+                    const G* xt = sem.src() + (int64_t)col[i] * K;
+                    const float* wt = sem.weighted ? sem.wts() + __ldg(sem.voffs() + t) : nullptr;
+                    int qb = 0;
+#pragma unroll
+                    for (int q = 0; q < TW; ++q) {
+                        uint32_t b = words[i * TW + q];
+                        while (b) {
+                            const int bit = __ffs(b) - 1;
+                            b &= b - 1;
+                            const G xv = __ldg(xt + bit % RB);
+                            const float wv = sem.weighted ? __ldg(wt + qb) : 1.0f;
+                            const int u = bit / RB;
+#pragma unroll
+                            for (int uu = 0; uu < RPW; ++uu)
+                                if (u == uu) acc.set(q * RPW + uu, sem.apply(acc.get(q * RPW + uu), xv, wv));
+                            ++qb;
+                        }
+                    }
+                    wk.end_tile(g, sem, acc, F, t, i, ls.cnt, idv);
+                }
             }
         }
     }
