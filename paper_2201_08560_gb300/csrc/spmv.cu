@@ -246,6 +246,7 @@ struct SemPlus {
     __device__ V comb(V a, V b) const { return a + b; }
     __device__ J jcomb(J a, J b) const { return a + b; }
     __device__ V apply(V acc, G xv, float) const { return acc + xv; }
+    __device__ V contrib(G xv, float) const { return xv; }
     template <class A>
     __device__ void store(int32_t R, const A& acc) const {
 #pragma unroll
@@ -281,6 +282,7 @@ struct SemMinPlus {
     __device__ V comb(V a, V b) const { return fminf(a, b); }
     __device__ J jcomb(J a, J b) const { return fminf(a, b); }
     __device__ V apply(V acc, G xv, float wv) const { return fminf(acc, xv + wv); }
+    __device__ V contrib(G xv, float wv) const { return xv + wv; }
     template <class A>
     __device__ void store(int32_t R, const A& acc) const {
 #pragma unroll
@@ -313,6 +315,7 @@ struct SemMinI32 {
     __device__ V comb(V a, V b) const { return min(a, b); }
     __device__ J jcomb(J a, J b) const { return min(a, b); }
     __device__ V apply(V acc, G xv, float) const { return min(acc, xv); }
+    __device__ V contrib(G xv, float) const { return xv; }
     template <class A>
     __device__ void store(int32_t R, const A& acc) const {
 #pragma unroll
@@ -345,6 +348,7 @@ struct SemOr64 {
     __device__ V comb(V a, V b) const { return a | b; }
     __device__ J jcomb(J a, J b) const { return a | b; }
     __device__ V apply(V acc, G xv, float) const { return acc | xv; }
+    __device__ V contrib(G xv, float) const { return xv; }
     template <class A>
     __device__ void store(int32_t R, const A& acc) const {
 #pragma unroll
@@ -772,11 +776,11 @@ __global__ void __launch_bounds__(kSpmvThreads, (K >= 16 ? 2 : 3)) spmv_gather_k
                     ++i;
                 }
                 const int r = tag % K;
-                const G xv = sx[s];
-                const float wv = sem.weighted ? sw[s] : 1.0f;
+                const V cv = sem.contrib(sx[s], sem.weighted ? sw[s] : 1.0f);
+                // branch-free row select: every row combines either the
+                // contribution or the identity
 #pragma unroll
-                for (int u = 0; u < K; ++u)
-                    if (r == u) acc.set(u, sem.apply(acc.get(u), xv, wv));
+                for (int u = 0; u < K; ++u) acc.set(u, sem.comb(acc.get(u), r == u ? cv : sem.ident()));
             }
             for (; i < ls.cnt; ++i) wk.end_tile(g, sem, acc, F, ls.tl + i, i, ls.cnt, idv);
         } else {
@@ -793,12 +797,11 @@ __global__ void __launch_bounds__(kSpmvThreads, (K >= 16 ? 2 : 3)) spmv_gather_k
                         while (b) {
                             const int bit = __ffs(b) - 1;
                             b &= b - 1;
-                            const G xv = __ldg(xt + bit % RB);
-                            const float wv = sem.weighted ? __ldg(wt + qb) : 1.0f;
+                            const V cv = sem.contrib(__ldg(xt + bit % RB), sem.weighted ? __ldg(wt + qb) : 1.0f);
                             const int u = bit / RB;
 #pragma unroll
                             for (int uu = 0; uu < RPW; ++uu)
-                                if (u == uu) acc.set(q * RPW + uu, sem.apply(acc.get(q * RPW + uu), xv, wv));
+                                acc.set(q * RPW + uu, sem.comb(acc.get(q * RPW + uu), u == uu ? cv : sem.ident()));
                             ++qb;
                         }
                     }
