@@ -408,8 +408,8 @@ struct GatherLayout<K, SEM, true> {
     using G = typename SEM::G;
     using S = ChunkShape<K>;
     static constexpr int NG = 512;
-    static constexpr int words_off = 0;                                    // [32][P*TW] u32
-    static constexpr int col_off = words_off + S::CT * S::TW * 4;          // [32][P] i32
+    static constexpr int words_off = 0;                                    // [P*TW][32] u32
+    static constexpr int col_off = words_off + S::CT * S::TW * 4;          // [P][32] i32
     static constexpr int x_off = col_off + S::CT * 4;                      // [NG] G
     static constexpr int w_off = x_off + NG * (int)sizeof(G);              // [NG] f32 (min-plus)
     static constexpr int tag_off = w_off + (SEM::kMayWeight ? NG * 4 : 0);  // [NG] u8
@@ -688,8 +688,9 @@ __global__ void __launch_bounds__(kSpmvThreads, (K >= 16 ? 2 : 3)) spmv_gather_k
     if (c >= g.nchunks) return;  // whole warps leave together
 
     uint8_t* wsm = smem + warp * L::bytes;
-    uint32_t* swords = reinterpret_cast<uint32_t*>(wsm + L::words_off) + lane * (P * TW);
-    int32_t* scol = reinterpret_cast<int32_t*>(wsm + L::col_off) + lane * P;
+    // lane-interleaved (element e of lane l at [e * 32 + l]): conflict-free
+    uint32_t* swords = reinterpret_cast<uint32_t*>(wsm + L::words_off) + lane;
+    int32_t* scol = reinterpret_cast<int32_t*>(wsm + L::col_off) + lane;
     G* sx = reinterpret_cast<G*>(wsm + L::x_off);
     float* sw = reinterpret_cast<float*>(wsm + L::w_off);
     uint8_t* stag = wsm + L::tag_off;
@@ -724,23 +725,23 @@ __global__ void __launch_bounds__(kSpmvThreads, (K >= 16 ? 2 : 3)) spmv_gather_k
 
     if (staged) {
 #pragma unroll
-        for (int q = 0; q < P * TW; ++q) swords[q] = words[q];
+        for (int q = 0; q < P * TW; ++q) swords[q * 32] = words[q];
 #pragma unroll
-        for (int i = 0; i < P; ++i) scol[i] = col[i];
+        for (int i = 0; i < P; ++i) scol[i * 32] = col[i];
         int wi = 0;
-        uint32_t cur = swords[0];
+        uint32_t cur = words[0];
         int ti = -1, qb = 0;
         const G* xt = nullptr;
         const float* wt = nullptr;
         for (int j = 0; j < nb; ++j) {
-            while (cur == 0u) cur = swords[++wi];
+            while (cur == 0u) cur = swords[(++wi) * 32];
             const int bit = __ffs(cur) - 1;
             cur &= cur - 1;
             const int i = wi / TW;
             if (i != ti) {  // first set bit of tile i
                 ti = i;
                 qb = 0;
-                xt = sem.src() + (int64_t)scol[i] * K;
+                xt = sem.src() + (int64_t)scol[i * 32] * K;
                 if (sem.weighted) wt = sem.wts() + __ldg(sem.voffs() + ls.tl + i);
             }
             const int s = gbase + j;
