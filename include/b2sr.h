@@ -195,6 +195,28 @@ b2sr_status b2sr_spmv(b2sr_handle h, b2sr_semiring semiring, b2sr_vec in_kind, c
 b2sr_status b2sr_spmm_bits64(b2sr_handle h, const uint64_t* X, uint64_t* Y, const uint64_t* M,
                              int complement, void* stream);
 
+/* Boolean SpMV that allocates no device memory.  The paper has no
+ * counterpart; it exists for callers that cannot allocate device memory when
+ * they call in, such as a host whose own allocator already holds the device's
+ * free memory, or a service that must not allocate once it is running.
+ * Computes exactly what b2sr_spmv computes for BOOL_OR_AND, BITS -> BITS
+ * (same x, y, mask and mask_complement meaning), but keeps its scratch (the
+ * partial rows of tile-rows that cross chunks) in a fixed 4 MiB array compiled
+ * into the library, which every device that loads the library holds until the
+ * process exits.  It calls no cudaMalloc, cudaFree or allocating routine.
+ *  - The first call on each device looks up that device's copy of the array
+ *    (cudaGetSymbolAddress) with the device current; make that first call
+ *    before any stream capture.
+ *  - Matrices needing more scratch than the array holds (more than 262,144
+ *    chunks of 256 tiles at k=8, or 524,288 chunks at k=4/16/32) are rejected
+ *    with B2SR_ERR_INVALID_ARG and a message giving both sizes.
+ *  - Every call uses the same array and leaves its contents behind.  Nothing
+ *    in it needs clearing (each call writes every value it reads), but calls
+ *    that run at the same time on the GPU (other streams, other threads)
+ *    overwrite each other's scratch: serialise them. */
+b2sr_status b2sr_spmv_bool_noalloc(b2sr_handle h, const uint32_t* x, uint32_t* y, const uint32_t* mask,
+                                   int mask_complement, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* SpGEMM: the BMM schemes of Table 3 and the Boolean product              */
 /* ---------------------------------------------------------------------- */

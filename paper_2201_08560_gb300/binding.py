@@ -55,6 +55,7 @@ def _load() -> ctypes.CDLL:
         "b2sr_weights_from_csr": (c_int, [p, p, p, p, p, p]),
         "b2sr_spmv": (c_int, [p, c_int, c_int, p, c_int, p, p, c_int, p, p]),
         "b2sr_spmm_bits64": (c_int, [p, p, p, p, c_int, p]),
+        "b2sr_spmv_bool_noalloc": (c_int, [p, p, p, p, c_int, p]),
         "b2sr_spgemm_masked_count": (c_int, [p, p, p, p, p]),
         "b2sr_spgemm_bool": (c_int, [p, p, p, pp]),
         "b2sr_bfs": (c_int, [p, i32, p, c_int, p]),
@@ -195,6 +196,14 @@ def b2sr_spmv(m: Matrix, semiring: int, in_kind: int, x: torch.Tensor, out_kind:
               weights: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     _check(lib.b2sr_spmv(m.handle, int(semiring), int(in_kind), _ptr(x), int(out_kind), _ptr(y), _ptr(mask),
                          int(bool(mask_complement)), _ptr(weights), _stream(stream)))
+    return y
+
+
+def b2sr_spmv_bool_noalloc(m: Matrix, x: torch.Tensor, y: torch.Tensor, mask: Optional[torch.Tensor] = None,
+                           mask_complement: bool = False, stream=None) -> torch.Tensor:
+    """Boolean SpMV with the library's fixed scratch array: no device allocation."""
+    _check(lib.b2sr_spmv_bool_noalloc(m.handle, _ptr(x), _ptr(y), _ptr(mask), int(bool(mask_complement)),
+                                      _stream(stream)))
     return y
 
 

@@ -22,6 +22,8 @@
 #include <algorithm>
 #include <cfloat>
 #include <climits>
+#include <mutex>
+#include <string>
 #include <type_traits>
 
 #include "b2sr_internal.cuh"
@@ -1056,4 +1058,94 @@ extern "C" b2sr_status b2sr_spmm_bits64(b2sr_handle h, const uint64_t* X, uint64
     if (h->n > 0 && (!X || !Y)) return fail(B2SR_ERR_INVALID_ARG, "X or Y is NULL");
     if (X == Y) return fail(B2SR_ERR_INVALID_ARG, "Y must not alias X");
     return spmm64_dispatch(h, X, Y, M, complement, to_stream(stream));
+}
+
+// ---------------------------------------------------------------------------
+// Boolean SpMV without device allocation.
+//
+// Some callers cannot allocate device memory when they call into the library:
+// a host whose own allocator has already reserved the device's free memory,
+// or a deployment that must not allocate once it is running (fixed-memory or
+// real-time services).  For them b2sr_spmv_bool_noalloc keeps the only scratch
+// the Boolean SpMV needs -- the per-chunk partial rows joined by the fixup
+// kernel -- in a fixed array compiled into the library.  That array exists on
+// every device that loads the library, for the life of the process.
+// ---------------------------------------------------------------------------
+namespace b2sr {
+
+constexpr size_t kNoallocScratchBytes = size_t(4) << 20;  // 4 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device (host code
+// cannot use the symbol itself as a device pointer).
+static void* noalloc_scratch_ptr(int dev, b2sr_status* st) {
+    static std::mutex mu;
+    static void* ptrs[64] = {nullptr};
+    if (dev < 0 || dev >= 64) {
+        *st = fail(B2SR_ERR_INVALID_ARG, "device index out of range for the fixed scratch");
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            *st = cuda_fail(e, "cudaGetSymbolAddress(fixed scratch)");
+            return nullptr;
+        }
+        ptrs[dev] = p;
+    }
+    *st = B2SR_OK;
+    return ptrs[dev];
+}
+
+template <int K>
+static b2sr_status run_spmv_bool_fixed(const b2sr_matrix* h, const SemBool<K>& sem, uint32_t* y, void* scratch,
+                                       cudaStream_t s) {
+    using SEM = SemBool<K>;
+    constexpr int NV = SEM::NV;
+    const size_t half = round_up((size_t)h->nchunks * NV * sizeof(uint32_t), 256);
+    if (2 * half > kNoallocScratchBytes)
+        return fail(B2SR_ERR_INVALID_ARG, "matrix too large for b2sr_spmv_bool_noalloc: " +
+                                              std::to_string(h->nchunks) + " chunks need " +
+                                              std::to_string(2 * half) + " scratch bytes, the fixed array holds " +
+                                              std::to_string(kNoallocScratchBytes));
+    SpmvGeom g{h->rowptr, h->colind, h->tiles, h->chunk_row, h->T, h->nchunks, h->ntr};
+    B2SR_TRY(clear_bitset_tail<K>(h, y, s));
+    B2SR_TRY((launch_edges<K, SEM>(h, sem, s)));
+    if (h->nchunks == 0) return B2SR_OK;
+    // every partial the fixup reads is written by the chunk kernel of the
+    // same call, so the scratch needs no clearing between calls
+    Partials<uint32_t> part;
+    part.val_first = static_cast<uint32_t*>(scratch);
+    part.val_last = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(scratch) + half);
+    spmv_chunks_kernel<K, SEM><<<(unsigned)ceil_div(h->nchunks, kSpmvWarps), kSpmvThreads, 0, s>>>(g, sem, part);
+    B2SR_LAUNCH_CHECK("spmv_chunks_kernel");
+    if (h->nchunks > 1) {
+        int fgrid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(h->nchunks - 1, 8), (int64_t)sm_count() * 16));
+        spmv_fixup_kernel<K, SEM><<<fgrid, 256, 0, s>>>(g, sem, part);
+        B2SR_LAUNCH_CHECK("spmv_fixup_kernel");
+    }
+    return B2SR_OK;
+}
+
+}  // namespace b2sr
+
+extern "C" b2sr_status b2sr_spmv_bool_noalloc(b2sr_handle h, const uint32_t* x, uint32_t* y, const uint32_t* mask,
+                                              int mask_complement, void* stream) {
+    clear_error();
+    B2SR_TRY(check_handle(h));
+    if (h->n > 0 && (!x || !y)) return fail(B2SR_ERR_INVALID_ARG, "x or y is NULL");
+    if (x == y) return fail(B2SR_ERR_INVALID_ARG, "y must not alias x");
+    int dev = 0;
+    B2SR_CUDA_TRY(cudaGetDevice(&dev));
+    b2sr_status st = B2SR_OK;
+    void* scratch = noalloc_scratch_ptr(dev, &st);
+    if (!scratch) return st;
+    const int comp = mask_complement ? 1 : 0;
+    return with_k(h->k, [&](auto kc) -> b2sr_status {
+        constexpr int K = decltype(kc)::value;
+        SemBool<K> sem{x, y, mask, comp, h->n};
+        return run_spmv_bool_fixed<K>(h, sem, y, scratch, to_stream(stream));
+    });
 }
