@@ -370,7 +370,8 @@ def main():
         d = fam[dom]
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
         traffic, _ = traffic_for(dom)
-        roofline = {"bound": "hbm", "kernel": f"spmv_chunks_kernel ({dom}, k={TILE})", "achieved": achieved,
+        kname = "spmv_gather_kernel" if dom not in ("spmv_bool", "spmv_count") and TILE <= 16 else "spmv_chunks_kernel"
+        roofline = {"bound": "hbm", "kernel": f"{kname} ({dom}, k={TILE})", "achieved": achieved,
                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                     "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
                     "avg_launch_us": d["ms"] / d["launches"] * 1e3, "launches": d["launches"],
