@@ -65,7 +65,7 @@ extern "C" b2sr_status b2sr_destroy(b2sr_handle h) {
     if (prev != h->device) cudaSetDevice(h->device);
     // all work that may still read the arrays has to finish first
     cudaError_t e = cudaDeviceSynchronize();
-    void* ptrs[] = {h->rowptr, h->colind, h->tiles, h->chunk_row, h->voff, h->outdeg};
+    void* ptrs[] = {h->rowptr, h->colind, h->tiles, h->chunk_row, h->voff, h->outdeg, h->split};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, 0);
     cudaStreamSynchronize(0);

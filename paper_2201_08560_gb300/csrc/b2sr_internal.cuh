@@ -65,6 +65,8 @@ __host__ __device__ constexpr int chunk_tiles(int k) { return 32 * tiles_per_lan
 // Arrays are padded (zero-filled) to a multiple of this many tiles so a chunk
 // can always be copied whole.
 constexpr int64_t kTilePad = 512;
+// Rows spanning more chunks than this are joined by a whole warp.
+constexpr int kSplitShort = 32;
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -115,6 +117,11 @@ struct b2sr_matrix {
     int64_t nchunks = 0;
     int32_t first_row = 0;       // tile-row of tile 0 (ntr if T == 0)
     int32_t last_row = -1;       // tile-row of tile T-1 (-1 if T == 0)
+    // tile-rows that span SpMV chunks: (row, first chunk, last chunk) triples,
+    // rows spanning at most kSplitShort chunks first, then the longer ones
+    int32_t* split = nullptr;
+    int64_t nsplit_short = 0;
+    int64_t nsplit_long = 0;
     // lazily built, cached derived arrays (built under the handle's mutex)
     int32_t* voff = nullptr;     // [T+1] set bits before each tile (weights offsets)
     int32_t* outdeg = nullptr;   // [n] ones per column

@@ -119,6 +119,73 @@ __global__ void chunk_rows_kernel(const int32_t* __restrict__ rowptr, int32_t nt
     }
 }
 
+// Tile-rows that span chunks: the row R that chunk c begins inside, when R
+// started in an earlier chunk and ends in c.  kind[c] = 1 (at most
+// kSplitShort chunks), 2 (more), 0 (none).
+__global__ void split_kind_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ chunk_row,
+                                  int64_t T, int64_t CT, int64_t nchunks, int32_t* __restrict__ kshort,
+                                  int32_t* __restrict__ klong) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int32_t ks = 0, kl = 0;
+        if (c > 0) {
+            const int64_t cs = c * CT, ce = min(cs + CT, T);
+            const int32_t R = chunk_row[c];
+            const int64_t rs = rowptr[R], re = rowptr[R + 1];
+            if (rs < cs && re <= ce) {
+                const int64_t np = c - rs / CT + 1;
+                if (np <= kSplitShort) ks = 1; else kl = 1;
+            }
+        }
+        kshort[c] = ks;
+        klong[c] = kl;
+    }
+}
+
+__global__ void split_fill_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ chunk_row,
+                                  int64_t CT, int64_t nchunks, const int32_t* __restrict__ kshort,
+                                  const int32_t* __restrict__ klong, const int64_t* __restrict__ pshort,
+                                  const int64_t* __restrict__ plong, int64_t nshort, int32_t* __restrict__ split) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (!kshort[c] && !klong[c]) continue;
+        const int32_t R = chunk_row[c];
+        const int64_t at = kshort[c] ? pshort[c] : nshort + plong[c];
+        split[3 * at] = R;
+        split[3 * at + 1] = (int32_t)(rowptr[R] / CT);
+        split[3 * at + 2] = (int32_t)c;
+    }
+}
+
+static b2sr_status build_split_list(b2sr_matrix* h, cudaStream_t s) {
+    const int64_t CT = chunk_tiles(h->k);
+    const int64_t nc = h->nchunks;
+    DevBuf ks(s), kl(s), ps(s), pl(s);
+    B2SR_TRY(ks.alloc((nc + 1) * sizeof(int32_t)));
+    B2SR_TRY(kl.alloc((nc + 1) * sizeof(int32_t)));
+    B2SR_TRY(ps.alloc((nc + 1) * sizeof(int64_t)));
+    B2SR_TRY(pl.alloc((nc + 1) * sizeof(int64_t)));
+    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nc, 256), (int64_t)sm_count() * 8));
+    split_kind_kernel<<<grid, 256, 0, s>>>(h->rowptr, h->chunk_row, h->T, CT, nc, ks.as<int32_t>(), kl.as<int32_t>());
+    B2SR_LAUNCH_CHECK("split_kind_kernel");
+    B2SR_CUDA_TRY(cudaMemsetAsync(ks.as<int32_t>() + nc, 0, sizeof(int32_t), s));
+    B2SR_CUDA_TRY(cudaMemsetAsync(kl.as<int32_t>() + nc, 0, sizeof(int32_t), s));
+    B2SR_TRY(exclusive_scan_i32_to_i64(ks.as<int32_t>(), ps.as<int64_t>(), nc + 1, s));
+    B2SR_TRY(exclusive_scan_i32_to_i64(kl.as<int32_t>(), pl.as<int64_t>(), nc + 1, s));
+    int64_t ns = 0, nl = 0;
+    B2SR_CUDA_TRY(cudaMemcpyAsync(&ns, ps.as<int64_t>() + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    B2SR_CUDA_TRY(cudaMemcpyAsync(&nl, pl.as<int64_t>() + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    B2SR_CUDA_TRY(cudaStreamSynchronize(s));
+    B2SR_TRY(dalloc(&h->split, (size_t)std::max<int64_t>(3 * (ns + nl), 3), s));
+    split_fill_kernel<<<grid, 256, 0, s>>>(h->rowptr, h->chunk_row, CT, nc, ks.as<int32_t>(), kl.as<int32_t>(),
+                                           ps.as<int64_t>(), pl.as<int64_t>(), ns, h->split);
+    B2SR_LAUNCH_CHECK("split_fill_kernel");
+    B2SR_CUDA_TRY(cudaStreamSynchronize(s));
+    h->nsplit_short = ns;
+    h->nsplit_long = nl;
+    return B2SR_OK;
+}
+
 b2sr_status build_schedule(b2sr_matrix* h, cudaStream_t s) {
     if (h->T == 0) {
         h->nchunks = 0;
@@ -138,7 +205,7 @@ b2sr_status build_schedule(b2sr_matrix* h, cudaStream_t s) {
     B2SR_CUDA_TRY(cudaStreamSynchronize(s));
     h->first_row = fr;
     h->last_row = lr;
-    return B2SR_OK;
+    return build_split_list(h, s);
 }
 
 b2sr_status new_handle_from_tiles(int32_t n, int k, int64_t T, int32_t* rowptr, int32_t* colind,

@@ -816,65 +816,74 @@ __global__ void __launch_bounds__(kSpmvThreads, (K >= 16 ? 2 : 3)) spmv_gather_k
     close_chunk(sem, part, c, ls, lane, rc.head_cs, rc.row, wk.has_end, wk.open, acc, F, P);
 }
 
-// Rows that span chunks: one warp per chunk c >= 1 whose first row began in an
-// earlier chunk and ends in c; the lanes fold the partials (lane l takes every
-// 32nd one, in order) and a fixed butterfly joins the lanes.
+// Rows that span chunks, from the handle's split list of (row, first chunk,
+// last chunk): the row's partials are the first chunk's val_last and every
+// later chunk's val_first, joined in chunk order.  Blocks [0, short_blocks)
+// give one thread to each row spanning at most kSplitShort chunks; the
+// remaining blocks give a warp to each longer row (lane l folds every 32nd
+// partial in order, then a fixed butterfly joins the lanes).
 template <int K, class SEM>
-__global__ void spmv_fixup_kernel(SpmvGeom g, SEM sem, Partials<typename SEM::V> part) {
-    using S = ChunkShape<K>;
+__global__ void spmv_fixup_kernel(const int32_t* __restrict__ split, int64_t nshort, int64_t nlong,
+                                  int64_t short_blocks, SEM sem, Partials<typename SEM::V> part) {
     using V = typename SEM::V;
     using J = typename SEM::J;
     constexpr int NV = SEM::NV;
-    const int lane = (int)lane_id();
-    const int64_t wpb = blockDim.x >> 5;
-    for (int64_t c = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5) + 1; c < g.nchunks;
-         c += (int64_t)gridDim.x * wpb) {
-        const int64_t cs = c * S::CT;
-        const int64_t ce = min(cs + (int64_t)S::CT, g.T);
-        const int32_t R = __ldg(g.chunk_row + c);
-        const int64_t rs = __ldg(g.rowptr + R), re = __ldg(g.rowptr + R + 1);
-        if (rs >= cs || re > ce) continue;  // R starts here, or does not end here
-        const int64_t ca = rs / S::CT;
-        const int64_t np = c - ca + 1;
+    if ((int64_t)blockIdx.x < short_blocks) {
+        const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (e >= nshort) return;
+        const int32_t R = split[3 * e], ca = split[3 * e + 1], cb = split[3 * e + 2];
         J acc[NV];
-        if (np <= 16) {
-            // few partials (the usual case): lane 0 joins them in order
-            if (lane == 0) {
-                RegAcc<V, NV> out;
 #pragma unroll
-                for (int v = 0; v < NV; ++v) acc[v] = (J)part.val_last[ca * NV + v];
-                for (int64_t q = ca + 1; q <= c; ++q) {
+        for (int v = 0; v < NV; ++v) acc[v] = (J)part.val_last[(int64_t)ca * NV + v];
+        for (int64_t q = ca + 1; q <= cb; ++q) {
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) acc[v] = sem.jcomb(acc[v], (J)part.val_first[q * NV + v]);
-                }
-#pragma unroll
-                for (int v = 0; v < NV; ++v) out.set(v, (V)acc[v]);
-                sem.store(R, out);
-            }
-            continue;
+            for (int v = 0; v < NV; ++v) acc[v] = sem.jcomb(acc[v], (J)part.val_first[q * NV + v]);
         }
+        RegAcc<V, NV> out;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] = (J)sem.ident();
-        for (int64_t p = lane; p < np; p += 32) {
-            const V* src = p == 0 ? part.val_last + ca * NV : part.val_first + (ca + p) * NV;
+        for (int v = 0; v < NV; ++v) out.set(v, (V)acc[v]);
+        sem.store(R, out);
+        return;
+    }
+    const int lane = (int)lane_id();
+    const int64_t e = nshort + ((int64_t)(blockIdx.x - short_blocks) * blockDim.x + threadIdx.x) / 32;
+    if (e >= nshort + nlong) return;  // whole warps leave together
+    const int32_t R = split[3 * e], ca = split[3 * e + 1], cb = split[3 * e + 2];
+    const int64_t np = (int64_t)cb - ca + 1;
+    J acc[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) acc[v] = sem.jcomb(acc[v], (J)src[v]);
-        }
+    for (int v = 0; v < NV; ++v) acc[v] = (J)sem.ident();
+    for (int64_t p = lane; p < np; p += 32) {
+        const V* src = p == 0 ? part.val_last + (int64_t)ca * NV : part.val_first + (ca + p) * NV;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
+        for (int v = 0; v < NV; ++v) acc[v] = sem.jcomb(acc[v], (J)src[v]);
+    }
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const J other = __shfl_xor_sync(0xffffffffu, acc[v], o);
-                acc[v] = (lane & o) ? sem.jcomb(other, acc[v]) : sem.jcomb(acc[v], other);
-            }
-        }
-        if (lane == 0) {
-            RegAcc<V, NV> out;
+    for (int o = 1; o < 32; o <<= 1) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) out.set(v, (V)acc[v]);
-            sem.store(R, out);
+        for (int v = 0; v < NV; ++v) {
+            const J other = __shfl_xor_sync(0xffffffffu, acc[v], o);
+            acc[v] = (lane & o) ? sem.jcomb(other, acc[v]) : sem.jcomb(acc[v], other);
         }
     }
+    if (lane == 0) {
+        RegAcc<V, NV> out;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) out.set(v, (V)acc[v]);
+        sem.store(R, out);
+    }
+}
+
+template <int K, class SEM>
+static b2sr_status launch_fixup(const b2sr_matrix* h, const SEM& sem, Partials<typename SEM::V> part,
+                                cudaStream_t s) {
+    if (h->nsplit_short + h->nsplit_long == 0) return B2SR_OK;
+    const int64_t short_blocks = ceil_div(h->nsplit_short, 256);
+    const int64_t long_blocks = ceil_div(h->nsplit_long, 8);
+    spmv_fixup_kernel<K, SEM><<<(unsigned)(short_blocks + long_blocks), 256, 0, s>>>(
+        h->split, h->nsplit_short, h->nsplit_long, short_blocks, sem, part);
+    B2SR_LAUNCH_CHECK("spmv_fixup_kernel");
+    return B2SR_OK;
 }
 
 // Tile-rows before the first tile and after the last one (every row when the
@@ -958,13 +967,7 @@ static b2sr_status run_spmv(const b2sr_matrix* h, const SEM& sem, uint32_t* bits
         timing_end(tok, family, spmv_bytes(h, vec_bytes), s);
         B2SR_LAUNCH_CHECK("spmv_chunks_kernel");
     }
-    if (h->nchunks > 1) {
-        const int64_t warps = h->nchunks - 1;
-        int fgrid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(warps, 8), (int64_t)sm_count() * 16));
-        spmv_fixup_kernel<K, SEM><<<fgrid, 256, 0, s>>>(g, sem, part);
-        B2SR_LAUNCH_CHECK("spmv_fixup_kernel");
-    }
-    return B2SR_OK;
+    return launch_fixup<K, SEM>(h, sem, part, s);
 }
 
 template <class F>
@@ -1121,12 +1124,7 @@ static b2sr_status run_spmv_bool_fixed(const b2sr_matrix* h, const SemBool<K>& s
     part.val_last = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(scratch) + half);
     spmv_chunks_kernel<K, SEM><<<(unsigned)ceil_div(h->nchunks, kSpmvWarps), kSpmvThreads, 0, s>>>(g, sem, part);
     B2SR_LAUNCH_CHECK("spmv_chunks_kernel");
-    if (h->nchunks > 1) {
-        int fgrid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(h->nchunks - 1, 8), (int64_t)sm_count() * 16));
-        spmv_fixup_kernel<K, SEM><<<fgrid, 256, 0, s>>>(g, sem, part);
-        B2SR_LAUNCH_CHECK("spmv_fixup_kernel");
-    }
-    return B2SR_OK;
+    return launch_fixup<K, SEM>(h, sem, part, s);
 }
 
 }  // namespace b2sr
