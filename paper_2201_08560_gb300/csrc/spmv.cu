@@ -415,7 +415,8 @@ struct GatherLayout<K, SEM, true> {
     static constexpr int x_off = col_off + S::CT * 4;                      // [NG] G
     static constexpr int w_off = x_off + NG * (int)sizeof(G);              // [NG] f32 (min-plus)
     static constexpr int tag_off = w_off + (SEM::kMayWeight ? NG * 4 : 0);  // [NG] u8
-    static constexpr int bytes = (tag_off + NG + 15) / 16 * 16;
+    static constexpr int pre_off = (tag_off + NG + 15) / 16 * 16;           // [P][32] i32: first slot of each tile
+    static constexpr int bytes = pre_off + S::CT * 4;
 };
 
 // ---------------------------------------------------------------------------
@@ -723,9 +724,21 @@ __global__ void __launch_bounds__(kSpmvThreads, (K >= 16 ? 2 : 3)) spmv_gather_k
         if (lane >= d) incl += o;
     }
     const int gbase = incl - nb;
-    const bool staged = __shfl_sync(FULL, incl, 31) <= L::NG;  // warp-uniform
+    const int nbits = __shfl_sync(FULL, incl, 31);
+    const bool staged = nbits <= L::NG;  // warp-uniform
 
     if (staged) {
+        // first staging slot of each of the lane's tiles
+        int32_t* spre = reinterpret_cast<int32_t*>(wsm + L::pre_off) + lane;
+        int run = gbase;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            spre[i * 32] = run;
+            if (i < ls.cnt) {
+#pragma unroll
+                for (int q = 0; q < TW; ++q) run += __popc(words[i * TW + q]);
+            }
+        }
 #pragma unroll
         for (int q = 0; q < P * TW; ++q) swords[q * 32] = words[q];
 #pragma unroll
@@ -755,10 +768,78 @@ __global__ void __launch_bounds__(kSpmvThreads, (K >= 16 ? 2 : 3)) spmv_gather_k
         cp_async_commit();
     }
 
-    const RowCursor rc = locate_row(g, c, ls, lane);
-    RegAcc<V, NV> acc, F, idv;
+    RegAcc<V, NV> idv;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) { acc.set(v, sem.ident()); F.set(v, sem.ident()); idv.set(v, sem.ident()); }
+    for (int v = 0; v < NV; ++v) idv.set(v, sem.ident());
+
+    // ---- fast path: a staged chunk spanning at most four tile-rows.  Each
+    // tile-row's staged values (contiguous slots, tile order) are dealt to
+    // the lanes round-robin, summed in registers, and joined by a fixed
+    // butterfly, so no lane waits on another's bit count.
+    {
+        const int32_t r0 = __ldg(g.chunk_row + c);
+        const int32_t span = __ldg(g.chunk_row + c + 1) - r0;
+        if (staged && span <= 3) {
+            const int64_t win = lane <= span + 1 ? (int64_t)__ldg(g.rowptr + r0 + lane) : INT64_MAX;
+            cp_async_wait_all();
+            __syncwarp();  // values, tags and slot starts of every lane are visible
+            const int32_t* pre = reinterpret_cast<const int32_t*>(wsm + L::pre_off);
+            auto slot_of = [&](int64_t t) -> int {  // first slot of chunk tile t (nbits at the chunk end)
+                if (t >= ls.ce) return nbits;
+                const int64_t o = t - ls.cs;
+                return pre[(int)(o % P) * 32 + (int)(o / P)];
+            };
+            const int64_t a0 = __shfl_sync(FULL, win, 0);
+            if (lane == 0 && a0 == ls.cs && ls.cs > 0)  // empty rows just before the chunk's first tile-row
+                for (int32_t R = r0 - 1; R >= 0 && (int64_t)__ldg(g.rowptr + R) == ls.cs; --R) sem.store(R, idv);
+            for (int j = 0; j <= span; ++j) {
+                const int32_t R = r0 + j;
+                const int64_t a = __shfl_sync(FULL, win, j), b = __shfl_sync(FULL, win, j + 1);
+                if (a == b) {  // empty tile-row inside the chunk's range
+                    if (lane == 0 && a >= ls.cs && a < ls.ce && a > 0) sem.store(R, idv);
+                    continue;
+                }
+                const int64_t ts = max(a, ls.cs), te = min(b, ls.ce);
+                if (ts >= te) continue;  // its tiles lie outside this chunk
+                const int s0 = slot_of(ts), s1 = slot_of(te);
+                RegAcc<V, NV> acc;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) acc.set(v, sem.ident());
+                for (int sidx = s0 + lane; sidx < s1; sidx += 32) {
+                    const int r = stag[sidx] % K;
+                    const V cv = sem.contrib(sx[sidx], sem.weighted ? sw[sidx] : 1.0f);
+#pragma unroll
+                    for (int u = 0; u < K; ++u) acc.set(u, sem.comb(acc.get(u), r == u ? cv : sem.ident()));
+                }
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        const V other = __shfl_xor_sync(FULL, acc.get(v), o);
+                        acc.set(v, (lane & o) ? sem.comb(other, acc.get(v)) : sem.comb(acc.get(v), other));
+                    }
+                }
+                if (lane == 0) {
+                    const bool started = a >= ls.cs, ended = b <= ls.ce;
+                    if (started && ended) {
+                        sem.store(R, acc);
+                    } else if (!started) {
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) part.val_first[c * NV + v] = acc.get(v);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) part.val_last[c * NV + v] = acc.get(v);
+                    }
+                }
+            }
+            return;
+        }
+    }
+
+    const RowCursor rc = locate_row(g, c, ls, lane);
+    RegAcc<V, NV> acc, F;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { acc.set(v, sem.ident()); F.set(v, sem.ident()); }
     Walk<SEM, RegAcc<V, NV>> wk;
     wk.row = rc.row;
     wk.next = rc.next;
