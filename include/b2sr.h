@@ -208,7 +208,8 @@ b2sr_status b2sr_spmm_bits64(b2sr_handle h, const uint64_t* X, uint64_t* Y, cons
  *    (cudaGetSymbolAddress) with the device current; make that first call
  *    before any stream capture.
  *  - Matrices needing more scratch than the array holds (more than 262,144
- *    chunks of 256 tiles at k=8, or 524,288 chunks at k=4/16/32) are rejected
+ *    chunks at k=8, or 524,288 at k=4/16/32; a chunk is 256 tiles at k=4/8,
+ *    128 at k=16, 64 at k=32) are rejected
  *    with B2SR_ERR_INVALID_ARG and a message giving both sizes.
  *  - Every call uses the same array and leaves its contents behind.  Nothing
  *    in it needs clearing (each call writes every value it reads), but calls

@@ -56,10 +56,10 @@ __host__ __device__ inline int word_bytes(int k) { return k <= 8 ? 1 : (k == 16 
 __host__ __device__ inline int tile_bytes(int k) { return k * word_bytes(k); }
 inline bool valid_tile(int k) { return k == 4 || k == 8 || k == 16 || k == 32; }
 
-// Tiles per warp-chunk of the SpMV kernels: 32 lanes x P tiles, P = 512/(32 k)
-// rounded so one chunk holds 2-8 KB of tile data.
+// Tiles per warp-chunk of the SpMV kernels: 32 lanes x P tiles, P = 8, 8, 4, 2
+// for k = 4, 8, 16, 32 (1-8 KB of tile data per chunk).
 __host__ __device__ constexpr int tiles_per_lane(int k) {
-    return k == 4 ? 16 : (k == 8 ? 8 : (k == 16 ? 4 : 2));
+    return k <= 8 ? 8 : (k == 16 ? 4 : 2);
 }
 __host__ __device__ constexpr int chunk_tiles(int k) { return 32 * tiles_per_lane(k); }
 // Arrays are padded (zero-filled) to a multiple of this many tiles so a chunk
