@@ -117,6 +117,24 @@ const char* b2sr_version(void);
 b2sr_status b2sr_from_csr(int32_t n, const int32_t* rowptr, const int32_t* colind, int64_t nnz,
                           int tile_dim, void* stream, b2sr_handle* out);
 
+/* Many graphs in one B2SR arena: graph g's CSR is placed on the diagonal at
+ * rows and columns [base[g], base[g] + n_g), with base[g] a multiple of 32, so
+ * that its tiles never share a tile-row or a bitset word with another graph.
+ * The result is one block-diagonal matrix on which every SpMV and driver runs
+ * all graphs in the same launches (the batching the paper has no counterpart
+ * for; Sec. III-A storage applied to the union).
+ *   ngraphs   >= 1
+ *   n_host    host int32[ngraphs] vertex counts (0 allowed)
+ *   rowptrs   host array of ngraphs device int32[n_g+1] pointers
+ *   colinds   host array of ngraphs device int32[nnz_g] pointers (ids local)
+ *   nnz_host  host int64[ngraphs]
+ *   base_host host int64[ngraphs+1] (written): offsets, base[ngraphs] = arena n
+ * Fails with B2SR_ERR_INVALID_ARG when the arena reaches 2^31 rows or entries;
+ * otherwise as b2sr_from_csr.  Synchronises `stream`. */
+b2sr_status b2sr_from_csr_batch(int ngraphs, const int32_t* n_host, const int32_t* const* rowptrs,
+                                const int32_t* const* colinds, const int64_t* nnz_host, int tile_dim,
+                                void* stream, b2sr_handle* out, int64_t* base_host);
+
 /* B2SR -> CSR (sorted, duplicate-free rows): the inverse of b2sr_from_csr.
  *   rowptr   device int32[n+1] (written)
  *   colind   device int32[nnz] (written) or NULL to query only
@@ -243,8 +261,22 @@ b2sr_status b2sr_spgemm_bool(b2sr_handle A, b2sr_handle B, void* stream, b2sr_ha
 /* BFS levels from `src` (Sec. V BFS: Boolean semiring, the visited set as a
  * complemented mask).  levels device int32[n]: 0 at src, -1 if unreachable.
  * At most max_iters levels (<= 0: n); B2SR_ERR_NOT_CONVERGED if exceeded.
- * Synchronises `stream` once per batch of levels. */
+ * Synchronises `stream` once per four levels (see b2sr_bfs_sources). */
 b2sr_status b2sr_bfs(b2sr_handle h, int32_t src, int32_t* levels, int max_iters, void* stream);
+
+/* BFS from a set of sources, all at level 0 (Sec. V BFS with the first
+ * frontier holding every source).  levels[v] is the distance from v to the
+ * nearest source, -1 if none reaches it.  On a matrix built by
+ * b2sr_from_csr_batch with one source per graph, graph g's levels are
+ * levels[base[g] .. base[g] + n_g) and equal a BFS of graph g alone, since
+ * no edge joins two graphs: one call runs every graph's BFS at once.
+ *   srcs_host host int32[nsrc], nsrc >= 1, each in [0, n), repeats allowed
+ *   levels    device int32[n]
+ * Level rounds run as a CUDA graph of four gated rounds replayed until a
+ * round finds no new vertex: one host synchronisation per four levels.
+ * B2SR_ERR_NOT_CONVERGED past max_iters levels (<= 0: n). */
+b2sr_status b2sr_bfs_sources(b2sr_handle h, const int32_t* srcs_host, int nsrc, int32_t* levels,
+                             int max_iters, void* stream);
 
 /* Multi-source BFS: up to 64 BFS runs of Sec. V advance together, their
  * frontiers packed as one uint64 per vertex (b2sr_spmm_bits64).
@@ -257,7 +289,8 @@ b2sr_status b2sr_bfs_multi(b2sr_handle h, const int32_t* srcs_host, int nsrc, in
  * relaxation, d <- min(d, A min.+ d), until no distance changes (the fixed
  * point delta-stepping also reaches).  weights in set-bit order
  * (b2sr_weights_from_csr), non-negative, or NULL for unit weights.
- * dist device float[n]: 0 at src, +inf if unreachable. */
+ * dist device float[n]: 0 at src, +inf if unreachable.  Rounds run as a CUDA
+ * graph of 16 gated rounds: one host synchronisation per 16 rounds. */
 b2sr_status b2sr_sssp(b2sr_handle h, const float* weights, int32_t src, float* dist, int max_iters,
                       void* stream);
 

@@ -60,6 +60,8 @@ def _load() -> ctypes.CDLL:
         "b2sr_spgemm_bool": (c_int, [p, p, p, pp]),
         "b2sr_bfs": (c_int, [p, i32, p, c_int, p]),
         "b2sr_bfs_multi": (c_int, [p, p, c_int, p, c_int, p]),
+        "b2sr_bfs_sources": (c_int, [p, p, c_int, p, c_int, p]),
+        "b2sr_from_csr_batch": (c_int, [c_int, p, p, p, p, c_int, p, pp, p]),
         "b2sr_sssp": (c_int, [p, p, i32, p, c_int, p]),
         "b2sr_pagerank": (c_int, [p, f32, c_int, p, p, p]),
         "b2sr_cc": (c_int, [p, p, c_int, p]),
@@ -153,6 +155,21 @@ def b2sr_from_csr(n: int, rowptr: torch.Tensor, colind: torch.Tensor, tile_dim: 
     return Matrix(h)
 
 
+def b2sr_from_csr_batch(graphs_csr: Sequence, tile_dim: int, stream=None):
+    """Block-diagonal arena of several graphs.  graphs_csr: (n, rowptr, colind)
+    per graph with device int32 tensors.  Returns (Matrix, bases) where bases
+    is a list of ngraphs+1 row offsets."""
+    g = len(graphs_csr)
+    ns = (ctypes.c_int32 * g)(*[int(n) for n, _, _ in graphs_csr])
+    rps = (ctypes.c_void_p * g)(*[_ptr(rp) for _, rp, _ in graphs_csr])
+    cis = (ctypes.c_void_p * g)(*[_ptr(ci) for _, _, ci in graphs_csr])
+    nnz = (ctypes.c_int64 * g)(*[int(ci.numel()) for _, _, ci in graphs_csr])
+    bases = (ctypes.c_int64 * (g + 1))()
+    h = ctypes.c_void_p()
+    _check(lib.b2sr_from_csr_batch(g, ns, rps, cis, nnz, int(tile_dim), _stream(stream), ctypes.byref(h), bases))
+    return Matrix(h), list(bases)
+
+
 def b2sr_to_csr(m: Matrix, stream=None):
     dev = torch.device("cuda", torch.cuda.current_device())
     rowptr = torch.empty(m.n + 1, dtype=torch.int32, device=dev)
@@ -244,6 +261,16 @@ def b2sr_bfs(m: Matrix, src: int, levels: Optional[torch.Tensor] = None, max_ite
     if levels is None:
         levels = torch.empty(max(m.n, 1), dtype=torch.int32, device=_dev())
     _check(lib.b2sr_bfs(m.handle, int(src), _ptr(levels), int(max_iters), _stream(stream)))
+    return levels[: m.n]
+
+
+def b2sr_bfs_sources(m: Matrix, srcs: Sequence[int], levels: Optional[torch.Tensor] = None, max_iters: int = 0,
+                     stream=None) -> torch.Tensor:
+    srcs = [int(s) for s in srcs]
+    arr = (ctypes.c_int32 * len(srcs))(*srcs)
+    if levels is None:
+        levels = torch.empty(max(m.n, 1), dtype=torch.int32, device=_dev())
+    _check(lib.b2sr_bfs_sources(m.handle, arr, len(srcs), _ptr(levels), int(max_iters), _stream(stream)))
     return levels[: m.n]
 
 

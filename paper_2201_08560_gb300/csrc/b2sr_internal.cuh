@@ -22,6 +22,7 @@ b2sr_status cuda_fail(cudaError_t e, const char* what);
 
 // telemetry (telemetry.cu): launch counter and optional per-family event timing
 void note_launch();
+void note_launches(long long n);
 bool timing_on();
 // Records events around one launch of `family` moving `bytes` algorithmic bytes;
 // call timing_begin before and timing_end after the launch (no-ops when off).

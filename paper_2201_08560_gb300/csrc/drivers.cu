@@ -1,10 +1,15 @@
 // Graph algorithms over B2SR (Sec. V): BFS (Boolean semiring, visited set as a
-// complemented output mask), multi-source BFS (64 frontiers per machine word),
-// SSSP (min-plus relaxation rounds), PageRank (plus-times with the
-// column-stochastic matrix), connected components (FastSV hooking and
-// shortcutting around the min step) and triangle counting (masked SpGEMM on
-// the lower triangle).  Each driver loops on the host, one SpMV plus one
-// element-wise kernel per iteration, with an iteration cap.
+// complemented output mask), BFS from a set of sources (which also runs many
+// graphs packed block-diagonally in one arena), multi-source BFS (64 frontiers
+// per machine word), SSSP (min-plus relaxation rounds), PageRank (plus-times
+// with the column-stochastic matrix), connected components (FastSV hooking
+// and shortcutting around the min step) and triangle counting (masked SpGEMM
+// on the lower triangle).
+//
+// Level-synchronous loops are captured once as a CUDA graph of several rounds;
+// each round's kernels are gated on a device flag that the round's update
+// kernel clears when nothing changes, and the graph is replayed until the host
+// reads the flag as 0.  One host synchronisation covers several rounds.
 #include <algorithm>
 #include <climits>
 #include <vector>
@@ -13,9 +18,10 @@
 
 namespace b2sr {
 b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, const void* x, b2sr_vec out_kind,
-                          void* y, const uint32_t* mask, int comp, const float* weights, cudaStream_t s);
+                          void* y, const uint32_t* mask, int comp, const float* weights, cudaStream_t s,
+                          const int32_t* gate);
 b2sr_status spmm64_dispatch(b2sr_matrix* h, const uint64_t* X, uint64_t* Y, const uint64_t* M, int comp,
-                            cudaStream_t s);
+                            cudaStream_t s, const int32_t* gate);
 b2sr_status masked_count(const b2sr_matrix* A, const b2sr_matrix* B, const b2sr_matrix* M, int64_t* count,
                          cudaStream_t s);
 
@@ -38,66 +44,157 @@ static b2sr_status read_flag(const int32_t* dev, HostFlag& hf, cudaStream_t s, i
     return B2SR_OK;
 }
 
+__device__ __forceinline__ bool gate_closed(const int32_t* gate) { return gate && *gate == 0; }
+
 // ---------------------------------------------------------------------------
-// BFS
+// captured round loop
 // ---------------------------------------------------------------------------
-__global__ void bfs_init_kernel(int32_t* levels, int32_t n, int32_t src, uint32_t* frontier, uint32_t* visited,
-                                int64_t words) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n || i < words;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        if (i < n) levels[i] = (i == src) ? 0 : -1;
-        if (i < words) {
-            uint32_t w = (i == (src >> 5)) ? (1u << (src & 31)) : 0u;
-            frontier[i] = w;
-            visited[i] = w;
+// Enqueues `per_graph` rounds (body(stream, r)) into one CUDA graph on a
+// private stream, then replays it until *active reads 0.  Every round must be
+// gated on *active.  Returns in *rounds the rounds replayed; B2SR_ERR_NOT_CONVERGED
+// if *active is still set after max_rounds.
+template <class Body>
+static b2sr_status run_captured(cudaStream_t user, int per_graph, int64_t max_rounds, const int32_t* active,
+                                Body&& body, int64_t* rounds) {
+    *rounds = 0;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    HostFlag hf;
+    auto cleanup = [&](b2sr_status st) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) {
+            if (ev) {  // the caller's stream waits for everything enqueued here
+                cudaEventRecord(ev, cs);
+                cudaStreamWaitEvent(user, ev, 0);
+            }
+            cudaStreamDestroy(cs);
         }
+        if (ev) cudaEventDestroy(ev);
+        return st;
+    };
+    B2SR_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaEventCreate"));
+    e = cudaEventRecord(ev, user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "order capture stream"));
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamBeginCapture"));
+    const int64_t l0 = b2sr_launch_count();
+    b2sr_status st = B2SR_OK;
+    for (int r = 0; r < per_graph && st == B2SR_OK; ++r) st = body(cs, r);
+    e = cudaStreamEndCapture(cs, &graph);
+    if (st != B2SR_OK) return cleanup(st);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamEndCapture"));
+    const int64_t per_replay = b2sr_launch_count() - l0;
+    note_launches(-per_replay);  // counted again per replay below
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaGraphInstantiate"));
+    for (;;) {
+        e = cudaGraphLaunch(exec, cs);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaGraphLaunch"));
+        note_launches(per_replay);
+        *rounds += per_graph;
+        int32_t got = 0;
+        st = read_flag(active, hf, cs, &got);
+        if (st != B2SR_OK) return cleanup(st);
+        if (!got) return cleanup(B2SR_OK);
+        if (*rounds >= max_rounds) return cleanup(fail(B2SR_ERR_NOT_CONVERGED, "exceeded max_iters rounds"));
     }
 }
 
-// visited |= next; levels[v] = level for every new vertex; count new vertices
+// active <- found (only while active); level counter advances with it
+__global__ void advance_kernel(int32_t* active, const int32_t* found, int32_t* level) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && *active) {
+        *active = *found;
+        *level += 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// BFS from a set of sources (all at level 0)
+// ---------------------------------------------------------------------------
+__global__ void bfs_init_kernel(int32_t* levels, int32_t n, uint32_t* frontier, uint32_t* visited, int64_t words) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n || i < words;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < n) levels[i] = -1;
+        if (i < words) { frontier[i] = 0u; visited[i] = 0u; }
+    }
+}
+
+__global__ void bfs_seed_kernel(const int32_t* srcs, int nsrc, int32_t* levels, uint32_t* frontier,
+                                uint32_t* visited) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsrc; i += gridDim.x * blockDim.x) {
+        const int32_t v = srcs[i];
+        levels[v] = 0;
+        atomicOr(frontier + (v >> 5), 1u << (v & 31));
+        atomicOr(visited + (v >> 5), 1u << (v & 31));
+    }
+}
+
+// visited |= next; levels[v] = level+1 for every new vertex; found if any
 __global__ void bfs_update_kernel(const uint32_t* __restrict__ next, uint32_t* __restrict__ visited,
-                                  int32_t* __restrict__ levels, int64_t words, int32_t level, int32_t* any) {
-    int found = 0;
+                                  int32_t* __restrict__ levels, int64_t words, const int32_t* level,
+                                  const int32_t* gate, int32_t* found) {
+    if (gate_closed(gate)) return;
+    const int32_t lv = *level + 1;
+    int any = 0;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
          w += (int64_t)gridDim.x * blockDim.x) {
         uint32_t b = next[w];
         if (!b) continue;
-        found = 1;
+        any = 1;
         visited[w] |= b;
         while (b) {
             int c = __ffs(b) - 1;
             b &= b - 1;
-            levels[w * 32 + c] = level;
+            levels[w * 32 + c] = lv;
         }
     }
-    if (__syncthreads_or(found) && threadIdx.x == 0) atomicOr(any, 1);
+    if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(found, 1);
 }
 
-b2sr_status bfs(b2sr_matrix* h, int32_t src, int32_t* levels, int max_iters, cudaStream_t s) {
+b2sr_status bfs_sources(b2sr_matrix* h, const int32_t* srcs_host, int nsrc, int32_t* levels, int max_iters,
+                        cudaStream_t s) {
     const int32_t n = h->n;
     const int64_t words = ceil_div(n, 32);
     DevBuf buf(s);
-    B2SR_TRY(buf.alloc(3 * words * sizeof(uint32_t) + 16));
-    uint32_t* f = buf.as<uint32_t>();
-    uint32_t* nx = f + words;
-    uint32_t* vis = nx + words;
-    int32_t* any = reinterpret_cast<int32_t*>(vis + words);
-    bfs_init_kernel<<<grid_for(std::max<int64_t>(n, words)), 256, 0, s>>>(levels, n, src, f, vis, words);
+    B2SR_TRY(buf.alloc(3 * words * sizeof(uint32_t) + (size_t)(nsrc + 8) * sizeof(int32_t)));
+    uint32_t* fa = buf.as<uint32_t>();
+    uint32_t* fb = fa + words;
+    uint32_t* vis = fb + words;
+    int32_t* flags = reinterpret_cast<int32_t*>(vis + words);  // active, found, level
+    int32_t* dsrc = flags + 8;
+    B2SR_CUDA_TRY(cudaMemcpyAsync(dsrc, srcs_host, nsrc * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    bfs_init_kernel<<<grid_for(std::max<int64_t>(n, words)), 256, 0, s>>>(levels, n, fa, vis, words);
     B2SR_LAUNCH_CHECK("bfs_init_kernel");
-    HostFlag hf;
-    const int cap = max_iters > 0 ? max_iters : n;
-    for (int level = 1; level <= cap + 1; ++level) {
-        B2SR_TRY(spmv_dispatch(h, B2SR_BOOL_OR_AND, B2SR_VEC_BITS, f, B2SR_VEC_BITS, nx, vis, 1, nullptr, s));
-        B2SR_CUDA_TRY(cudaMemsetAsync(any, 0, sizeof(int32_t), s));
-        bfs_update_kernel<<<grid_for(words), 256, 0, s>>>(nx, vis, levels, words, level, any);
-        B2SR_LAUNCH_CHECK("bfs_update_kernel");
-        int32_t got = 0;
-        B2SR_TRY(read_flag(any, hf, s, &got));
-        if (!got) return B2SR_OK;
-        if (level > cap) break;
-        std::swap(f, nx);
-    }
-    return fail(B2SR_ERR_NOT_CONVERGED, "BFS exceeded max_iters levels");
+    bfs_seed_kernel<<<(unsigned)ceil_div(nsrc, 256), 256, 0, s>>>(dsrc, nsrc, levels, fa, vis);
+    B2SR_LAUNCH_CHECK("bfs_seed_kernel");
+    const int32_t init[3] = {1, 0, 0};
+    B2SR_CUDA_TRY(cudaMemcpyAsync(flags, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    int32_t* active = flags;
+    int32_t* found = flags + 1;
+    int32_t* level = flags + 2;
+    const int64_t cap = max_iters > 0 ? max_iters : (int64_t)n + 1;
+    int64_t rounds = 0;
+    return run_captured(s, 4, cap + 1, active,
+                        [&](cudaStream_t cs, int r) -> b2sr_status {
+                            uint32_t* f = (r & 1) ? fb : fa;
+                            uint32_t* nx = (r & 1) ? fa : fb;
+                            B2SR_TRY(spmv_dispatch(h, B2SR_BOOL_OR_AND, B2SR_VEC_BITS, f, B2SR_VEC_BITS, nx, vis, 1,
+                                                   nullptr, cs, active));
+                            B2SR_CUDA_TRY(cudaMemsetAsync(found, 0, sizeof(int32_t), cs));
+                            bfs_update_kernel<<<grid_for(words), 256, 0, cs>>>(nx, vis, levels, words, level, active,
+                                                                               found);
+                            B2SR_LAUNCH_CHECK("bfs_update_kernel");
+                            advance_kernel<<<1, 32, 0, cs>>>(active, found, level);
+                            B2SR_LAUNCH_CHECK("advance_kernel");
+                            return B2SR_OK;
+                        },
+                        &rounds);
 }
 
 // ---------------------------------------------------------------------------
@@ -124,97 +221,112 @@ __global__ void msbfs_seed_kernel(const int32_t* srcs, int nsrc, int32_t n, int3
 }
 
 __global__ void msbfs_update_kernel(const unsigned long long* __restrict__ Y, unsigned long long* __restrict__ vis,
-                                    int32_t* __restrict__ levels, int32_t n, int32_t level, int32_t* any) {
-    int found = 0;
+                                    int32_t* __restrict__ levels, int32_t n, const int32_t* level,
+                                    const int32_t* gate, int32_t* found) {
+    if (gate_closed(gate)) return;
+    const int32_t lv = *level + 1;
+    int any = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         unsigned long long b = Y[v];
         if (!b) continue;
-        found = 1;
+        any = 1;
         vis[v] |= b;
         while (b) {
             int s = __ffsll((long long)b) - 1;
             b &= b - 1;
-            levels[(int64_t)s * n + v] = level;
+            levels[(int64_t)s * n + v] = lv;
         }
     }
-    if (__syncthreads_or(found) && threadIdx.x == 0) atomicOr(any, 1);
+    if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(found, 1);
 }
 
 b2sr_status bfs_multi(b2sr_matrix* h, const int32_t* srcs_host, int nsrc, int32_t* levels, int max_iters,
                       cudaStream_t s) {
     const int32_t n = h->n;
     DevBuf buf(s);
-    B2SR_TRY(buf.alloc(3 * (size_t)n * sizeof(uint64_t) + 64 * sizeof(int32_t) + 16));
+    B2SR_TRY(buf.alloc(3 * (size_t)n * sizeof(uint64_t) + 72 * sizeof(int32_t)));
     unsigned long long* X = buf.as<unsigned long long>();
-    unsigned long long* Y = X + n;
-    unsigned long long* vis = Y + n;
+    unsigned long long* Yb = X + n;
+    unsigned long long* vis = Yb + n;
     int32_t* dsrc = reinterpret_cast<int32_t*>(vis + n);
-    int32_t* any = dsrc + 64;
+    int32_t* flags = dsrc + 64;  // active, found, level
     B2SR_CUDA_TRY(cudaMemcpyAsync(dsrc, srcs_host, nsrc * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     msbfs_init_kernel<<<grid_for((int64_t)n * nsrc), 256, 0, s>>>(levels, n, nsrc, X, vis);
     B2SR_LAUNCH_CHECK("msbfs_init_kernel");
     msbfs_seed_kernel<<<1, 64, 0, s>>>(dsrc, nsrc, n, levels, X, vis);
     B2SR_LAUNCH_CHECK("msbfs_seed_kernel");
-    HostFlag hf;
-    const int cap = max_iters > 0 ? max_iters : n;
-    for (int level = 1; level <= cap + 1; ++level) {
-        B2SR_TRY(spmm64_dispatch(h, reinterpret_cast<uint64_t*>(X), reinterpret_cast<uint64_t*>(Y),
-                                 reinterpret_cast<uint64_t*>(vis), 1, s));
-        B2SR_CUDA_TRY(cudaMemsetAsync(any, 0, sizeof(int32_t), s));
-        msbfs_update_kernel<<<grid_for(n), 256, 0, s>>>(Y, vis, levels, n, level, any);
-        B2SR_LAUNCH_CHECK("msbfs_update_kernel");
-        int32_t got = 0;
-        B2SR_TRY(read_flag(any, hf, s, &got));
-        if (!got) return B2SR_OK;
-        if (level > cap) break;
-        std::swap(X, Y);
-    }
-    return fail(B2SR_ERR_NOT_CONVERGED, "multi-source BFS exceeded max_iters levels");
+    const int32_t init[3] = {1, 0, 0};
+    B2SR_CUDA_TRY(cudaMemcpyAsync(flags, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    int32_t* active = flags;
+    int32_t* found = flags + 1;
+    int32_t* level = flags + 2;
+    const int64_t cap = max_iters > 0 ? max_iters : (int64_t)n + 1;
+    int64_t rounds = 0;
+    return run_captured(s, 4, cap + 1, active,
+                        [&](cudaStream_t cs, int r) -> b2sr_status {
+                            unsigned long long* cur = (r & 1) ? Yb : X;
+                            unsigned long long* nxt = (r & 1) ? X : Yb;
+                            B2SR_TRY(spmm64_dispatch(h, reinterpret_cast<uint64_t*>(cur), reinterpret_cast<uint64_t*>(nxt),
+                                                     reinterpret_cast<uint64_t*>(vis), 1, cs, active));
+                            B2SR_CUDA_TRY(cudaMemsetAsync(found, 0, sizeof(int32_t), cs));
+                            msbfs_update_kernel<<<grid_for(n), 256, 0, cs>>>(nxt, vis, levels, n, level, active, found);
+                            B2SR_LAUNCH_CHECK("msbfs_update_kernel");
+                            advance_kernel<<<1, 32, 0, cs>>>(active, found, level);
+                            B2SR_LAUNCH_CHECK("advance_kernel");
+                            return B2SR_OK;
+                        },
+                        &rounds);
 }
 
 // ---------------------------------------------------------------------------
-// SSSP: y = min(d, A min.+ d) until no distance changes
+// SSSP: d <- min(d, A min.+ d) until no distance changes
 // ---------------------------------------------------------------------------
 __global__ void sssp_init_kernel(float* d, int32_t n, int32_t src) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         d[i] = (i == src) ? 0.0f : INFINITY;
 }
 
-__global__ void changed_kernel(const float* __restrict__ a, const float* __restrict__ b, int32_t n, int32_t* any) {
+// found if a distance changed; the round's result becomes the current vector
+__global__ void sssp_update_kernel(const float* __restrict__ nxt, float* __restrict__ cur, int32_t n,
+                                   const int32_t* gate, int32_t* found) {
+    if (gate_closed(gate)) return;
     int diff = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        diff |= (a[i] != b[i]);
-    if (__syncthreads_or(diff) && threadIdx.x == 0) atomicOr(any, 1);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = nxt[i];
+        if (v != cur[i]) { diff = 1; cur[i] = v; }
+    }
+    if (__syncthreads_or(diff) && threadIdx.x == 0) atomicOr(found, 1);
 }
 
 b2sr_status sssp(b2sr_matrix* h, const float* w, int32_t src, float* dist, int max_iters, cudaStream_t s) {
     const int32_t n = h->n;
+    if (w) B2SR_TRY(ensure_voff(h, s));  // built before capture: capture must not allocate for the handle
     DevBuf buf(s);
     B2SR_TRY(buf.alloc((size_t)n * sizeof(float) + 16));
     float* tmp = buf.as<float>();
-    int32_t* any = reinterpret_cast<int32_t*>(tmp + n);
+    int32_t* flags = reinterpret_cast<int32_t*>(tmp + n);
     sssp_init_kernel<<<grid_for(n), 256, 0, s>>>(dist, n, src);
     B2SR_LAUNCH_CHECK("sssp_init_kernel");
-    HostFlag hf;
-    float* cur = dist;
-    float* nxt = tmp;
-    const int cap = max_iters > 0 ? max_iters : n;
-    for (int it = 0; it <= cap; ++it) {
-        B2SR_TRY(spmv_dispatch(h, B2SR_MIN_PLUS, B2SR_VEC_F32, cur, B2SR_VEC_F32, nxt, nullptr, 0, w, s));
-        B2SR_CUDA_TRY(cudaMemsetAsync(any, 0, sizeof(int32_t), s));
-        changed_kernel<<<grid_for(n), 256, 0, s>>>(cur, nxt, n, any);
-        B2SR_LAUNCH_CHECK("changed_kernel");
-        int32_t got = 0;
-        B2SR_TRY(read_flag(any, hf, s, &got));
-        std::swap(cur, nxt);
-        if (!got) {
-            if (cur != dist) B2SR_CUDA_TRY(cudaMemcpyAsync(dist, cur, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, s));
-            return B2SR_OK;
-        }
-    }
-    if (cur != dist) B2SR_CUDA_TRY(cudaMemcpyAsync(dist, cur, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    return fail(B2SR_ERR_NOT_CONVERGED, "SSSP exceeded max_iters rounds");
+    const int32_t init[3] = {1, 0, 0};
+    B2SR_CUDA_TRY(cudaMemcpyAsync(flags, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    int32_t* active = flags;
+    int32_t* found = flags + 1;
+    int32_t* level = flags + 2;
+    const int64_t cap = max_iters > 0 ? max_iters : (int64_t)n + 1;
+    int64_t rounds = 0;
+    return run_captured(s, 16, cap + 1, active,
+                        [&](cudaStream_t cs, int) -> b2sr_status {
+                            B2SR_TRY(spmv_dispatch(h, B2SR_MIN_PLUS, B2SR_VEC_F32, dist, B2SR_VEC_F32, tmp, nullptr, 0, w,
+                                                   cs, active));
+                            B2SR_CUDA_TRY(cudaMemsetAsync(found, 0, sizeof(int32_t), cs));
+                            sssp_update_kernel<<<grid_for(n), 256, 0, cs>>>(tmp, dist, n, active, found);
+                            B2SR_LAUNCH_CHECK("sssp_update_kernel");
+                            advance_kernel<<<1, 32, 0, cs>>>(active, found, level);
+                            B2SR_LAUNCH_CHECK("advance_kernel");
+                            return B2SR_OK;
+                        },
+                        &rounds);
 }
 
 // ---------------------------------------------------------------------------
@@ -255,7 +367,7 @@ b2sr_status pagerank(b2sr_matrix* h, float damp, int iters, const float* tele, f
     pr_init_kernel<<<grid_for(n), 256, 0, s>>>(pr, c, h->outdeg, n);
     B2SR_LAUNCH_CHECK("pr_init_kernel");
     for (int it = 0; it < iters; ++it) {
-        B2SR_TRY(spmv_dispatch(h, B2SR_PLUS_TIMES, B2SR_VEC_F32, c, B2SR_VEC_F32, y, nullptr, 0, nullptr, s));
+        B2SR_TRY(spmv_dispatch(h, B2SR_PLUS_TIMES, B2SR_VEC_F32, c, B2SR_VEC_F32, y, nullptr, 0, nullptr, s, nullptr));
         pr_step_kernel<<<grid_for(n), 256, 0, s>>>(y, tele, h->outdeg, damp, n, pr, c);
         B2SR_LAUNCH_CHECK("pr_step_kernel");
     }
@@ -316,7 +428,7 @@ b2sr_status cc(b2sr_matrix* h, int32_t* labels, int max_iters, cudaStream_t s) {
     HostFlag hf;
     const int cap = max_iters > 0 ? max_iters : n;
     for (int it = 0; it <= cap; ++it) {
-        B2SR_TRY(spmv_dispatch(h, B2SR_MIN_PLUS, B2SR_VEC_I32, gf, B2SR_VEC_I32, mngf, nullptr, 0, nullptr, s));
+        B2SR_TRY(spmv_dispatch(h, B2SR_MIN_PLUS, B2SR_VEC_I32, gf, B2SR_VEC_I32, mngf, nullptr, 0, nullptr, s, nullptr));
         cc_hook_kernel<<<grid_for(n), 256, 0, s>>>(f, mngf, n);
         B2SR_LAUNCH_CHECK("cc_hook_kernel");
         cc_short_kernel<<<grid_for(n), 256, 0, s>>>(f, mngf, gf, n);
@@ -332,6 +444,25 @@ b2sr_status cc(b2sr_matrix* h, int32_t* labels, int max_iters, cudaStream_t s) {
     return fail(B2SR_ERR_NOT_CONVERGED, "CC exceeded max_iters rounds");
 }
 
+// ---------------------------------------------------------------------------
+// many graphs in one block-diagonal arena
+// ---------------------------------------------------------------------------
+// rowptr of graph g placed at rows [base, base + ng), padding rows after it
+// empty; its column ids shifted by base.
+__global__ void arena_rows_kernel(const int32_t* __restrict__ rp, int32_t ng, int32_t base, int32_t npad,
+                                  int64_t eoff, int32_t* __restrict__ out_rp) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out_rp[base + i] = (int32_t)(eoff + rp[i < ng ? i : ng]);
+}
+
+__global__ void arena_cols_kernel(const int32_t* __restrict__ ci, int64_t nnz, int32_t base,
+                                  int32_t* __restrict__ out_ci) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x)
+        out_ci[e] = ci[e] + base;
+}
+
 }  // namespace b2sr
 
 using namespace b2sr;
@@ -341,7 +472,17 @@ extern "C" b2sr_status b2sr_bfs(b2sr_handle h, int32_t src, int32_t* levels, int
     B2SR_TRY(check_handle(h));
     if (src < 0 || src >= h->n) return fail(B2SR_ERR_INVALID_ARG, "source out of range");
     if (!levels) return fail(B2SR_ERR_INVALID_ARG, "levels is NULL");
-    return bfs(h, src, levels, max_iters, to_stream(stream));
+    return bfs_sources(h, &src, 1, levels, max_iters, to_stream(stream));
+}
+
+extern "C" b2sr_status b2sr_bfs_sources(b2sr_handle h, const int32_t* srcs_host, int nsrc, int32_t* levels,
+                                        int max_iters, void* stream) {
+    clear_error();
+    B2SR_TRY(check_handle(h));
+    if (nsrc < 1 || !srcs_host || !levels) return fail(B2SR_ERR_INVALID_ARG, "need at least one source and levels");
+    for (int i = 0; i < nsrc; ++i)
+        if (srcs_host[i] < 0 || srcs_host[i] >= h->n) return fail(B2SR_ERR_INVALID_ARG, "source out of range");
+    return bfs_sources(h, srcs_host, nsrc, levels, max_iters, to_stream(stream));
 }
 
 extern "C" b2sr_status b2sr_bfs_multi(b2sr_handle h, const int32_t* srcs_host, int nsrc, int32_t* levels,
@@ -389,4 +530,48 @@ extern "C" b2sr_status b2sr_tc(b2sr_handle h, int64_t* count, void* stream) {
     b2sr_status st = masked_count(L, L, L, count, to_stream(stream));
     b2sr_destroy(L);
     return st;
+}
+
+extern "C" b2sr_status b2sr_from_csr_batch(int ngraphs, const int32_t* n_host, const int32_t* const* rowptrs,
+                                           const int32_t* const* colinds, const int64_t* nnz_host, int tile_dim,
+                                           void* stream, b2sr_handle* out, int64_t* base_host) {
+    clear_error();
+    if (!out) return fail(B2SR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (ngraphs < 1 || !n_host || !rowptrs || !colinds || !nnz_host || !base_host)
+        return fail(B2SR_ERR_INVALID_ARG, "null pointer or no graphs");
+    if (!valid_tile(tile_dim)) return fail(B2SR_ERR_UNSUPPORTED_TILE, "tile_dim must be 4, 8, 16 or 32");
+    cudaStream_t s = to_stream(stream);
+    int64_t N = 0, NNZ = 0;
+    for (int g = 0; g < ngraphs; ++g) {
+        if (n_host[g] < 0 || nnz_host[g] < 0 || !rowptrs[g] || (nnz_host[g] > 0 && !colinds[g]))
+            return fail(B2SR_ERR_INVALID_ARG, "bad graph " + std::to_string(g));
+        base_host[g] = N;
+        N += round_up(n_host[g], 32);
+        NNZ += nnz_host[g];
+    }
+    base_host[ngraphs] = N;
+    if (N >= (int64_t(1) << 31) || NNZ >= (int64_t(1) << 31)) return fail(B2SR_ERR_INVALID_ARG, "arena too large");
+    DevBuf rp(s), ci(s);
+    B2SR_TRY(rp.alloc((N + 1) * sizeof(int32_t)));
+    B2SR_TRY(ci.alloc(std::max<int64_t>(NNZ, 1) * sizeof(int32_t)));
+    int64_t eoff = 0;
+    for (int g = 0; g < ngraphs; ++g) {
+        const int32_t npad = (int32_t)round_up(n_host[g], 32);
+        if (npad > 0) {
+            arena_rows_kernel<<<grid_for(npad), 256, 0, s>>>(rowptrs[g], n_host[g], (int32_t)base_host[g], npad, eoff,
+                                                            rp.as<int32_t>());
+            B2SR_LAUNCH_CHECK("arena_rows_kernel");
+        }
+        if (nnz_host[g] > 0) {
+            arena_cols_kernel<<<grid_for(nnz_host[g]), 256, 0, s>>>(colinds[g], nnz_host[g], (int32_t)base_host[g],
+                                                                   ci.as<int32_t>() + eoff);
+            B2SR_LAUNCH_CHECK("arena_cols_kernel");
+        }
+        eoff += nnz_host[g];
+    }
+    const int32_t last = (int32_t)NNZ;
+    B2SR_CUDA_TRY(cudaMemcpyAsync(rp.as<int32_t>() + N, &last, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    B2SR_CUDA_TRY(cudaStreamSynchronize(s));  // `last` lives on this stack frame
+    return b2sr_from_csr((int32_t)N, rp.as<int32_t>(), ci.as<int32_t>(), NNZ, tile_dim, stream, out);
 }

@@ -376,7 +376,12 @@ struct SpmvGeom {
     int64_t T;
     int64_t nchunks;
     int32_t ntr;
+    // optional device flag: when it reads 0 the launch does nothing (lets a
+    // captured loop of SpMVs run past the point where its driver is done)
+    const int32_t* gate;
 };
+
+__device__ __forceinline__ bool gated_off(const int32_t* gate) { return gate && *gate == 0; }
 
 template <class V>
 struct Partials {
@@ -600,7 +605,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
     const int warp = threadIdx.x >> 5;
     const int lane = (int)lane_id();
     const int64_t c = (int64_t)blockIdx.x * kSpmvWarps + warp;
-    if (c >= g.nchunks) return;  // whole warps leave together
+    if (c >= g.nchunks || gated_off(g.gate)) return;  // whole warps leave together
 
     LaneSpan ls;
     ls.cs = c * S::CT;
@@ -688,7 +693,7 @@ __global__ void __launch_bounds__(kSpmvThreads, (K >= 16 ? 2 : 3)) spmv_gather_k
     const int warp = threadIdx.x >> 5;
     const int lane = (int)lane_id();
     const int64_t c = (int64_t)blockIdx.x * kSpmvWarps + warp;
-    if (c >= g.nchunks) return;  // whole warps leave together
+    if (c >= g.nchunks || gated_off(g.gate)) return;  // whole warps leave together
 
     uint8_t* wsm = smem + warp * L::bytes;
     // lane-interleaved (element e of lane l at [e * 32 + l]): conflict-free
@@ -905,10 +910,12 @@ __global__ void __launch_bounds__(kSpmvThreads, (K >= 16 ? 2 : 3)) spmv_gather_k
 // partial in order, then a fixed butterfly joins the lanes).
 template <int K, class SEM>
 __global__ void spmv_fixup_kernel(const int32_t* __restrict__ split, int64_t nshort, int64_t nlong,
-                                  int64_t short_blocks, SEM sem, Partials<typename SEM::V> part) {
+                                  int64_t short_blocks, SEM sem, Partials<typename SEM::V> part,
+                                  const int32_t* gate) {
     using V = typename SEM::V;
     using J = typename SEM::J;
     constexpr int NV = SEM::NV;
+    if (gated_off(gate)) return;
     if ((int64_t)blockIdx.x < short_blocks) {
         const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         if (e >= nshort) return;
@@ -957,12 +964,12 @@ __global__ void spmv_fixup_kernel(const int32_t* __restrict__ split, int64_t nsh
 
 template <int K, class SEM>
 static b2sr_status launch_fixup(const b2sr_matrix* h, const SEM& sem, Partials<typename SEM::V> part,
-                                cudaStream_t s) {
+                                cudaStream_t s, const int32_t* gate) {
     if (h->nsplit_short + h->nsplit_long == 0) return B2SR_OK;
     const int64_t short_blocks = ceil_div(h->nsplit_short, 256);
     const int64_t long_blocks = ceil_div(h->nsplit_long, 8);
     spmv_fixup_kernel<K, SEM><<<(unsigned)(short_blocks + long_blocks), 256, 0, s>>>(
-        h->split, h->nsplit_short, h->nsplit_long, short_blocks, sem, part);
+        h->split, h->nsplit_short, h->nsplit_long, short_blocks, sem, part, gate);
     B2SR_LAUNCH_CHECK("spmv_fixup_kernel");
     return B2SR_OK;
 }
@@ -970,8 +977,10 @@ static b2sr_status launch_fixup(const b2sr_matrix* h, const SEM& sem, Partials<t
 // Tile-rows before the first tile and after the last one (every row when the
 // matrix has no tiles) get the identity.
 template <int K, class SEM>
-__global__ void spmv_edges_kernel(SEM sem, int32_t lead_end, int32_t trail_begin, int32_t ntr) {
+__global__ void spmv_edges_kernel(SEM sem, int32_t lead_end, int32_t trail_begin, int32_t ntr,
+                                  const int32_t* gate) {
     using V = typename SEM::V;
+    if (gated_off(gate)) return;
     RegAcc<V, SEM::NV> idv;
 #pragma unroll
     for (int v = 0; v < SEM::NV; ++v) idv.set(v, sem.ident());
@@ -995,13 +1004,13 @@ static b2sr_status clear_bitset_tail(const b2sr_matrix* h, uint32_t* bits, cudaS
 }
 
 template <int K, class SEM>
-static b2sr_status launch_edges(const b2sr_matrix* h, const SEM& sem, cudaStream_t s) {
+static b2sr_status launch_edges(const b2sr_matrix* h, const SEM& sem, cudaStream_t s, const int32_t* gate) {
     int32_t lead_end = h->T == 0 ? h->ntr : h->first_row;
     int32_t trail_begin = h->T == 0 ? h->ntr : h->last_row + 1;
     int64_t work = (int64_t)lead_end + (h->ntr - trail_begin);
     if (work <= 0) return B2SR_OK;
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), (int64_t)sm_count() * 4));
-    spmv_edges_kernel<K, SEM><<<grid, 256, 0, s>>>(sem, lead_end, trail_begin, h->ntr);
+    spmv_edges_kernel<K, SEM><<<grid, 256, 0, s>>>(sem, lead_end, trail_begin, h->ntr, gate);
     B2SR_LAUNCH_CHECK("spmv_edges_kernel");
     return B2SR_OK;
 }
@@ -1024,11 +1033,11 @@ static double spmv_bytes(const b2sr_matrix* h, double vec_bytes) {
 
 template <int K, class SEM>
 static b2sr_status run_spmv(const b2sr_matrix* h, const SEM& sem, uint32_t* bits_out, cudaStream_t s,
-                            const char* family, double vec_bytes) {
+                            const char* family, double vec_bytes, const int32_t* gate) {
     using V = typename SEM::V;
-    SpmvGeom g{h->rowptr, h->colind, h->tiles, h->chunk_row, h->T, h->nchunks, h->ntr};
+    SpmvGeom g{h->rowptr, h->colind, h->tiles, h->chunk_row, h->T, h->nchunks, h->ntr, gate};
     if (bits_out) B2SR_TRY(clear_bitset_tail<K>(h, bits_out, s));
-    B2SR_TRY((launch_edges<K, SEM>(h, sem, s)));
+    B2SR_TRY((launch_edges<K, SEM>(h, sem, s, gate)));
     if (h->nchunks == 0) return B2SR_OK;
     DevBuf pbuf(s);
     Partials<V> part;
@@ -1048,7 +1057,7 @@ static b2sr_status run_spmv(const b2sr_matrix* h, const SEM& sem, uint32_t* bits
         timing_end(tok, family, spmv_bytes(h, vec_bytes), s);
         B2SR_LAUNCH_CHECK("spmv_chunks_kernel");
     }
-    return launch_fixup<K, SEM>(h, sem, part, s);
+    return launch_fixup<K, SEM>(h, sem, part, s, gate);
 }
 
 template <class F>
@@ -1063,14 +1072,15 @@ static b2sr_status with_k(int k, F&& f) {
 }
 
 b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, const void* x, b2sr_vec out_kind,
-                          void* y, const uint32_t* mask, int comp, const float* weights, cudaStream_t s) {
+                          void* y, const uint32_t* mask, int comp, const float* weights, cudaStream_t s,
+                          const int32_t* gate) {
     comp = comp ? 1 : 0;
     if (sr == B2SR_BOOL_OR_AND && in_kind == B2SR_VEC_BITS && out_kind == B2SR_VEC_BITS) {
         if (weights) return fail(B2SR_ERR_INVALID_ARG, "weights apply to MIN_PLUS only");
         return with_k(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
             SemBool<K> sem{static_cast<const uint32_t*>(x), static_cast<uint32_t*>(y), mask, comp, h->n};
-            return run_spmv<K>(h, sem, static_cast<uint32_t*>(y), s, "spmv_bool", (mask ? 3.0 : 2.0) * h->n / 8.0);
+            return run_spmv<K>(h, sem, static_cast<uint32_t*>(y), s, "spmv_bool", (mask ? 3.0 : 2.0) * h->n / 8.0, gate);
         });
     }
     if (sr == B2SR_PLUS_TIMES && in_kind == B2SR_VEC_BITS && out_kind == B2SR_VEC_I32) {
@@ -1078,7 +1088,7 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
         return with_k(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
             SemCount<K> sem{static_cast<const uint32_t*>(x), static_cast<int32_t*>(y), mask, comp, h->n};
-            return run_spmv<K>(h, sem, nullptr, s, "spmv_count", (mask ? 2.0 : 1.0) * h->n / 8.0 + 4.0 * h->n);
+            return run_spmv<K>(h, sem, nullptr, s, "spmv_count", (mask ? 2.0 : 1.0) * h->n / 8.0 + 4.0 * h->n, gate);
         });
     }
     if (sr == B2SR_PLUS_TIMES && in_kind == B2SR_VEC_F32 && out_kind == B2SR_VEC_F32) {
@@ -1086,7 +1096,7 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
         return with_k(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
             SemPlus<K> sem{static_cast<const float*>(x), static_cast<float*>(y), mask, comp, h->n};
-            return run_spmv<K>(h, sem, nullptr, s, "spmv_plus", 8.0 * h->n + (mask ? h->n / 8.0 : 0.0));
+            return run_spmv<K>(h, sem, nullptr, s, "spmv_plus", 8.0 * h->n + (mask ? h->n / 8.0 : 0.0), gate);
         });
     }
     if (sr == B2SR_MIN_PLUS && in_kind == B2SR_VEC_F32 && out_kind == B2SR_VEC_F32) {
@@ -1097,7 +1107,7 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
                               h->voff, weights != nullptr};
             return run_spmv<K>(h, sem, nullptr, s, "spmv_minplus",
                                8.0 * h->n + (mask ? h->n / 8.0 : 0.0) +
-                                   (weights ? 4.0 * (double)h->nnz + 4.0 * (double)h->T : 0.0));
+                                   (weights ? 4.0 * (double)h->nnz + 4.0 * (double)h->T : 0.0), gate);
         });
     }
     if (sr == B2SR_MIN_PLUS && in_kind == B2SR_VEC_I32 && out_kind == B2SR_VEC_I32) {
@@ -1105,19 +1115,19 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
         return with_k(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
             SemMinI32<K> sem{static_cast<const int32_t*>(x), static_cast<int32_t*>(y), mask, comp, h->n};
-            return run_spmv<K>(h, sem, nullptr, s, "spmv_min_i32", 8.0 * h->n + (mask ? h->n / 8.0 : 0.0));
+            return run_spmv<K>(h, sem, nullptr, s, "spmv_min_i32", 8.0 * h->n + (mask ? h->n / 8.0 : 0.0), gate);
         });
     }
     return fail(B2SR_ERR_INVALID_ARG, "unsupported semiring / vector kind combination");
 }
 
 b2sr_status spmm64_dispatch(b2sr_matrix* h, const uint64_t* X, uint64_t* Y, const uint64_t* M, int comp,
-                            cudaStream_t s) {
+                            cudaStream_t s, const int32_t* gate) {
     return with_k(h->k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
         SemOr64<K> sem{reinterpret_cast<const unsigned long long*>(X), reinterpret_cast<unsigned long long*>(Y),
                        reinterpret_cast<const unsigned long long*>(M), comp ? 1 : 0, h->n};
-        return run_spmv<K>(h, sem, nullptr, s, "spmm_or64", (M ? 24.0 : 16.0) * h->n);
+        return run_spmv<K>(h, sem, nullptr, s, "spmm_or64", (M ? 24.0 : 16.0) * h->n, gate);
     });
 }
 
@@ -1132,7 +1142,8 @@ extern "C" b2sr_status b2sr_spmv(b2sr_handle h, b2sr_semiring semiring, b2sr_vec
     B2SR_TRY(check_handle(h));
     if (h->n > 0 && (!x || !y)) return fail(B2SR_ERR_INVALID_ARG, "x or y is NULL");
     if (x == y) return fail(B2SR_ERR_INVALID_ARG, "y must not alias x");
-    return spmv_dispatch(h, semiring, in_kind, x, out_kind, y, mask, mask_complement, weights, to_stream(stream));
+    return spmv_dispatch(h, semiring, in_kind, x, out_kind, y, mask, mask_complement, weights, to_stream(stream),
+                         nullptr);
 }
 
 extern "C" b2sr_status b2sr_spmm_bits64(b2sr_handle h, const uint64_t* X, uint64_t* Y, const uint64_t* M,
@@ -1141,7 +1152,7 @@ extern "C" b2sr_status b2sr_spmm_bits64(b2sr_handle h, const uint64_t* X, uint64
     B2SR_TRY(check_handle(h));
     if (h->n > 0 && (!X || !Y)) return fail(B2SR_ERR_INVALID_ARG, "X or Y is NULL");
     if (X == Y) return fail(B2SR_ERR_INVALID_ARG, "Y must not alias X");
-    return spmm64_dispatch(h, X, Y, M, complement, to_stream(stream));
+    return spmm64_dispatch(h, X, Y, M, complement, to_stream(stream), nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1194,9 +1205,9 @@ static b2sr_status run_spmv_bool_fixed(const b2sr_matrix* h, const SemBool<K>& s
                                               std::to_string(h->nchunks) + " chunks need " +
                                               std::to_string(2 * half) + " scratch bytes, the fixed array holds " +
                                               std::to_string(kNoallocScratchBytes));
-    SpmvGeom g{h->rowptr, h->colind, h->tiles, h->chunk_row, h->T, h->nchunks, h->ntr};
+    SpmvGeom g{h->rowptr, h->colind, h->tiles, h->chunk_row, h->T, h->nchunks, h->ntr, nullptr};
     B2SR_TRY(clear_bitset_tail<K>(h, y, s));
-    B2SR_TRY((launch_edges<K, SEM>(h, sem, s)));
+    B2SR_TRY((launch_edges<K, SEM>(h, sem, s, nullptr)));
     if (h->nchunks == 0) return B2SR_OK;
     // every partial the fixup reads is written by the chunk kernel of the
     // same call, so the scratch needs no clearing between calls
@@ -1205,7 +1216,7 @@ static b2sr_status run_spmv_bool_fixed(const b2sr_matrix* h, const SemBool<K>& s
     part.val_last = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(scratch) + half);
     spmv_chunks_kernel<K, SEM><<<(unsigned)ceil_div(h->nchunks, kSpmvWarps), kSpmvThreads, 0, s>>>(g, sem, part);
     B2SR_LAUNCH_CHECK("spmv_chunks_kernel");
-    return launch_fixup<K, SEM>(h, sem, part, s);
+    return launch_fixup<K, SEM>(h, sem, part, s, nullptr);
 }
 
 }  // namespace b2sr

@@ -25,8 +25,15 @@ static std::vector<TimedLaunch> g_records;
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 bool timing_on() { return g_timing.load(std::memory_order_relaxed); }
 
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 void* timing_begin(cudaStream_t s) {
     if (!timing_on()) return nullptr;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return nullptr;  // launches inside a captured graph are not timed one by one
+    }
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
     cudaEventRecord(e, s);
