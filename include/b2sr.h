@@ -82,11 +82,24 @@ typedef enum {
     B2SR_VEC_F32 = 2   /* float[n] */
 } b2sr_vec;
 
+/* SpMV kernel schedule for the value schemes (plus-times on floats, min-plus,
+ * b2sr_spmm_bits64) at tile_dim <= 16; the Boolean and count schemes and
+ * tile_dim 32 have one schedule.  Both give identical results (the same
+ * fixed reduction order); they differ only in speed, which depends on the
+ * graph (b2sr_autotune measures it).  The paper stages the dense vector
+ * segment of a tile in shared memory (Sec. IV); STAGED is that idea for a
+ * gather per set bit, DIRECT reads the vector from global memory. */
+typedef enum {
+    B2SR_SCHED_AUTO = 0,   /* STAGED where it exists */
+    B2SR_SCHED_STAGED = 1, /* set-bit gathers staged in shared memory (cp.async), then reduced */
+    B2SR_SCHED_DIRECT = 2  /* each lane walks its tiles and loads x directly */
+} b2sr_schedule;
+
 typedef struct {
     int32_t n;           /* vertices (rows = columns) */
     int32_t tile_dim;    /* k */
     int32_t n_tile_rows; /* ceil(n/k) */
-    int32_t reserved;
+    int32_t schedule;    /* b2sr_schedule of the handle */
     int64_t n_tiles;     /* T, non-empty tiles */
     int64_t nnz;         /* set bits = distinct stored entries */
     int64_t bytes;       /* 4(nTileRow+1) + 4T + T*k*word_bytes (Sec. III-C sizes) */
@@ -144,6 +157,11 @@ b2sr_status b2sr_to_csr(b2sr_handle h, int32_t* rowptr, int32_t* colind, int64_t
 
 /* Sizes of a handle (host struct). */
 b2sr_status b2sr_info(b2sr_handle h, b2sr_info_t* info);
+
+/* Selects the handle's SpMV schedule (b2sr_schedule; the vector staging of
+ * Sec. IV or direct loads); B2SR_ERR_INVALID_ARG for another value.  Not synchronised with SpMVs in flight on other host
+ * threads; the next SpMV enqueued uses it. */
+b2sr_status b2sr_set_schedule(b2sr_handle h, int schedule);
 
 /* Device pointers to the handle's three arrays (owned by the handle; valid
  * until b2sr_destroy).  BitTiles is returned as bytes. */
@@ -253,6 +271,50 @@ b2sr_status b2sr_spgemm_masked_count(b2sr_handle A, b2sr_handle B, b2sr_handle M
  * tile_dim (not in the paper's Table 3; built from the same tile products):
  * C_IJ[r] = OR_K OR_{m: bit m of A_IK[r]} B_KJ[m].  Synchronises `stream`. */
 b2sr_status b2sr_spgemm_bool(b2sr_handle A, b2sr_handle B, void* stream, b2sr_handle* C);
+
+/* ---------------------------------------------------------------------- */
+/* Tile size selection (Sec. III-C, Algorithm 1)                           */
+/* ---------------------------------------------------------------------- */
+
+/* Sampling profile (Sec. III-C, Algorithm 1).  Every sampled row i stands for
+ * its tile-row i/k; the mean number of distinct tile columns over the sampled
+ * tile-rows, times nTileRow, estimates the tile count T_k, and
+ *   est[q] = (4(nTileRow+1) + T_k (4 + k word_bytes)) / (4(n+1) + 8 nnz)
+ * estimates the B2SR size over the fp32 CSR size, for k = 4, 8, 16, 32
+ * (q = 0..3).  Exact (T_k = T) when every row is sampled once and k divides n.
+ *   rowptr, colind device CSR (as b2sr_from_csr; rows need not be sorted)
+ *   sample_host    host int32[nsample] rows in [0, n), repeats allowed; the
+ *                  caller draws them (nsample <= 2^28)
+ *   est_host, tiles_est_host host double[4] (either may be NULL)
+ * B2SR_ERR_INVALID_ARG for a row out of range or a malformed rowptr at a
+ * sampled tile-row.  Synchronises `stream`. */
+b2sr_status b2sr_sample_profile(int32_t n, const int32_t* rowptr, const int32_t* colind, int64_t nnz,
+                                const int32_t* sample_host, int64_t nsample, double* est_host,
+                                double* tiles_est_host, void* stream);
+
+typedef struct {
+    double est_ratio[4];   /* b2sr_sample_profile estimates, k = 4, 8, 16, 32 */
+    double est_tiles[4];
+    double trial_us[4][2]; /* mean SpMV time per (k, schedule slot), -1 where not tried;
+                              slot 0 = STAGED (or the only schedule), slot 1 = DIRECT */
+    int64_t tiles[4];      /* tile count of each converted candidate, -1 if not converted */
+    int32_t tile_dim;      /* the chosen k */
+    int32_t schedule;      /* the chosen b2sr_schedule */
+} b2sr_tune_report_t;
+
+/* Autotuner: the Sec. III-C tile size choice, with the Algorithm 1 estimate as
+ * a pre-filter and measured SpMV time as the decision.  k is a candidate if
+ * est_ratio[k] <= keep_ratio * min est_ratio (keep_ratio <= 0: every k;
+ * 0 < keep_ratio < 1 is B2SR_ERR_INVALID_ARG).  Each candidate is converted
+ * and timed over `trials` SpMVs of the (sr, in_kind) scheme on a fixed
+ * synthetic vector, under each schedule it has (b2sr_schedule); the fastest
+ * handle is returned in *out with that schedule set, the others destroyed.
+ * The timings are taken on `stream` while other work may share the device,
+ * so the choice is a measurement, not a guarantee.  Synchronises `stream`. */
+b2sr_status b2sr_autotune(int32_t n, const int32_t* rowptr, const int32_t* colind, int64_t nnz,
+                          const int32_t* sample_host, int64_t nsample, b2sr_semiring sr, b2sr_vec in_kind,
+                          double keep_ratio, int trials, void* stream, b2sr_handle* out,
+                          b2sr_tune_report_t* report);
 
 /* ---------------------------------------------------------------------- */
 /* Graph algorithms (Sec. V)                                               */

@@ -32,8 +32,19 @@ class B2SRError(RuntimeError):
 
 class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("tile_dim", ctypes.c_int32), ("n_tile_rows", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("n_tiles", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("schedule", ctypes.c_int32), ("n_tiles", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("bytes", ctypes.c_int64)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("est_ratio", ctypes.c_double * 4), ("est_tiles", ctypes.c_double * 4),
+                ("trial_us", (ctypes.c_double * 2) * 4), ("tiles", ctypes.c_int64 * 4),
+                ("tile_dim", ctypes.c_int32), ("schedule", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"est_ratio": list(self.est_ratio), "est_tiles": list(self.est_tiles),
+                "trial_us": [list(r) for r in self.trial_us], "tiles": list(self.tiles),
+                "tile_dim": self.tile_dim, "schedule": self.schedule}
 
 
 def _load() -> ctypes.CDLL:
@@ -58,6 +69,10 @@ def _load() -> ctypes.CDLL:
         "b2sr_spmv_bool_noalloc": (c_int, [p, p, p, p, c_int, p]),
         "b2sr_spgemm_masked_count": (c_int, [p, p, p, p, p]),
         "b2sr_spgemm_bool": (c_int, [p, p, p, pp]),
+        "b2sr_set_schedule": (c_int, [p, c_int]),
+        "b2sr_sample_profile": (c_int, [i32, p, p, i64, p, i64, p, p, p]),
+        "b2sr_autotune": (c_int, [i32, p, p, i64, p, i64, c_int, c_int, ctypes.c_double, c_int, p, pp,
+                                  ctypes.POINTER(TuneReport)]),
         "b2sr_bfs": (c_int, [p, i32, p, c_int, p]),
         "b2sr_bfs_multi": (c_int, [p, p, c_int, p, c_int, p]),
         "b2sr_bfs_sources": (c_int, [p, p, c_int, p, c_int, p]),
@@ -121,6 +136,12 @@ class Matrix:
         self.bytes = inf.bytes
 
     @property
+    def schedule(self) -> int:
+        inf = Info()
+        _check(lib.b2sr_info(self.handle, ctypes.byref(inf)))
+        return inf.schedule
+
+    @property
     def handle(self):
         if self._h is None:
             raise ValueError("matrix is closed")
@@ -168,6 +189,37 @@ def b2sr_from_csr_batch(graphs_csr: Sequence, tile_dim: int, stream=None):
     h = ctypes.c_void_p()
     _check(lib.b2sr_from_csr_batch(g, ns, rps, cis, nnz, int(tile_dim), _stream(stream), ctypes.byref(h), bases))
     return Matrix(h), list(bases)
+
+
+SCHED_AUTO, SCHED_STAGED, SCHED_DIRECT = 0, 1, 2
+
+
+def b2sr_set_schedule(m: Matrix, schedule: int) -> None:
+    _check(lib.b2sr_set_schedule(m.handle, int(schedule)))
+
+
+def b2sr_sample_profile(n: int, rowptr: torch.Tensor, colind: torch.Tensor, sample, stream=None):
+    """Alg. 1 estimate on the device: (est_ratio[4], est_tiles[4]) for k = 4, 8, 16, 32."""
+    import numpy as np
+    smp = np.ascontiguousarray(np.asarray(sample, dtype=np.int32))
+    est = (ctypes.c_double * 4)()
+    th = (ctypes.c_double * 4)()
+    _check(lib.b2sr_sample_profile(int(n), _ptr(rowptr), _ptr(colind), int(colind.numel()),
+                                   smp.ctypes.data_as(ctypes.c_void_p), int(smp.size), est, th, _stream(stream)))
+    return list(est), list(th)
+
+
+def b2sr_autotune(n: int, rowptr: torch.Tensor, colind: torch.Tensor, sample, semiring: int, in_kind: int,
+                  keep_ratio: float = 0.0, trials: int = 5, stream=None):
+    """Returns (Matrix with the chosen tile_dim and schedule, report dict)."""
+    import numpy as np
+    smp = np.ascontiguousarray(np.asarray(sample, dtype=np.int32))
+    rep = TuneReport()
+    h = ctypes.c_void_p()
+    _check(lib.b2sr_autotune(int(n), _ptr(rowptr), _ptr(colind), int(colind.numel()),
+                             smp.ctypes.data_as(ctypes.c_void_p), int(smp.size), int(semiring), int(in_kind),
+                             float(keep_ratio), int(trials), _stream(stream), ctypes.byref(h), ctypes.byref(rep)))
+    return Matrix(h), rep.as_dict()
 
 
 def b2sr_to_csr(m: Matrix, stream=None):

@@ -23,10 +23,19 @@ extern "C" b2sr_status b2sr_info(b2sr_handle h, b2sr_info_t* info) {
     info->n = h->n;
     info->tile_dim = h->k;
     info->n_tile_rows = h->ntr;
-    info->reserved = 0;
+    info->schedule = h->schedule;
     info->n_tiles = h->T;
     info->nnz = h->nnz;
     info->bytes = 4 * ((int64_t)h->ntr + 1) + 4 * h->T + h->T * tile_bytes(h->k);
+    return B2SR_OK;
+}
+
+extern "C" b2sr_status b2sr_set_schedule(b2sr_handle h, int schedule) {
+    clear_error();
+    B2SR_TRY(check_handle(h));
+    if (schedule < B2SR_SCHED_AUTO || schedule > B2SR_SCHED_DIRECT)
+        return fail(B2SR_ERR_INVALID_ARG, "schedule must be B2SR_SCHED_AUTO, _STAGED or _DIRECT");
+    h->schedule = schedule;
     return B2SR_OK;
 }
 

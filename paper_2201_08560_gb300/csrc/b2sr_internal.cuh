@@ -126,6 +126,7 @@ struct b2sr_matrix {
     // lazily built, cached derived arrays (built under the handle's mutex)
     int32_t* voff = nullptr;     // [T+1] set bits before each tile (weights offsets)
     int32_t* outdeg = nullptr;   // [n] ones per column
+    int32_t schedule = 0;        // b2sr_schedule: SpMV kernel for value semirings at k <= 16
     int device = 0;
     void* mtx = nullptr;         // std::mutex*
 };

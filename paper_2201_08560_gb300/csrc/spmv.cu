@@ -1043,7 +1043,9 @@ static b2sr_status run_spmv(const b2sr_matrix* h, const SEM& sem, uint32_t* bits
     Partials<V> part;
     B2SR_TRY((alloc_partials<V, SEM::NV>(pbuf, h->nchunks, &part)));
     const unsigned blocks = (unsigned)ceil_div(h->nchunks, kSpmvWarps);
-    if constexpr (SEM::kGather && K <= 16) {
+    bool staged = false;
+    if constexpr (SEM::kGather && K <= 16) staged = h->schedule != B2SR_SCHED_DIRECT;
+    if constexpr (SEM::kGather && K <= 16) if (staged) {
         const int smem = kSpmvWarps * GatherLayout<K, SEM>::bytes;
         if (smem > 48 * 1024)
             B2SR_CUDA_TRY(cudaFuncSetAttribute(spmv_gather_kernel<K, SEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -1051,7 +1053,8 @@ static b2sr_status run_spmv(const b2sr_matrix* h, const SEM& sem, uint32_t* bits
         spmv_gather_kernel<K, SEM><<<blocks, kSpmvThreads, smem, s>>>(g, sem, part);
         timing_end(tok, family, spmv_bytes(h, vec_bytes), s);
         B2SR_LAUNCH_CHECK("spmv_gather_kernel");
-    } else {
+    }
+    if (!staged) {
         void* tok = timing_begin(s);
         spmv_chunks_kernel<K, SEM><<<blocks, kSpmvThreads, 0, s>>>(g, sem, part);
         timing_end(tok, family, spmv_bytes(h, vec_bytes), s);

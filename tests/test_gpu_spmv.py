@@ -47,6 +47,7 @@ def canon(g):
 
 
 MASKS = [None, False, True]
+SCHEDS = [1, 2]   # b2sr_schedule STAGED, DIRECT (the same at k = 32)
 
 
 @pytest.mark.parametrize("k", KS)
@@ -69,8 +70,10 @@ def test_bool_and_count(B, mats, k, gi, masked):
 
 @pytest.mark.parametrize("k", KS)
 @pytest.mark.parametrize("gi", range(len(GRAPH_IDS)), ids=GRAPH_IDS)
-def test_plus_times(B, mats, k, gi):
+@pytest.mark.parametrize("sched", SCHEDS, ids=["staged", "direct"])
+def test_plus_times(B, mats, k, gi, sched):
     g, m = mats(gi, k)
+    B.b2sr_set_schedule(m, sched)
     x = np.random.default_rng(gi).random(g.n).astype(np.float32)
     y = torch.full((max(g.n, 1),), float("nan"), dtype=torch.float32, device="cuda")
     B.b2sr_spmv(m, B.PLUS_TIMES, B.VEC_F32, to_dev(x), B.VEC_F32, y)
@@ -89,8 +92,10 @@ def test_plus_times(B, mats, k, gi):
 
 @pytest.mark.parametrize("k", KS)
 @pytest.mark.parametrize("gi", range(len(GRAPH_IDS)), ids=GRAPH_IDS)
-def test_min_plus_unit_and_labels(B, mats, k, gi):
+@pytest.mark.parametrize("sched", SCHEDS, ids=["staged", "direct"])
+def test_min_plus_unit_and_labels(B, mats, k, gi, sched):
     g, m = mats(gi, k)
+    B.b2sr_set_schedule(m, sched)
     rng = np.random.default_rng(gi + 3)
     x = (rng.integers(0, 1000, g.n) / 4).astype(np.float32)   # exact sums
     x[rng.random(g.n) < 0.3] = np.inf
@@ -109,8 +114,10 @@ def test_min_plus_unit_and_labels(B, mats, k, gi):
 
 @pytest.mark.parametrize("k", KS)
 @pytest.mark.parametrize("gi", [0, 2, 3, 4, 5], ids=["rmat12", "star20k", "grid37x41", "gaps", "directed300"])
-def test_min_plus_weighted(B, mats, k, gi):
+@pytest.mark.parametrize("sched", SCHEDS, ids=["staged", "direct"])
+def test_min_plus_weighted(B, mats, k, gi, sched):
     g, m = mats(gi, k)
+    B.b2sr_set_schedule(m, sched)
     gc = canon(g)
     rng = np.random.default_rng(gi + 11)
     w_grid = (1 + rng.integers(0, 99 * 16, gc.colind.size) / 16).astype(np.float32)   # exact sums
@@ -135,8 +142,10 @@ def test_min_plus_weighted(B, mats, k, gi):
 @pytest.mark.parametrize("k", KS)
 @pytest.mark.parametrize("gi", range(len(GRAPH_IDS)), ids=GRAPH_IDS)
 @pytest.mark.parametrize("masked", MASKS, ids=["nomask", "mask", "complement"])
-def test_or64(B, mats, k, gi, masked):
+@pytest.mark.parametrize("sched", SCHEDS, ids=["staged", "direct"])
+def test_or64(B, mats, k, gi, masked, sched):
     g, m = mats(gi, k)
+    B.b2sr_set_schedule(m, sched)
     rng = np.random.default_rng(gi + 5)
     X = rng.integers(0, 2**63, g.n, dtype=np.int64).astype(np.uint64)
     X[rng.random(g.n) < 0.7] = 0
