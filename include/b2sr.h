@@ -83,10 +83,11 @@ typedef enum {
 } b2sr_vec;
 
 /* SpMV kernel schedule for the value schemes (plus-times on floats, min-plus,
- * b2sr_spmm_bits64) at tile_dim <= 16; the Boolean and count schemes and
- * tile_dim 32 have one schedule.  Both give identical results (the same
- * fixed reduction order); they differ only in speed, which depends on the
- * graph (b2sr_autotune measures it).  The paper stages the dense vector
+ * b2sr_spmm_bits64, b2sr_spmm_f32x4) at tile_dim <= 16; the Boolean and count schemes and
+ * tile_dim 32 have one schedule.  Min and OR results are identical under
+ * both; plus-times sums are added in a different fixed order (each schedule
+ * bitwise reproducible, both within the fp32 tolerance).  Speed depends on
+ * the graph (b2sr_autotune measures it).  The paper stages the dense vector
  * segment of a tile in shared memory (Sec. IV); STAGED is that idea for a
  * gather per set bit, DIRECT reads the vector from global memory. */
 typedef enum {
@@ -230,6 +231,18 @@ b2sr_status b2sr_spmv(b2sr_handle h, b2sr_semiring semiring, b2sr_vec in_kind, c
  *   X, Y device uint64[n]; M device uint64[n] or NULL. */
 b2sr_status b2sr_spmm_bits64(b2sr_handle h, const uint64_t* X, uint64_t* Y, const uint64_t* M,
                              int complement, void* stream);
+
+/* Plus-times SpMM over a block of four fp32 columns (bmv_bin_full_full of
+ * Table 2 on the arithmetic semiring of Table 4, four vectors per pass over
+ * the tiles; Sec. V PR batched):
+ *   Y[4i+b] = sum_{j: A_ij=1} X[4j+b], b = 0..3, then masked like b2sr_spmv
+ *   (masked-out rows get 0).
+ *   X, Y device float[4n], vertex-major (the four values of vertex v are
+ *   contiguous), 16-byte aligned (else B2SR_ERR_INVALID_ARG); Y must not alias X.
+ * Column b of Y is bitwise equal to b2sr_spmv(PLUS_TIMES, F32) on column b
+ * of X: each column is summed in the same fixed order. */
+b2sr_status b2sr_spmm_f32x4(b2sr_handle h, const float* X, float* Y, const uint32_t* mask,
+                            int mask_complement, void* stream);
 
 /* Boolean SpMV that allocates no device memory.  The paper has no
  * counterpart; it exists for callers that cannot allocate device memory when
@@ -396,6 +409,89 @@ b2sr_status b2sr_timing_read(const char* family, double* total_ms, int64_t* laun
 
 /* Drops all recorded launches (no counterpart in the paper). */
 b2sr_status b2sr_timing_reset(void);
+
+/* ---------------------------------------------------------------------- */
+/* Query serving (no counterpart in the paper: a request loop around the   */
+/* Sec. V BFS and PR drivers)                                              */
+/* ---------------------------------------------------------------------- */
+
+typedef struct b2sr_server* b2sr_server_t;
+
+typedef struct {
+    int64_t submitted, completed, failed, refused; /* since the last reset */
+    int64_t steps;          /* batched device steps (one BFS level and one PR iteration per busy slot) */
+    double p50_us, p99_us;  /* submit-to-done latency, nearest-rank percentiles */
+    double mean_us, max_us;
+    double wall_s;          /* first submission to last completion */
+    double queries_per_s;   /* completed / wall_s */
+    int64_t bytes_in_use;   /* resident graphs plus batch state */
+    int64_t budget;
+} b2sr_server_stats_t;
+
+/* A query server on the current device, not in the paper (the Sec. V
+ * drivers run one query per call).  It keeps graphs resident and batches
+ * queries continuously: BFS queries on one graph share a 64-lane bit-SpMM
+ * (b2sr_spmm_bits64) and join at a level boundary; PageRank queries share
+ * four-column blocks (b2sr_spmm_f32x4) and join at an iteration boundary.  A
+ * worker thread drives every graph on its own stream, so different graphs'
+ * steps overlap on the device.
+ *   budget_bytes   device memory for resident graphs and batch state
+ *   max_bfs_lanes  1..64 concurrent BFS queries per graph
+ *   max_pr_blocks  four-column PageRank blocks per graph (0: no PageRank)
+ * A result is the same alone and in any mix: levels bit-exact; PageRank
+ * bitwise equal to b2sr_pagerank with the query's teleport vector. */
+b2sr_status b2sr_server_create(int64_t budget_bytes, int max_bfs_lanes, int max_pr_blocks,
+                               b2sr_server_t* out);
+
+/* Registers a graph (no counterpart in the paper).  The server borrows the
+ * handle: it must stay alive until b2sr_server_destroy.  Its bytes (and its
+ * out-degree array, built here) count against the budget;
+ * B2SR_ERR_ADMISSION_REFUSED if they do not fit.  Synchronises once. */
+b2sr_status b2sr_server_add_graph(b2sr_server_t s, b2sr_handle h, int32_t* graph_id);
+
+/* Budget accounting of a registered graph (no counterpart in the paper):
+ * its resident bytes (B2SR arrays with padding, out-degrees), the working
+ * memory of its 64-lane BFS batch and of one four-column PageRank block.
+ * Any pointer may be NULL. */
+b2sr_status b2sr_server_graph_bytes(b2sr_server_t s, int32_t graph, int64_t* resident, int64_t* bfs_batch,
+                                    int64_t* pr_block);
+
+/* Submits a BFS query (Sec. V BFS, levels as b2sr_bfs; no counterpart in the
+ * paper for the queueing).  levels: device int32[n], written by the server;
+ * the caller must not touch it until the query is done.  Returns at once
+ * with *query_id.  B2SR_ERR_ADMISSION_REFUSED if the graph's BFS batch can
+ * never fit the budget beside the resident graphs. */
+b2sr_status b2sr_server_submit_bfs(b2sr_server_t s, int32_t graph, int32_t src, int32_t* levels,
+                                   int64_t* query_id);
+
+/* Submits a PageRank query (Sec. V PR, as b2sr_pagerank with damping d and
+ * `iters` iterations; no counterpart in the paper for the queueing).
+ * src < 0: uniform teleport 1/n; else all teleport mass on src (personalised
+ * PageRank).  pr: device float[n], written by the server. */
+b2sr_status b2sr_server_submit_pagerank(b2sr_server_t s, int32_t graph, int32_t src, float d, int iters,
+                                        float* pr, int64_t* query_id);
+
+/* Waits up to timeout_s seconds (<= 0: just polls) for a query (no
+ * counterpart in the paper).  *done = 1 once its output is complete on the
+ * device; *latency_us then holds submit-to-done time (may be NULL).  Returns
+ * the query's failure status if it failed. */
+b2sr_status b2sr_server_wait(b2sr_server_t s, int64_t query_id, double timeout_s, int* done,
+                             double* latency_us);
+
+/* Waits until every submitted query is done (no counterpart in the paper);
+ * B2SR_ERR_NOT_CONVERGED at the timeout (<= 0: none). */
+b2sr_status b2sr_server_drain(b2sr_server_t s, double timeout_s);
+
+/* Counters and latency percentiles (no counterpart in the paper). */
+b2sr_status b2sr_server_stats(b2sr_server_t s, b2sr_server_stats_t* stats);
+
+/* Clears the counters and latencies of b2sr_server_stats (no counterpart in the paper). */
+b2sr_status b2sr_server_reset_stats(b2sr_server_t s);
+
+/* Stops the worker after the steps in flight, fails the queries not done with
+ * B2SR_ERR_ABORTED and frees the server (no counterpart in the paper).  The
+ * graphs stay with the caller.  NULL is a no-op. */
+b2sr_status b2sr_server_destroy(b2sr_server_t s);
 
 #ifdef __cplusplus
 }

@@ -47,6 +47,14 @@ class TuneReport(ctypes.Structure):
                 "tile_dim": self.tile_dim, "schedule": self.schedule}
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("refused", ctypes.c_int64), ("steps", ctypes.c_int64), ("p50_us", ctypes.c_double),
+                ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double),
+                ("wall_s", ctypes.c_double), ("queries_per_s", ctypes.c_double), ("bytes_in_use", ctypes.c_int64),
+                ("budget", ctypes.c_int64)]
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise RuntimeError(f"the CUDA library {LIB_PATH} is not built; run __graft_entry__.build()")
@@ -67,6 +75,7 @@ def _load() -> ctypes.CDLL:
         "b2sr_spmv": (c_int, [p, c_int, c_int, p, c_int, p, p, c_int, p, p]),
         "b2sr_spmm_bits64": (c_int, [p, p, p, p, c_int, p]),
         "b2sr_spmv_bool_noalloc": (c_int, [p, p, p, p, c_int, p]),
+        "b2sr_spmm_f32x4": (c_int, [p, p, p, p, c_int, p]),
         "b2sr_spgemm_masked_count": (c_int, [p, p, p, p, p]),
         "b2sr_spgemm_bool": (c_int, [p, p, p, pp]),
         "b2sr_set_schedule": (c_int, [p, c_int]),
@@ -81,6 +90,16 @@ def _load() -> ctypes.CDLL:
         "b2sr_pagerank": (c_int, [p, f32, c_int, p, p, p]),
         "b2sr_cc": (c_int, [p, p, c_int, p]),
         "b2sr_tc": (c_int, [p, p, p]),
+        "b2sr_server_create": (c_int, [i64, c_int, c_int, pp]),
+        "b2sr_server_add_graph": (c_int, [p, p, ctypes.POINTER(i32)]),
+        "b2sr_server_graph_bytes": (c_int, [p, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "b2sr_server_submit_bfs": (c_int, [p, i32, i32, p, ctypes.POINTER(i64)]),
+        "b2sr_server_submit_pagerank": (c_int, [p, i32, i32, f32, c_int, p, ctypes.POINTER(i64)]),
+        "b2sr_server_wait": (c_int, [p, i64, ctypes.c_double, ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_double)]),
+        "b2sr_server_drain": (c_int, [p, ctypes.c_double]),
+        "b2sr_server_stats": (c_int, [p, ctypes.POINTER(ServerStats)]),
+        "b2sr_server_reset_stats": (c_int, [p]),
+        "b2sr_server_destroy": (c_int, [p]),
         "b2sr_launch_count": (i64, []),
         "b2sr_timing_enable": (None, [c_int]),
         "b2sr_timing_read": (c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
@@ -282,6 +301,13 @@ def b2sr_spmm_bits64(m: Matrix, X: torch.Tensor, Y: torch.Tensor, M: Optional[to
     return Y
 
 
+def b2sr_spmm_f32x4(m: Matrix, X: torch.Tensor, Y: torch.Tensor, mask: Optional[torch.Tensor] = None,
+                    complement: bool = False, stream=None) -> torch.Tensor:
+    """X, Y: float32 tensors of shape (n, 4), contiguous."""
+    _check(lib.b2sr_spmm_f32x4(m.handle, _ptr(X), _ptr(Y), _ptr(mask), int(bool(complement)), _stream(stream)))
+    return Y
+
+
 # ---------------------------------------------------------------------------
 # SpGEMM
 # ---------------------------------------------------------------------------
@@ -393,3 +419,103 @@ def b2sr_timing_read(family: str):
 
 def b2sr_timing_reset():
     _check(lib.b2sr_timing_reset())
+
+
+# ---------------------------------------------------------------------------
+# query server
+# ---------------------------------------------------------------------------
+
+class Server:
+    """Owner of a b2sr_server_t.  Keeps the registered matrices and every
+    query's output tensor alive until the query has been waited for."""
+
+    def __init__(self, budget_bytes: int, max_bfs_lanes: int = 64, max_pr_blocks: int = 2):
+        h = ctypes.c_void_p()
+        _check(lib.b2sr_server_create(int(budget_bytes), int(max_bfs_lanes), int(max_pr_blocks), ctypes.byref(h)))
+        self._h = h
+        self._graphs = []
+        self._outs = {}
+
+    def add_graph(self, m: Matrix) -> int:
+        gid = ctypes.c_int32()
+        _check(lib.b2sr_server_add_graph(self._h, m.handle, ctypes.byref(gid)))
+        self._graphs.append(m)
+        return gid.value
+
+    def _n(self, graph: int) -> int:
+        return self._graphs[graph].n if 0 <= graph < len(self._graphs) else 1
+
+    def graph_bytes(self, graph: int):
+        """(resident, bfs_batch, pr_block) bytes the budget counts for a graph."""
+        r, b, p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.b2sr_server_graph_bytes(self._h, int(graph), ctypes.byref(r), ctypes.byref(b), ctypes.byref(p)))
+        return r.value, b.value, p.value
+
+    def submit_bfs(self, graph: int, src: int, levels: Optional[torch.Tensor] = None):
+        if levels is None:
+            levels = torch.empty(max(self._n(graph), 1), dtype=torch.int32, device=_dev())
+            # the server writes on its own streams: the block must be free of earlier work
+            torch.cuda.current_stream().synchronize()
+        qid = ctypes.c_int64()
+        _check(lib.b2sr_server_submit_bfs(self._h, int(graph), int(src), _ptr(levels), ctypes.byref(qid)))
+        self._outs[qid.value] = levels
+        return qid.value, levels
+
+    def submit_pagerank(self, graph: int, src: int = -1, d: float = 0.85, iters: int = 20,
+                        pr: Optional[torch.Tensor] = None):
+        if pr is None:
+            pr = torch.empty(max(self._n(graph), 1), dtype=torch.float32, device=_dev())
+            torch.cuda.current_stream().synchronize()
+        qid = ctypes.c_int64()
+        _check(lib.b2sr_server_submit_pagerank(self._h, int(graph), int(src), float(d), int(iters), _ptr(pr),
+                                               ctypes.byref(qid)))
+        self._outs[qid.value] = pr
+        return qid.value, pr
+
+    def wait(self, qid: int, timeout: float = 60.0) -> float:
+        """Latency in microseconds; raises B2SRError if the query failed or timed out."""
+        done = ctypes.c_int()
+        lat = ctypes.c_double()
+        try:
+            _check(lib.b2sr_server_wait(self._h, int(qid), float(timeout), ctypes.byref(done), ctypes.byref(lat)))
+        except B2SRError:
+            self._outs.pop(qid, None)
+            raise
+        if not done.value:
+            raise B2SRError(5, f"query {qid} not done after {timeout} s")
+        self._outs.pop(qid, None)
+        return lat.value
+
+    def poll(self, qid: int) -> bool:
+        done = ctypes.c_int()
+        _check(lib.b2sr_server_wait(self._h, int(qid), 0.0, ctypes.byref(done), None))
+        return bool(done.value)
+
+    def drain(self, timeout: float = 0.0) -> None:
+        _check(lib.b2sr_server_drain(self._h, float(timeout)))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib.b2sr_server_stats(self._h, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+    def reset_stats(self) -> None:
+        _check(lib.b2sr_server_reset_stats(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            _check(lib.b2sr_server_destroy(self._h))
+            self._h = None
+            self._outs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

