@@ -128,6 +128,134 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# serving: resident R-MAT graphs and a Poisson stream of mixed queries
+# ---------------------------------------------------------------------------
+SERVE_GRAPHS, SERVE_SCALES = 32, (14, 20)
+SERVE_QUERIES, SERVE_RATE, SERVE_PR_ITERS = 10000, 2000.0, 20
+SERVE_BUDGET = 64 << 30
+SERVE_BASELINE_QUERIES = 300
+
+
+def _serve_graph(scale, seed):
+    from paper_2201_08560_gb300 import graphs
+    g = graphs.rmat(scale, EDGE_FACTOR, seed=seed)
+    deg = np.diff(g.rowptr)
+    return g.n, g.rowptr, g.colind, np.flatnonzero(deg > 0).astype(np.int32)
+
+
+def serving_extra(B, dev):
+    """32 resident graphs (scales 14..20, k = 8); 10,000 queries, half BFS from
+    a random non-isolated source and half personalised PageRank (20 iterations,
+    all teleport mass on a random non-isolated source), arriving as a Poisson
+    stream at 2,000 queries/s.  Reports the server's latency percentiles and
+    throughput for that stream, its throughput when all queries are queued at
+    once, and the throughput of one query per driver call on a sample of the
+    same mix."""
+    import multiprocessing as mp
+    import torch
+    lo, hi = SERVE_SCALES
+    specs = [(lo + i % (hi - lo + 1), 1000 + i) for i in range(SERVE_GRAPHS)]
+    t_gen = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        gs = pool.starmap(_serve_graph, specs)
+    t_gen = time.perf_counter() - t_gen
+    mats = []
+    for n, rp, ci, _ in gs:
+        mats.append(B.b2sr_from_csr(n, torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), TILE))
+    rng = np.random.default_rng(11)
+    plan = []
+    for _ in range(SERVE_QUERIES):
+        gi = int(rng.integers(SERVE_GRAPHS))
+        cand = gs[gi][3]
+        src = int(cand[rng.integers(cand.size)])
+        plan.append(("bfs" if rng.random() < 0.5 else "pr", gi, src))
+    arrivals = np.cumsum(rng.exponential(1.0 / SERVE_RATE, SERVE_QUERIES))
+    # every query's output preallocated (one slab), so submission is one C call
+    sizes = [gs[gi][0] for _, gi, _ in plan]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    slab = torch.empty(int(offs[-1]), dtype=torch.int32, device=dev)
+    outs_i = [slab[offs[i]:offs[i + 1]] for i in range(SERVE_QUERIES)]
+    outs_f = [o.view(torch.float32) for o in outs_i]
+    torch.cuda.synchronize()
+
+    def run(srv, gids, queries, times=None):
+        srv.reset_stats()
+        t0 = time.perf_counter()
+        ids = []
+        for i, (kind, gi, src) in enumerate(queries):
+            if times is not None:
+                due = t0 + times[i]
+                while True:
+                    now = time.perf_counter()
+                    if now >= due:
+                        break
+                    if due - now > 3e-4:
+                        time.sleep(due - now - 2e-4)
+            if kind == "bfs":
+                ids.append(srv.submit_bfs(gids[gi], src, outs_i[i])[0])
+            else:
+                ids.append(srv.submit_pagerank(gids[gi], src, DAMP, SERVE_PR_ITERS, outs_f[i])[0])
+        srv.drain(600.0)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        return {"queries": len(queries), "wall_s": wall, "queries_per_s": len(queries) / wall,
+                "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3,
+                "device_steps": st["steps"], "failed": st["failed"]}
+
+    res = {}
+    with B.Server(SERVE_BUDGET, 64, 2) as srv:
+        gids = [srv.add_graph(m) for m in mats]
+        resident = sum(srv.graph_bytes(g)[0] for g in gids)
+        run(srv, gids, plan[:200])                                     # warm-up
+        res["poisson"] = run(srv, gids, plan, arrivals)
+        res["saturated"] = run(srv, gids, plan)
+        bfs_only = [q for q in plan if q[0] == "bfs"]
+        res["saturated_bfs_only"] = run(srv, gids, bfs_only)
+    # one query per driver call, same mix
+    base = plan[:SERVE_BASELINE_QUERIES]
+    tele = torch.zeros(max(n for n, _, _, _ in gs), dtype=torch.float32, device=dev)
+    for kind, gi, src in base[:20]:   # warm-up
+        if kind == "bfs":
+            B.b2sr_bfs(mats[gi], src, outs_i[0])
+        else:
+            B.b2sr_pagerank(mats[gi], DAMP, 2, None, outs_f[0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nb = 0
+    for i, (kind, gi, src) in enumerate(base):
+        m = mats[gi]
+        if kind == "bfs":
+            B.b2sr_bfs(m, src, outs_i[i])
+            nb += 1
+        else:
+            t = tele[: m.n]
+            t[src] = 1.0
+            B.b2sr_pagerank(m, DAMP, SERVE_PR_ITERS, t, outs_f[i])
+            t[src] = 0.0
+    torch.cuda.synchronize()
+    base_wall = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    bq = [q for q in plan if q[0] == "bfs"][:SERVE_BASELINE_QUERIES]
+    for i, (kind, gi, src) in enumerate(bq):
+        B.b2sr_bfs(mats[gi], src, outs_i[i])
+    torch.cuda.synchronize()
+    base_bfs_wall = time.perf_counter() - t0
+    res["one_query_per_call"] = {"queries": len(base), "queries_per_s": len(base) / base_wall}
+    res["one_query_per_call_bfs_only"] = {"queries": len(bq), "queries_per_s": len(bq) / base_bfs_wall}
+    res["speedup_saturated_vs_one_per_call"] = res["saturated"]["queries_per_s"] / res["one_query_per_call"]["queries_per_s"]
+    res["speedup_bfs_saturated_vs_one_per_call"] = (res["saturated_bfs_only"]["queries_per_s"] /
+                                                     res["one_query_per_call_bfs_only"]["queries_per_s"])
+    res["config"] = (f"{SERVE_GRAPHS} R-MAT graphs, scales {lo}..{hi} (scale {lo} + i mod {hi - lo + 1}), ef{EDGE_FACTOR}, "
+                     f"seeds 1000+i, k={TILE}, {resident / 2**30:.2f} GiB resident; {SERVE_QUERIES} queries, 50% BFS "
+                     f"(random non-isolated source) / 50% personalised PageRank ({SERVE_PR_ITERS} iters, d={DAMP}), "
+                     f"Poisson arrivals at {SERVE_RATE:.0f}/s; budget {SERVE_BUDGET >> 30} GiB, 64 BFS lanes and 2 "
+                     f"four-column PageRank blocks per graph; graph generation {t_gen:.1f} s on the host (untimed)")
+    for m in mats:
+        m.close()
+    return res
+
+
+# ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
 
@@ -208,6 +336,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -355,6 +484,12 @@ def main():
         B.b2sr_timing_reset()
         extra["spmv_bool_k8"] = {"kernel_us": tb / nb * 1e3, "gteps": g.nnz / (tb / nb / 1e3) / 1e9,
                                  "gbs": byb / nb / (tb / nb / 1e3) / 1e9}
+
+    if not args.no_serving:
+        try:
+            extra["serving"] = serving_extra(B, dev)
+        except Exception as e:  # reported, never fatal to the main line
+            extra["serving"] = {"failed": repr(e)}
 
     # ---- roofline of the dominant kernel ----
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")

@@ -168,8 +168,8 @@ class Matrix:
 
     def close(self):
         if getattr(self, "_h", None) is not None:
-            _check(lib.b2sr_destroy(self._h))
-            self._h = None
+            h, self._h = self._h, None  # never destroyed twice, even if this call fails
+            _check(lib.b2sr_destroy(h))
 
     def __del__(self):
         try:
@@ -504,9 +504,9 @@ class Server:
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None:
-            _check(lib.b2sr_server_destroy(self._h))
-            self._h = None
+            h, self._h = self._h, None
             self._outs.clear()
+            _check(lib.b2sr_server_destroy(h))
 
     def __del__(self):
         try:

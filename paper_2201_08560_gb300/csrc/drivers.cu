@@ -419,11 +419,12 @@ b2sr_status cc(b2sr_matrix* h, int32_t* labels, int max_iters, cudaStream_t s) {
     const int32_t n = h->n;
     if (n == 0) return B2SR_OK;
     DevBuf buf(s);
-    B2SR_TRY(buf.alloc(3 * (size_t)n * sizeof(int32_t) + 16));
+    const size_t vb = round_up((size_t)n * sizeof(int32_t), 256);  // each vector 256-byte aligned
+    B2SR_TRY(buf.alloc(3 * vb + 256));
     int32_t* gf = buf.as<int32_t>();
-    int32_t* gfn = gf + n;
-    int32_t* mngf = gfn + n;
-    int32_t* any = mngf + n;
+    int32_t* gfn = reinterpret_cast<int32_t*>(buf.as<char>() + vb);
+    int32_t* mngf = reinterpret_cast<int32_t*>(buf.as<char>() + 2 * vb);
+    int32_t* any = reinterpret_cast<int32_t*>(buf.as<char>() + 3 * vb);
     int32_t* f = labels;
     cc_init_kernel<<<grid_for(n), 256, 0, s>>>(f, gf, n);
     B2SR_LAUNCH_CHECK("cc_init_kernel");
