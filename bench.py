@@ -143,7 +143,7 @@ def _serve_graph(scale, seed):
     return g.n, g.rowptr, g.colind, np.flatnonzero(deg > 0).astype(np.int32)
 
 
-def serving_extra(B, dev):
+def serving_extra(B, dev, pool=None):
     """32 resident graphs (scales 14..20, k = 8); 10,000 queries, half BFS from
     a random non-isolated source and half personalised PageRank (20 iterations,
     all teleport mass on a random non-isolated source), arriving as a Poisson
@@ -156,7 +156,10 @@ def serving_extra(B, dev):
     lo, hi = SERVE_SCALES
     specs = [(lo + i % (hi - lo + 1), 1000 + i) for i in range(SERVE_GRAPHS)]
     t_gen = time.perf_counter()
-    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+    if pool is None:
+        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as own:
+            gs = own.starmap(_serve_graph, specs)
+    else:
         gs = pool.starmap(_serve_graph, specs)
     t_gen = time.perf_counter() - t_gen
     mats = []
@@ -256,6 +259,128 @@ def serving_extra(B, dev):
 
 
 # ---------------------------------------------------------------------------
+# the other workloads: weighted grid SSSP and triangle counting; batching
+# ---------------------------------------------------------------------------
+GRID_SIDE, GRID_WSEED = 4096, 5
+TC_SCALE, TC_EF = 18, 32
+MS_SCALE, MS_SOURCES = 22, 64
+ARENA_GRAPHS, ARENA_SCALES = 256, (8, 16)
+
+
+def _grid_weighted():
+    from paper_2201_08560_gb300 import graphs
+    g = graphs.grid2d(GRID_SIDE, GRID_SIDE)
+    return g.n, g.rowptr, g.colind, graphs.symmetric_weights(g, GRID_WSEED)
+
+
+def _rmat_plain(scale, ef, seed):
+    from paper_2201_08560_gb300 import graphs
+    g = graphs.rmat(scale, ef, seed=seed)
+    return g.n, g.rowptr, g.colind
+
+
+def _timed(fn, reps=1):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def grid_tc_extra(B, dev, grid_res, tc_res):
+    """SSSP from the corner of a 4096 x 4096 4-neighbour grid with fp32 weights
+    on the 1/16 lattice in [1, 100); triangle count of R-MAT scale 18 ef32."""
+    import torch
+    out = {}
+    n, rp, ci, w = grid_res.get()
+    rp_d, ci_d = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
+    with B.b2sr_from_csr(n, rp_d, ci_d, TILE) as m:
+        wb = B.b2sr_weights_from_csr(m, rp_d, ci_d, torch.from_numpy(w).to(dev))
+        dist = torch.empty(n, dtype=torch.float32, device=dev)
+        # push rounds over the frontier (the grid is symmetric: the handle is its own transpose)
+        ms = _timed(lambda: B.b2sr_sssp_push(m, 0, wb, dist), reps=3)
+        far = float(dist[-1].item())
+        out["sssp_grid4096"] = {"driver": "b2sr_sssp_push", "ms": ms, "nnz": int(ci.size),
+                                "gteps": ci.size / (ms / 1e3) / 1e9, "dist_far_corner": far, "n": int(n)}
+    del rp_d, ci_d
+    n, rp, ci = tc_res.get()
+    rp_d, ci_d = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
+    with B.b2sr_from_csr(n, rp_d, ci_d, TILE) as m:
+        cnt = {}
+        ms = _timed(lambda: cnt.__setitem__("t", B.b2sr_tc(m)), reps=3)
+        out["tc_rmat18_ef32"] = {"ms": ms, "nnz": int(ci.size), "edges_per_s": ci.size / (ms / 1e3),
+                                 "triangles": int(cnt["t"].item()), "n": int(n)}
+    return out
+
+
+def batching_extra(B, dev, big_res, arena_res, arena_scales):
+    """64-source BFS on R-MAT scale 22 (tile_dim and schedule from the
+    autotuner) against 64 single-source BFS calls; 256 R-MAT graphs (scales
+    8..16) in one block-diagonal arena, one BFS each in one captured level loop,
+    against one BFS call per separately converted graph."""
+    import torch
+    from paper_2201_08560_gb300 import graphs
+    out = {}
+    n, rp, ci = big_res.get()
+    rp_d, ci_d = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
+    rng = np.random.default_rng(17)
+    deg = np.diff(rp)
+    cand = np.flatnonzero(deg > 0)
+    srcs = [int(v) for v in cand[rng.integers(0, cand.size, MS_SOURCES)]]
+    smp = rng.integers(0, n, 8192).astype(np.int32)
+    t0 = time.perf_counter()
+    m, rep = B.b2sr_autotune(n, rp_d, ci_d, smp, B.BOOL_OR_AND, B.VEC_BITS64, keep_ratio=0.0, trials=3)
+    t_tune = time.perf_counter() - t0
+    with m:
+        lv = torch.empty((MS_SOURCES, n), dtype=torch.int32, device=dev)
+        t_multi = _timed(lambda: B.b2sr_bfs_multi(m, srcs, lv))
+        lv1 = torch.empty(n, dtype=torch.int32, device=dev)
+
+        def plain():
+            for s in srcs:
+                B.b2sr_bfs(m, s, lv1)
+        t_plain = _timed(plain)
+        out["bfs64_rmat22"] = {"tile_dim": rep["tile_dim"], "schedule": rep["schedule"],
+                               "autotune_s": t_tune, "trial_us": rep["trial_us"], "est_ratio": rep["est_ratio"],
+                               "batched_ms": t_multi, "plain_ms": t_plain,
+                               "batched_queries_per_s": MS_SOURCES / (t_multi / 1e3),
+                               "plain_queries_per_s": MS_SOURCES / (t_plain / 1e3),
+                               "speedup": t_plain / t_multi, "nnz": int(ci.size),
+                               "batched_gteps": MS_SOURCES * ci.size / (t_multi / 1e3) / 1e9}
+    del rp_d, ci_d
+    gs = arena_res.get()
+    csrs = [(gn, torch.from_numpy(grp).to(dev), torch.from_numpy(gci).to(dev)) for gn, grp, gci in gs]
+    arena, bases = B.b2sr_from_csr_batch(csrs, TILE)
+    srcs_a = [int(bases[i]) for i in range(len(gs))]  # vertex 0 of every graph (its hub)
+    with arena:
+        lva = torch.empty(arena.n, dtype=torch.int32, device=dev)
+        t_arena = _timed(lambda: B.b2sr_bfs_sources(arena, srcs_a, lva))
+        mats = [B.b2sr_from_csr(gn, grp, gci, TILE) for gn, grp, gci in csrs]
+        outs = [torch.empty(gn, dtype=torch.int32, device=dev) for gn, _, _ in csrs]
+
+        def per_graph():
+            for mm, o in zip(mats, outs):
+                B.b2sr_bfs(mm, 0, o)
+        t_each = _timed(per_graph)
+        # the arena's per-graph slices equal the separate runs
+        same = all(torch.equal(lva[b0:b0 + gn], o) for (gn, _, _), b0, o in zip(csrs, bases, outs))
+        for mm in mats:
+            mm.close()
+        out["arena_256_graphs"] = {"graphs": len(gs), "scales": arena_scales, "arena_n": int(arena.n),
+                                   "arena_ms": t_arena, "per_graph_ms": t_each,
+                                   "graphs_per_s_arena": len(gs) / (t_arena / 1e3),
+                                   "graphs_per_s_per_graph": len(gs) / (t_each / 1e3),
+                                   "speedup": t_each / t_arena, "same_levels": bool(same)}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
 
@@ -336,7 +461,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the serving, grid/TC and batching extras")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -485,11 +610,23 @@ def main():
         extra["spmv_bool_k8"] = {"kernel_us": tb / nb * 1e3, "gteps": g.nnz / (tb / nb / 1e3) / 1e9,
                                  "gbs": byb / nb / (tb / nb / 1e3) / 1e9}
 
-    if not args.no_serving:
-        try:
-            extra["serving"] = serving_extra(B, dev)
-        except Exception as e:  # reported, never fatal to the main line
-            extra["serving"] = {"failed": repr(e)}
+    if not args.no_extras:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+            rng = np.random.default_rng(23)
+            a_scales = [int(v) for v in rng.integers(ARENA_SCALES[0], ARENA_SCALES[1] + 1, ARENA_GRAPHS)]
+            grid_res = pool.apply_async(_grid_weighted)
+            tc_res = pool.apply_async(_rmat_plain, (TC_SCALE, TC_EF, 2))
+            big_res = pool.apply_async(_rmat_plain, (MS_SCALE, EDGE_FACTOR, 3))
+            arena_res = pool.starmap_async(_rmat_plain, [(sc, EDGE_FACTOR, 5000 + i) for i, sc in enumerate(a_scales)])
+            for name, fn in (("serving", lambda: serving_extra(B, dev, pool)),
+                             ("grid_sssp_and_tc", lambda: grid_tc_extra(B, dev, grid_res, tc_res)),
+                             ("batching", lambda: batching_extra(B, dev, big_res, arena_res,
+                                                                 f"{ARENA_SCALES[0]}..{ARENA_SCALES[1]} uniform, seed 23"))):
+                try:
+                    extra[name] = fn()
+                except Exception as e:  # reported, never fatal to the main line
+                    extra[name] = {"failed": repr(e)}
 
     # ---- roofline of the dominant kernel ----
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")

@@ -79,7 +79,9 @@ typedef enum {
 typedef enum {
     B2SR_VEC_BITS = 0, /* bitset, ceil(n/32) uint32 words */
     B2SR_VEC_I32 = 1,  /* int32[n] */
-    B2SR_VEC_F32 = 2   /* float[n] */
+    B2SR_VEC_F32 = 2,  /* float[n] */
+    B2SR_VEC_BITS64 = 3 /* uint64[n]: 64 Boolean vectors, one bit each per vertex
+                           (the b2sr_spmm_bits64 scheme; accepted by b2sr_autotune only) */
 } b2sr_vec;
 
 /* SpMV kernel schedule for the value schemes (plus-times on floats, min-plus,
@@ -320,7 +322,8 @@ typedef struct {
  * est_ratio[k] <= keep_ratio * min est_ratio (keep_ratio <= 0: every k;
  * 0 < keep_ratio < 1 is B2SR_ERR_INVALID_ARG).  Each candidate is converted
  * and timed over `trials` SpMVs of the (sr, in_kind) scheme on a fixed
- * synthetic vector, under each schedule it has (b2sr_schedule); the fastest
+ * synthetic vector (BOOL_OR_AND with B2SR_VEC_BITS64: b2sr_spmm_bits64, the
+ * multi-source BFS step), under each schedule it has (b2sr_schedule); the fastest
  * handle is returned in *out with that schedule set, the others destroyed.
  * The timings are taken on `stream` while other work may share the device,
  * so the choice is a measurement, not a guarantee.  Synchronises `stream`. */
@@ -368,6 +371,24 @@ b2sr_status b2sr_bfs_multi(b2sr_handle h, const int32_t* srcs_host, int nsrc, in
  * graph of 16 gated rounds: one host synchronisation per 16 rounds. */
 b2sr_status b2sr_sssp(b2sr_handle h, const float* weights, int32_t src, float* dist, int max_iters,
                       void* stream);
+
+/* SSSP by frontier-driven push (Sec. V SSSP; the same fixed point as
+ * b2sr_sssp, reached by relaxing only the out-edges of the vertices whose
+ * distance dropped in the previous round).  It reads the transpose:
+ *   hT         B2SR of A^T (tile-row J lists the out-edges of vertices
+ *              kJ .. kJ+k-1); for a symmetric matrix, the matrix's own handle
+ *   weights_t  fp32 weights in set-bit order of hT (b2sr_weights_from_csr on
+ *              the transposed CSR; for symmetric weights, those of the
+ *              matrix), non-negative, or NULL for unit weights
+ *   dist       device float[n]: 0 at src, +inf if unreachable
+ * Each round is one launch over the active tile-rows only, so a round costs
+ * what its frontier touches.  Distances are updated with integer atomicMin on
+ * the float bits; the order of updates changes the number of rounds, never
+ * the result (bit-exact).  Rounds run as a CUDA graph of 8 gated rounds: one
+ * host synchronisation per 8 rounds.  B2SR_ERR_NOT_CONVERGED past max_iters
+ * rounds (<= 0: n). */
+b2sr_status b2sr_sssp_push(b2sr_handle hT, const float* weights_t, int32_t src, float* dist, int max_iters,
+                           void* stream);
 
 /* PageRank (Sec. V PR): x^0 = 1/n, then `iters` steps of
  *   x_i <- (1-d) t_i + d * sum_{j: A_ij=1} x_j / outdeg(j)

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libb2sr.so")
 
 BOOL_OR_AND, PLUS_TIMES, MIN_PLUS = 0, 1, 2
-VEC_BITS, VEC_I32, VEC_F32 = 0, 1, 2
+VEC_BITS, VEC_I32, VEC_F32, VEC_BITS64 = 0, 1, 2, 3
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_TILE", 3: "OOM", 4: "CUDA", 5: "NOT_CONVERGED",
           6: "ADMISSION_REFUSED", 7: "ABORTED"}
 WORD_BYTES = {4: 1, 8: 1, 16: 2, 32: 4}
@@ -87,6 +87,7 @@ def _load() -> ctypes.CDLL:
         "b2sr_bfs_sources": (c_int, [p, p, c_int, p, c_int, p]),
         "b2sr_from_csr_batch": (c_int, [c_int, p, p, p, p, c_int, p, pp, p]),
         "b2sr_sssp": (c_int, [p, p, i32, p, c_int, p]),
+        "b2sr_sssp_push": (c_int, [p, p, i32, p, c_int, p]),
         "b2sr_pagerank": (c_int, [p, f32, c_int, p, p, p]),
         "b2sr_cc": (c_int, [p, p, c_int, p]),
         "b2sr_tc": (c_int, [p, p, p]),
@@ -383,6 +384,15 @@ def b2sr_cc(m: Matrix, labels: Optional[torch.Tensor] = None, max_iters: int = 0
         labels = torch.empty(max(m.n, 1), dtype=torch.int32, device=_dev())
     _check(lib.b2sr_cc(m.handle, _ptr(labels), int(max_iters), _stream(stream)))
     return labels[: m.n]
+
+
+def b2sr_sssp_push(mT: Matrix, src: int, weights_t: Optional[torch.Tensor] = None,
+                   dist: Optional[torch.Tensor] = None, max_iters: int = 0, stream=None) -> torch.Tensor:
+    """Push SSSP on the transpose handle (the matrix itself when symmetric)."""
+    if dist is None:
+        dist = torch.empty(max(mT.n, 1), dtype=torch.float32, device=_dev())
+    _check(lib.b2sr_sssp_push(mT.handle, _ptr(weights_t), int(src), _ptr(dist), int(max_iters), _stream(stream)))
+    return dist[: mT.n]
 
 
 def b2sr_tc(m: Matrix, count: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:

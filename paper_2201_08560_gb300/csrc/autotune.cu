@@ -18,6 +18,8 @@ namespace b2sr {
 b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, const void* x, b2sr_vec out_kind,
                           void* y, const uint32_t* mask, int comp, const float* weights, cudaStream_t s,
                           const int32_t* gate);
+b2sr_status spmm64_dispatch(b2sr_matrix* h, const uint64_t* X, uint64_t* Y, const uint64_t* M, int comp,
+                            cudaStream_t s, const int32_t* gate);
 
 static const int kTileDims[4] = {4, 8, 16, 32};
 
@@ -175,6 +177,7 @@ __global__ void trial_vector_kernel(uint32_t* v, int64_t words, int kind) {
 
 static bool scheme_ok(b2sr_semiring sr, b2sr_vec in, b2sr_vec* out) {
     if (sr == B2SR_BOOL_OR_AND && in == B2SR_VEC_BITS) { *out = B2SR_VEC_BITS; return true; }
+    if (sr == B2SR_BOOL_OR_AND && in == B2SR_VEC_BITS64) { *out = B2SR_VEC_BITS64; return true; }
     if (sr == B2SR_PLUS_TIMES && in == B2SR_VEC_BITS) { *out = B2SR_VEC_I32; return true; }
     if (sr == B2SR_PLUS_TIMES && in == B2SR_VEC_F32) { *out = B2SR_VEC_F32; return true; }
     if (sr == B2SR_MIN_PLUS && (in == B2SR_VEC_F32 || in == B2SR_VEC_I32)) { *out = in; return true; }
@@ -182,10 +185,20 @@ static bool scheme_ok(b2sr_semiring sr, b2sr_vec in, b2sr_vec* out) {
 }
 
 static bool has_staged(int k, b2sr_semiring sr, b2sr_vec in) {
-    return k <= 16 && in != B2SR_VEC_BITS && (sr == B2SR_PLUS_TIMES || sr == B2SR_MIN_PLUS);
+    return k <= 16 && in != B2SR_VEC_BITS &&
+           (sr == B2SR_PLUS_TIMES || sr == B2SR_MIN_PLUS || in == B2SR_VEC_BITS64);
 }
 
-static int64_t vec_words(int32_t n, b2sr_vec kind) { return kind == B2SR_VEC_BITS ? ceil_div(n, 32) : n; }
+static int64_t vec_words(int32_t n, b2sr_vec kind) {
+    return kind == B2SR_VEC_BITS ? ceil_div(n, 32) : kind == B2SR_VEC_BITS64 ? 2 * (int64_t)n : n;
+}
+
+static b2sr_status run_scheme(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in, b2sr_vec out, const void* x, void* y,
+                              cudaStream_t s) {
+    if (in == B2SR_VEC_BITS64)
+        return spmm64_dispatch(h, static_cast<const uint64_t*>(x), static_cast<uint64_t*>(y), nullptr, 0, s, nullptr);
+    return spmv_dispatch(h, sr, in, x, out, y, nullptr, 0, nullptr, s, nullptr);
+}
 
 // Mean time of `trials` SpMVs of the scheme on h (after one untimed call).
 static b2sr_status time_trials(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in, b2sr_vec out, const void* x, void* y,
@@ -194,10 +207,10 @@ static b2sr_status time_trials(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in, b2
     B2SR_CUDA_TRY(cudaEventCreate(&e0));
     cudaError_t e = cudaEventCreate(&e1);
     b2sr_status st = e == cudaSuccess ? B2SR_OK : cuda_fail(e, "cudaEventCreate");
-    if (st == B2SR_OK) st = spmv_dispatch(h, sr, in, x, out, y, nullptr, 0, nullptr, s, nullptr);
+    if (st == B2SR_OK) st = run_scheme(h, sr, in, out, x, y, s);
     if (st == B2SR_OK && (e = cudaEventRecord(e0, s)) != cudaSuccess) st = cuda_fail(e, "cudaEventRecord");
     for (int t = 0; t < trials && st == B2SR_OK; ++t)
-        st = spmv_dispatch(h, sr, in, x, out, y, nullptr, 0, nullptr, s, nullptr);
+        st = run_scheme(h, sr, in, out, x, y, s);
     if (st == B2SR_OK && (e = cudaEventRecord(e1, s)) != cudaSuccess) st = cuda_fail(e, "cudaEventRecord");
     if (st == B2SR_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) st = cuda_fail(e, "cudaEventSynchronize");
     float ms = 0.0f;

@@ -750,8 +750,15 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
 // closes tiles as the walk passes them.  Lanes with fewer set bits finish
 // early instead of idling through per-word loops.
 // ---------------------------------------------------------------------------
+// Resident blocks the gather kernel is compiled for: wide (16-byte) values
+// need the registers of two blocks per SM rather than three.
 template <int K, class SEM>
-__global__ void __launch_bounds__(kSpmvThreads, (K >= 16 ? 2 : 3)) spmv_gather_kernel(SpmvGeom g, SEM sem,
+constexpr int gather_min_blocks() {
+    return (K >= 16 || sizeof(typename SEM::V) > 8) ? 2 : 3;
+}
+
+template <int K, class SEM>
+__global__ void __launch_bounds__(kSpmvThreads, (gather_min_blocks<K, SEM>())) spmv_gather_kernel(SpmvGeom g, SEM sem,
                                                                    Partials<typename SEM::V> part) {
     using S = ChunkShape<K>;
     using V = typename SEM::V;

@@ -205,3 +205,57 @@ def test_cc_disjoint_unions(B):
             lab = to_np(B.b2sr_cc(m))
             np.testing.assert_array_equal(lab, oracle.cc(u))
             assert len(set(lab.tolist())) == len(parts)
+
+
+def transposed(g, w):
+    """A^T of a canonical CSR, with each entry's weight carried over."""
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.rowptr))
+    order = np.lexsort((rows, g.colind.astype(np.int64)))
+    rp = np.zeros(g.n + 1, dtype=np.int32)
+    np.cumsum(np.bincount(g.colind, minlength=g.n), out=rp[1:])
+    return graphs.CSR(g.n, rp, rows[order].astype(np.int32)), w[order]
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("gi", range(len(GRAPH_IDS)), ids=GRAPH_IDS)
+def test_sssp_push(B, k, gi):
+    """Push SSSP on the transpose: unit weights give BFS levels, lattice
+    weights the oracle's distances bit for bit, continuous weights exactly the
+    pull rounds' result (both reach the same least fixed point of the fp32
+    relaxation)."""
+    g = oracle.canonicalize(small_graphs()[gi])
+    rng = np.random.default_rng(gi + 100)
+    w_grid = (1 + rng.integers(0, 99 * 16, g.colind.size) / 16).astype(np.float32)
+    w_cont = rng.uniform(1.0, 100.0, g.colind.size).astype(np.float32)
+    rp, ci = to_dev(g.rowptr), to_dev(g.colind)
+    src = min(1, g.n - 1)
+    with B.b2sr_from_csr(g.n, rp, ci, k) as m:
+        gT, _ = transposed(g, w_grid)
+        rpT, ciT = to_dev(gT.rowptr), to_dev(gT.colind)
+        with B.b2sr_from_csr(g.n, rpT, ciT, k) as mT:
+            d = to_np(B.b2sr_sssp_push(mT, 0))
+            lv = oracle.bfs(g, 0).astype(np.float64)
+            lv[lv < 0] = np.inf
+            np.testing.assert_array_equal(d.astype(np.float64), lv)
+            for w, exact in ((w_grid, True), (w_cont, False)):
+                _, wT = transposed(g, w)
+                wbT = B.b2sr_weights_from_csr(mT, rpT, ciT, to_dev(wT))
+                d = to_np(B.b2sr_sssp_push(mT, src, wbT))
+                if exact:
+                    np.testing.assert_array_equal(d.astype(np.float64), oracle.sssp(g, src, w))
+                else:
+                    wb = B.b2sr_weights_from_csr(m, rp, ci, to_dev(w))
+                    np.testing.assert_array_equal(d.view(np.uint32), to_np(B.b2sr_sssp(m, src, wb)).view(np.uint32))
+
+
+def test_sssp_push_symmetric_uses_own_handle(B):
+    g = graphs.grid2d(60, 70)
+    w = graphs.symmetric_weights(g, 3)
+    rp, ci = csr_dev(g)
+    with B.b2sr_from_csr(g.n, rp, ci, 8) as m:
+        wb = B.b2sr_weights_from_csr(m, rp, ci, to_dev(w))
+        d = to_np(B.b2sr_sssp_push(m, 0, wb))
+        np.testing.assert_array_equal(d.astype(np.float64), oracle.sssp(g, 0, w))
+        np.testing.assert_array_equal(d, to_np(B.b2sr_sssp(m, 0, wb)))
+        with pytest.raises(B.B2SRError):
+            B.b2sr_sssp_push(m, 0, wb, max_iters=5)

@@ -215,3 +215,17 @@ def test_directed_bfs_sssp_match_scipy_on_transpose(seed):
         np.testing.assert_allclose(oracle.sssp(g, s, w), d, rtol=1e-12)
         hops = csgraph.shortest_path(At, method="D", directed=True, unweighted=True, indices=s)
         np.testing.assert_array_equal(oracle.bfs(g, s), np.where(np.isinf(hops), -1, hops).astype(np.int32))
+
+
+def test_fullsize_tc_golden_input_is_reproduced():
+    """The stored full-size triangle count belongs to the graph the seeded
+    generator makes on this machine (same sizes and CSR digest)."""
+    import hashlib
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fullsize_tc.json")))
+    g = graphs.rmat(18, 32, seed=2)
+    h = hashlib.sha256()
+    h.update(g.rowptr.astype("<i8").tobytes())
+    h.update(g.colind.astype("<i4").tobytes())
+    assert (g.n, len(g.colind), h.hexdigest()) == (gold["n"], gold["nnz"], gold["csr_sha256"])
