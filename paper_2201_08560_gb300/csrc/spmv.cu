@@ -114,10 +114,34 @@ struct SmemAcc {
 // warp shuffles of accumulator values (scalars, and the four-column blocks of
 // SemPlus4 one component at a time)
 // ---------------------------------------------------------------------------
-struct D4 {  // fp64 join type of a four-column block
-    double v[4];
-    D4() = default;
-    __device__ __forceinline__ D4(float4 a) : v{a.x, a.y, a.z, a.w} {}
+// Join type of the plus-times partials of rows that cross chunks: a
+// compensated fp32 sum.  Each addition is Knuth's TwoSum of the leading parts
+// (the exact rounding error, whatever the magnitudes), added to the carried
+// error terms; the rounding is spelled out so no contraction or reordering
+// can change it.  fp32 keeps the join off the fp64 pipe, which is narrow on
+// GB300; the compensation keeps it as accurate as an fp64 join for the few
+// hundred partials a row can have.
+struct CSum {
+    float s, c;
+    CSum() = default;
+    __device__ __forceinline__ CSum(float a) : s(a), c(0.0f) {}
+    __device__ __forceinline__ explicit operator float() const { return __fadd_rn(s, c); }
+};
+
+__device__ __forceinline__ CSum csum_add(CSum a, CSum b) {
+    const float t = __fadd_rn(a.s, b.s);
+    const float bp = __fsub_rn(t, a.s);
+    const float e = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(b.s, bp));
+    CSum r;
+    r.s = t;
+    r.c = __fadd_rn(__fadd_rn(a.c, b.c), e);
+    return r;
+}
+
+struct CSum4 {  // the same for a four-column block, column by column
+    CSum v[4];
+    CSum4() = default;
+    __device__ __forceinline__ CSum4(float4 a) : v{CSum(a.x), CSum(a.y), CSum(a.z), CSum(a.w)} {}
     __device__ __forceinline__ explicit operator float4() const {
         return make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
     }
@@ -133,8 +157,14 @@ __device__ __forceinline__ float4 shfl_up(float4 v, int d) {
 __device__ __forceinline__ float4 shfl_xor(float4 v, int o) {
     return make_float4(shfl_xor(v.x, o), shfl_xor(v.y, o), shfl_xor(v.z, o), shfl_xor(v.w, o));
 }
-__device__ __forceinline__ D4 shfl_xor(D4 a, int o) {
-    D4 r;
+__device__ __forceinline__ CSum shfl_xor(CSum a, int o) {
+    CSum r;
+    r.s = shfl_xor(a.s, o);
+    r.c = shfl_xor(a.c, o);
+    return r;
+}
+__device__ __forceinline__ CSum4 shfl_xor(CSum4 a, int o) {
+    CSum4 r;
 #pragma unroll
     for (int i = 0; i < 4; ++i) r.v[i] = shfl_xor(a.v[i], o);
     return r;
@@ -256,12 +286,12 @@ struct SemCount {
 };
 
 // bmv_bin_full_full over plus-times: float in, float out; partials of rows
-// that cross chunks are joined in fp64
+// that cross chunks are joined with a compensated fp32 sum (CSum)
 template <int K>
 struct SemPlus {
     using V = float;
     using G = float;
-    using J = double;
+    using J = CSum;
     static constexpr int NV = K;
     static constexpr bool kGather = true;
     static constexpr bool kMayWeight = false;
@@ -276,28 +306,29 @@ struct SemPlus {
     __device__ const int32_t* voffs() const { return nullptr; }
     __device__ V ident() const { return 0.0f; }
     __device__ V comb(V a, V b) const { return a + b; }
-    __device__ J jcomb(J a, J b) const { return a + b; }
+    __device__ J jcomb(J a, J b) const { return csum_add(a, b); }
     __device__ V apply(V acc, G xv, float) const { return acc + xv; }
     __device__ V contrib(G xv, float) const { return xv; }
+    __device__ void store_row(int32_t R, int r, V v) const {
+        int64_t i = (int64_t)R * K + r;
+        if (i < n) y[i] = mask_allows(mask, comp, i) ? v : 0.0f;
+    }
     template <class A>
     __device__ void store(int32_t R, const A& acc) const {
 #pragma unroll
-        for (int r = 0; r < K; ++r) {
-            int64_t i = (int64_t)R * K + r;
-            if (i < n) y[i] = mask_allows(mask, comp, i) ? (float)acc.get(r) : 0.0f;
-        }
+        for (int r = 0; r < K; ++r) store_row(R, r, acc.get(r));
     }
 };
 
 // plus-times over a block of four fp32 columns (vertex-major: x[v] holds the
 // four columns' values of vertex v).  Every component is added in exactly the
-// order SemPlus adds a single column, and joined in fp64 the same way, so
-// column b of the result is bitwise the SemPlus result for column b.
+// order SemPlus adds a single column, and joined the same way, so column b
+// of the result is bitwise the SemPlus result for column b.
 template <int K>
 struct SemPlus4 {
     using V = float4;
     using G = float4;
-    using J = D4;
+    using J = CSum4;
     static constexpr int NV = K;
     static constexpr bool kGather = true;
     static constexpr bool kMayWeight = false;
@@ -315,18 +346,19 @@ struct SemPlus4 {
     __device__ J jcomb(J a, J b) const {
         J r;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) r.v[i] = a.v[i] + b.v[i];
+        for (int i = 0; i < 4; ++i) r.v[i] = csum_add(a.v[i], b.v[i]);
         return r;
     }
     __device__ V apply(V acc, G xv, float) const { return comb(acc, xv); }
     __device__ V contrib(G xv, float) const { return xv; }
+    __device__ void store_row(int32_t R, int r, V v) const {
+        int64_t i = (int64_t)R * K + r;
+        if (i < n) y[i] = mask_allows(mask, comp, i) ? v : ident();
+    }
     template <class A>
     __device__ void store(int32_t R, const A& acc) const {
 #pragma unroll
-        for (int r = 0; r < K; ++r) {
-            int64_t i = (int64_t)R * K + r;
-            if (i < n) y[i] = mask_allows(mask, comp, i) ? acc.get(r) : ident();
-        }
+        for (int r = 0; r < K; ++r) store_row(R, r, acc.get(r));
     }
 };
 
@@ -356,13 +388,14 @@ struct SemMinPlus {
     __device__ J jcomb(J a, J b) const { return fminf(a, b); }
     __device__ V apply(V acc, G xv, float wv) const { return fminf(acc, xv + wv); }
     __device__ V contrib(G xv, float wv) const { return xv + wv; }
+    __device__ void store_row(int32_t R, int r, V v) const {
+        int64_t i = (int64_t)R * K + r;
+        if (i < n) y[i] = mask_allows(mask, comp, i) ? fminf(__ldg(x + i), v) : INFINITY;
+    }
     template <class A>
     __device__ void store(int32_t R, const A& acc) const {
 #pragma unroll
-        for (int r = 0; r < K; ++r) {
-            int64_t i = (int64_t)R * K + r;
-            if (i < n) y[i] = mask_allows(mask, comp, i) ? fminf(__ldg(x + i), (float)acc.get(r)) : INFINITY;
-        }
+        for (int r = 0; r < K; ++r) store_row(R, r, acc.get(r));
     }
 };
 
@@ -389,13 +422,14 @@ struct SemMinI32 {
     __device__ J jcomb(J a, J b) const { return min(a, b); }
     __device__ V apply(V acc, G xv, float) const { return min(acc, xv); }
     __device__ V contrib(G xv, float) const { return xv; }
+    __device__ void store_row(int32_t R, int r, V v) const {
+        int64_t i = (int64_t)R * K + r;
+        if (i < n) y[i] = mask_allows(mask, comp, i) ? min(__ldg(x + i), v) : INT_MAX;
+    }
     template <class A>
     __device__ void store(int32_t R, const A& acc) const {
 #pragma unroll
-        for (int r = 0; r < K; ++r) {
-            int64_t i = (int64_t)R * K + r;
-            if (i < n) y[i] = mask_allows(mask, comp, i) ? min(__ldg(x + i), (int32_t)acc.get(r)) : INT_MAX;
-        }
+        for (int r = 0; r < K; ++r) store_row(R, r, acc.get(r));
     }
 };
 
@@ -422,17 +456,17 @@ struct SemOr64 {
     __device__ J jcomb(J a, J b) const { return a | b; }
     __device__ V apply(V acc, G xv, float) const { return acc | xv; }
     __device__ V contrib(G xv, float) const { return xv; }
+    __device__ void store_row(int32_t R, int r, V v) const {
+        int64_t i = (int64_t)R * K + r;
+        if (i < n) {
+            if (mask) v &= comp ? ~__ldg(mask + i) : __ldg(mask + i);
+            y[i] = v;
+        }
+    }
     template <class A>
     __device__ void store(int32_t R, const A& acc) const {
 #pragma unroll
-        for (int r = 0; r < K; ++r) {
-            int64_t i = (int64_t)R * K + r;
-            if (i < n) {
-                V v = acc.get(r);
-                if (mask) v &= comp ? ~__ldg(mask + i) : __ldg(mask + i);
-                y[i] = v;
-            }
-        }
+        for (int r = 0; r < K; ++r) store_row(R, r, acc.get(r));
     }
 };
 
@@ -848,7 +882,7 @@ __global__ void __launch_bounds__(kSpmvThreads, (gather_min_blocks<K, SEM>())) s
             const int s = gbase + j;
             cp_async_gather<sizeof(G)>(sx + s, xt + bit % RB);
             if (sem.weighted) cp_async_gather<4>(sw + s, wt + qb);
-            stag[s] = (uint8_t)(i * K + (wi % TW) * RPW + bit / RB);
+            stag[s] = (uint8_t)(wi * RPW + bit / RB);  // = i * K + (wi % TW) * RPW + row in word
             ++qb;
         }
         cp_async_commit();
@@ -905,17 +939,14 @@ __global__ void __launch_bounds__(kSpmvThreads, (gather_min_blocks<K, SEM>())) s
                         acc.set(v, (lane & o) ? sem.comb(other, acc.get(v)) : sem.comb(acc.get(v), other));
                     }
                 }
-                if (lane == 0) {
+                if (lane < K) {  // every lane holds the totals: lane r writes row r
+                    V v = acc.get(0);
+#pragma unroll
+                    for (int u = 1; u < K; ++u) v = lane == u ? acc.get(u) : v;
                     const bool started = a >= ls.cs, ended = b <= ls.ce;
-                    if (started && ended) {
-                        sem.store(R, acc);
-                    } else if (!started) {
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) part.val_first[c * NV + v] = acc.get(v);
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) part.val_last[c * NV + v] = acc.get(v);
-                    }
+                    if (started && ended) sem.store_row(R, lane, v);
+                    else if (!started) part.val_first[c * NV + lane] = v;
+                    else part.val_last[c * NV + lane] = v;
                 }
             }
             return;

@@ -5,8 +5,9 @@ relative error of the fp64 oracle.  The tolerance follows from the kernel's
 arithmetic: with non-negative inputs, a fixed-order fp32 sum of m terms has
 relative error at most about m * 2^-24; each lane adds at most P*k = 64 set
 bits in sequence, the warp joins 32 lanes in a 5-level tree, and partials of
-rows that cross chunks are joined in fp64, so m <= 69 and the bound is
-69 * 2^-24 = 4.1e-6 < 1e-5."""
+rows that cross chunks are joined by a compensated (TwoSum) fp32 sum, which
+adds at most 2 roundings, so m <= 71 and the bound is 71 * 2^-24 = 4.2e-6 <
+1e-5."""
 import numpy as np
 import pytest
 import torch
