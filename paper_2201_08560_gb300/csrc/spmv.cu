@@ -1029,6 +1029,19 @@ __global__ void spmv_fixup_kernel(const int32_t* __restrict__ split, int64_t nsh
     constexpr int NV = SEM::NV;
     if (gated_off(gate)) return;
     if ((int64_t)blockIdx.x < short_blocks) {
+        if constexpr (SEM::kGather) {
+            // value schemes: a thread per (row, value); the NV threads of a
+            // row read each partial's NV values side by side
+            const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+            const int64_t e = tid / NV;
+            const int v = (int)(tid % NV);
+            if (e >= nshort) return;
+            const int32_t R = split[3 * e], ca = split[3 * e + 1], cb = split[3 * e + 2];
+            J acc = (J)part.val_last[(int64_t)ca * NV + v];
+            for (int64_t q = ca + 1; q <= cb; ++q) acc = sem.jcomb(acc, (J)part.val_first[q * NV + v]);
+            sem.store_row(R, v, (V)acc);
+            return;
+        }
         const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         if (e >= nshort) return;
         const int32_t R = split[3 * e], ca = split[3 * e + 1], cb = split[3 * e + 2];
@@ -1078,7 +1091,7 @@ template <int K, class SEM>
 static b2sr_status launch_fixup(const b2sr_matrix* h, const SEM& sem, Partials<typename SEM::V> part,
                                 cudaStream_t s, const int32_t* gate) {
     if (h->nsplit_short + h->nsplit_long == 0) return B2SR_OK;
-    const int64_t short_blocks = ceil_div(h->nsplit_short, 256);
+    const int64_t short_blocks = ceil_div(h->nsplit_short * (SEM::kGather ? SEM::NV : 1), 256);
     const int64_t long_blocks = ceil_div(h->nsplit_long, 8);
     spmv_fixup_kernel<K, SEM><<<(unsigned)(short_blocks + long_blocks), 256, 0, s>>>(
         h->split, h->nsplit_short, h->nsplit_long, short_blocks, sem, part, gate);
