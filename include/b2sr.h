@@ -381,14 +381,17 @@ b2sr_status b2sr_sssp(b2sr_handle h, const float* weights, int32_t src, float* d
  *              the transposed CSR; for symmetric weights, those of the
  *              matrix), non-negative, or NULL for unit weights
  *   dist       device float[n]: 0 at src, +inf if unreachable
- * Each round is one launch over the active tile-rows only, so a round costs
- * what its frontier touches.  Distances are updated with integer atomicMin on
- * the float bits; the order of updates changes the number of rounds, never
- * the result (bit-exact).  Rounds run as a CUDA graph of 8 gated rounds: one
- * host synchronisation per 8 rounds.  B2SR_ERR_NOT_CONVERGED past max_iters
- * rounds (<= 0: n). */
-b2sr_status b2sr_sssp_push(b2sr_handle hT, const float* weights_t, int32_t src, float* dist, int max_iters,
-                           void* stream);
+ *   delta      > 0: the buckets of delta-stepping (Sec. V names it): a round
+ *              relaxes only active vertices closer than a threshold, which
+ *              starts at delta and grows by delta whenever a round has none;
+ *              <= 0: every active vertex every round (Bellman-Ford frontier)
+ * A round touches only the active tile-rows.  Distances are updated with
+ * integer atomicMin on the float bits; the order of updates and delta change
+ * the number of rounds, never the result (bit-exact).  Rounds run as a CUDA
+ * graph of 32 gated rounds: one host synchronisation per 32 rounds.
+ * B2SR_ERR_NOT_CONVERGED past max_iters rounds (<= 0: n). */
+b2sr_status b2sr_sssp_push(b2sr_handle hT, const float* weights_t, int32_t src, float* dist, float delta,
+                           int max_iters, void* stream);
 
 /* PageRank (Sec. V PR): x^0 = 1/n, then `iters` steps of
  *   x_i <- (1-d) t_i + d * sum_{j: A_ij=1} x_j / outdeg(j)

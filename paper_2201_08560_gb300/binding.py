@@ -87,7 +87,7 @@ def _load() -> ctypes.CDLL:
         "b2sr_bfs_sources": (c_int, [p, p, c_int, p, c_int, p]),
         "b2sr_from_csr_batch": (c_int, [c_int, p, p, p, p, c_int, p, pp, p]),
         "b2sr_sssp": (c_int, [p, p, i32, p, c_int, p]),
-        "b2sr_sssp_push": (c_int, [p, p, i32, p, c_int, p]),
+        "b2sr_sssp_push": (c_int, [p, p, i32, p, f32, c_int, p]),
         "b2sr_pagerank": (c_int, [p, f32, c_int, p, p, p]),
         "b2sr_cc": (c_int, [p, p, c_int, p]),
         "b2sr_tc": (c_int, [p, p, p]),
@@ -387,11 +387,14 @@ def b2sr_cc(m: Matrix, labels: Optional[torch.Tensor] = None, max_iters: int = 0
 
 
 def b2sr_sssp_push(mT: Matrix, src: int, weights_t: Optional[torch.Tensor] = None,
-                   dist: Optional[torch.Tensor] = None, max_iters: int = 0, stream=None) -> torch.Tensor:
-    """Push SSSP on the transpose handle (the matrix itself when symmetric)."""
+                   dist: Optional[torch.Tensor] = None, delta: float = 0.0, max_iters: int = 0,
+                   stream=None) -> torch.Tensor:
+    """Push SSSP on the transpose handle (the matrix itself when symmetric);
+    delta > 0 turns on delta-stepping buckets."""
     if dist is None:
         dist = torch.empty(max(mT.n, 1), dtype=torch.float32, device=_dev())
-    _check(lib.b2sr_sssp_push(mT.handle, _ptr(weights_t), int(src), _ptr(dist), int(max_iters), _stream(stream)))
+    _check(lib.b2sr_sssp_push(mT.handle, _ptr(weights_t), int(src), _ptr(dist), float(delta), int(max_iters),
+                              _stream(stream)))
     return dist[: mT.n]
 
 

@@ -62,21 +62,32 @@ __device__ __forceinline__ uint32_t tile_row(const uint32_t* w, int r) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(256) push_relax_kernel(const int32_t* __restrict__ rowptr,
-                                                         const int32_t* __restrict__ colind,
-                                                         const uint8_t* __restrict__ tiles,
-                                                         const int32_t* __restrict__ voff, const float* __restrict__ w,
-                                                         int32_t n, PushSide cur, PushSide nxt, int32_t* flag,
-                                                         float* dist, const int32_t* gate) {
+__device__ __forceinline__ void relax_round(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                                            const uint8_t* __restrict__ tiles, const int32_t* __restrict__ voff,
+                                            const float* __restrict__ w, PushSide cur, PushSide nxt, int32_t* flag,
+                                            float* dist, const float* theta, int32_t* relaxed, int64_t warp0,
+                                            int64_t warps) {
     constexpr int TB = K * (K <= 8 ? 1 : (K == 16 ? 2 : 4));  // bytes per tile
     constexpr int TW = (TB + 3) / 4;
-    if (gate && *gate == 0) return;
-    const int32_t ncur = *cur.count;
+    const int32_t ncur = *reinterpret_cast<volatile int32_t*>(cur.count);
+    const float th = theta ? *reinterpret_cast<const volatile float*>(theta) : INFINITY;
     const int lane = (int)lane_id();
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < ncur; e += warps) {
+    for (int64_t e = warp0; e < ncur; e += warps) {
         const int32_t J = cur.list[e];
-        const uint32_t amask = seg_bits<K>(cur.act, J);
+        uint32_t amask = seg_bits<K>(cur.act, J);
+        if (theta) {
+            // active vertices at or past the threshold wait for a later round
+            uint32_t defer = 0u;
+            if (lane < K && ((amask >> lane) & 1u) && dist[J * K + lane] >= th) defer = 1u << lane;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) defer |= __shfl_xor_sync(0xffffffffu, defer, o);
+            if (defer) {
+                if (lane < K && ((defer >> lane) & 1u)) atomicOr(nxt.act + ((J * K + lane) >> 5), 1u << ((J * K + lane) & 31));
+                if (lane == 0 && atomicExch(flag + J, 1) == 0) nxt.list[atomicAdd(nxt.count, 1)] = J;
+            }
+            amask &= ~defer;
+            if (amask && lane == 0) *relaxed = 1;
+        }
         const int32_t t0 = rowptr[J], t1 = rowptr[J + 1];
         for (int32_t t = t0 + lane; t < t1; t += 32) {
             uint32_t wd[TW];
@@ -115,27 +126,57 @@ __global__ void __launch_bounds__(256) push_relax_kernel(const int32_t* __restri
     }
 }
 
+template <int K>
+__global__ void __launch_bounds__(256) push_relax_kernel(const int32_t* __restrict__ rowptr,
+                                                         const int32_t* __restrict__ colind,
+                                                         const uint8_t* __restrict__ tiles,
+                                                         const int32_t* __restrict__ voff, const float* __restrict__ w,
+                                                         PushSide cur, PushSide nxt, int32_t* flag, float* dist,
+                                                         const float* theta, int32_t* relaxed, const int32_t* gate) {
+    if (gate && *gate == 0) return;
+    relax_round<K>(rowptr, colind, tiles, voff, w, cur, nxt, flag, dist, theta, relaxed,
+                   ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, (int64_t)gridDim.x * (blockDim.x >> 5));
+}
+
 // After a round: the consumed active set is cleared (it becomes the next
 // round's empty "next" set) and the new list's membership flags are reset.
 template <int K>
-__global__ void push_epilogue_kernel(PushSide cur, PushSide nxt, int32_t* flag, const int32_t* gate) {
-    if (gate && *gate == 0) return;
-    const int32_t ncur = *cur.count, nnext = *nxt.count;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncur || i < nnext;
-         i += (int64_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void epilogue_round(PushSide cur, PushSide nxt, int32_t* flag, int64_t t0, int64_t nt) {
+    const int32_t ncur = *reinterpret_cast<volatile int32_t*>(cur.count);
+    const int32_t nnext = *reinterpret_cast<volatile int32_t*>(nxt.count);
+    for (int64_t i = t0; i < ncur || i < nnext; i += nt) {
         if (i < ncur) clear_seg<K>(cur.act, cur.list[i]);
         if (i < nnext) flag[nxt.list[i]] = 0;
     }
 }
 
-// The next round reads `nxt`; the list it builds starts empty.  The loop
-// stops when a round improved nothing.
-__global__ void push_advance_kernel(int32_t* cur_count, const int32_t* next_count, int32_t* active, int32_t* rounds) {
-    if (threadIdx.x == 0 && blockIdx.x == 0 && *active) {
-        *cur_count = 0;
-        *active = *next_count > 0 ? 1 : 0;
-        *rounds += 1;
+template <int K>
+__global__ void push_epilogue_kernel(PushSide cur, PushSide nxt, int32_t* flag, const int32_t* gate) {
+    if (gate && *gate == 0) return;
+    epilogue_round<K>(cur, nxt, flag, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                      (int64_t)gridDim.x * blockDim.x);
+}
+
+// After a round: the next round reads `nxt`, and the list it builds starts
+// empty; the loop stops when a round improved nothing.  With a threshold, a
+// round that relaxed nothing (everything active waits) raises it by delta.
+__device__ __forceinline__ void advance_round(int32_t* cur_count, const int32_t* next_count, int32_t* active,
+                                              int32_t* rounds, float* theta, int32_t* relaxed, float delta) {
+    *reinterpret_cast<volatile int32_t*>(cur_count) = 0;
+    const int32_t nn = *reinterpret_cast<const volatile int32_t*>(next_count);
+    *reinterpret_cast<volatile int32_t*>(active) = nn > 0 ? 1 : 0;
+    if (theta) {
+        if (!*reinterpret_cast<volatile int32_t*>(relaxed) && nn > 0)
+            *reinterpret_cast<volatile float*>(theta) = *reinterpret_cast<volatile float*>(theta) + delta;
+        *reinterpret_cast<volatile int32_t*>(relaxed) = 0;
     }
+    *rounds += 1;
+}
+
+__global__ void push_advance_kernel(int32_t* cur_count, const int32_t* next_count, int32_t* active, int32_t* rounds,
+                                    float* theta, int32_t* relaxed, float delta) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && *active)
+        advance_round(cur_count, next_count, active, rounds, theta, relaxed, delta);
 }
 
 __global__ void push_init_kernel(float* dist, int32_t n, int32_t src) {
@@ -154,7 +195,8 @@ static b2sr_status with_tile(int k, F&& f) {
     }
 }
 
-b2sr_status sssp_push(b2sr_matrix* hT, const float* w, int32_t src, float* dist, int max_iters, cudaStream_t s) {
+b2sr_status sssp_push(b2sr_matrix* hT, const float* w, int32_t src, float* dist, float delta, int max_iters,
+                      cudaStream_t s) {
     const int32_t n = hT->n;
     const int32_t ntr = hT->ntr;
     if (w) B2SR_TRY(ensure_voff(hT, s));  // before capture: capture must not allocate for the handle
@@ -171,6 +213,9 @@ b2sr_status sssp_push(b2sr_matrix* hT, const float* w, int32_t src, float* dist,
     Bs.count = ctl + 1;
     int32_t* active = ctl + 2;
     int32_t* rounds_dev = ctl + 3;
+    // ctl[5]: threshold (float), ctl[6]: relaxed-this-round
+    float* theta = delta > 0.0f ? reinterpret_cast<float*>(ctl + 5) : nullptr;
+    int32_t* relaxed = ctl + 6;
     B2SR_CUDA_TRY(cudaMemsetAsync(base, 0, 2 * bw + 3 * lw + 256, s));
     push_init_kernel<<<grid_for(n), 256, 0, s>>>(dist, n, src);
     B2SR_LAUNCH_CHECK("push_init_kernel");
@@ -182,6 +227,7 @@ b2sr_status sssp_push(b2sr_matrix* hT, const float* w, int32_t src, float* dist,
     B2SR_CUDA_TRY(cudaMemcpyAsync(A.list, &seed_row, sizeof(int32_t), cudaMemcpyHostToDevice, s));
     B2SR_CUDA_TRY(cudaMemcpyAsync(A.count, &one, sizeof(int32_t), cudaMemcpyHostToDevice, s));
     B2SR_CUDA_TRY(cudaMemcpyAsync(active, &one, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    if (theta) B2SR_CUDA_TRY(cudaMemcpyAsync(theta, &delta, sizeof(float), cudaMemcpyHostToDevice, s));
     const int relax_grid = sm_count() * 8;  // warps stride over the active list
     const int64_t cap = max_iters > 0 ? max_iters : (int64_t)n + 1;
     int64_t rounds = 0;
@@ -189,17 +235,18 @@ b2sr_status sssp_push(b2sr_matrix* hT, const float* w, int32_t src, float* dist,
     const int32_t* voff = w ? hT->voff : nullptr;
     return with_tile(hT->k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
-        return run_captured(s, 8, cap + 1, active,
+        return run_captured(s, 32, cap + 1, active,
                             [&](cudaStream_t cs, int r) -> b2sr_status {
                                 const PushSide& cur = (r & 1) ? Bs : A;
                                 const PushSide& nxt = (r & 1) ? A : Bs;
                                 push_relax_kernel<K><<<relax_grid, 256, 0, cs>>>(hT->rowptr, hT->colind, hT->tiles,
-                                                                                voff, wts, n, cur, nxt, flag, dist,
-                                                                                active);
+                                                                                voff, wts, cur, nxt, flag, dist,
+                                                                                theta, relaxed, active);
                                 B2SR_LAUNCH_CHECK("push_relax_kernel");
                                 push_epilogue_kernel<K><<<grid_for(ntr), 256, 0, cs>>>(cur, nxt, flag, active);
                                 B2SR_LAUNCH_CHECK("push_epilogue_kernel");
-                                push_advance_kernel<<<1, 32, 0, cs>>>(cur.count, nxt.count, active, rounds_dev);
+                                push_advance_kernel<<<1, 32, 0, cs>>>(cur.count, nxt.count, active, rounds_dev,
+                                                                      theta, relaxed, delta);
                                 B2SR_LAUNCH_CHECK("push_advance_kernel");
                                 return B2SR_OK;
                             },
@@ -211,11 +258,12 @@ b2sr_status sssp_push(b2sr_matrix* hT, const float* w, int32_t src, float* dist,
 
 using namespace b2sr;
 
-extern "C" b2sr_status b2sr_sssp_push(b2sr_handle hT, const float* weights_t, int32_t src, float* dist,
+extern "C" b2sr_status b2sr_sssp_push(b2sr_handle hT, const float* weights_t, int32_t src, float* dist, float delta,
                                       int max_iters, void* stream) {
     clear_error();
     B2SR_TRY(check_handle(hT));
     if (src < 0 || src >= hT->n) return fail(B2SR_ERR_INVALID_ARG, "source out of range");
     if (!dist) return fail(B2SR_ERR_INVALID_ARG, "dist is NULL");
-    return sssp_push(hT, weights_t, src, dist, max_iters, to_stream(stream));
+    if (!(delta == delta)) return fail(B2SR_ERR_INVALID_ARG, "delta is NaN");
+    return sssp_push(hT, weights_t, src, dist, delta, max_iters, to_stream(stream));
 }

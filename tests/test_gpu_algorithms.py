@@ -2,6 +2,7 @@
 algorithms (BFS, multi-source BFS, SSSP, PageRank, CC, TC) against the oracle.
 Levels, labels and counts are bit-exact; PageRank and continuous-weight SSSP
 are within 1e-5 relative error of the fp64 oracle."""
+import itertools
 import math
 
 import numpy as np
@@ -237,10 +238,11 @@ def test_sssp_push(B, k, gi):
             lv = oracle.bfs(g, 0).astype(np.float64)
             lv[lv < 0] = np.inf
             np.testing.assert_array_equal(d.astype(np.float64), lv)
-            for w, exact in ((w_grid, True), (w_cont, False)):
+            np.testing.assert_array_equal(to_np(B.b2sr_sssp_push(mT, 0, delta=1.0)).astype(np.float64), lv)
+            for (w, exact), delta in itertools.product(((w_grid, True), (w_cont, False)), (0.0, 7.0, 100.0)):
                 _, wT = transposed(g, w)
                 wbT = B.b2sr_weights_from_csr(mT, rpT, ciT, to_dev(wT))
-                d = to_np(B.b2sr_sssp_push(mT, src, wbT))
+                d = to_np(B.b2sr_sssp_push(mT, src, wbT, delta=delta))
                 if exact:
                     np.testing.assert_array_equal(d.astype(np.float64), oracle.sssp(g, src, w))
                 else:
@@ -254,8 +256,9 @@ def test_sssp_push_symmetric_uses_own_handle(B):
     rp, ci = csr_dev(g)
     with B.b2sr_from_csr(g.n, rp, ci, 8) as m:
         wb = B.b2sr_weights_from_csr(m, rp, ci, to_dev(w))
-        d = to_np(B.b2sr_sssp_push(m, 0, wb))
-        np.testing.assert_array_equal(d.astype(np.float64), oracle.sssp(g, 0, w))
-        np.testing.assert_array_equal(d, to_np(B.b2sr_sssp(m, 0, wb)))
-        with pytest.raises(B.B2SRError):
-            B.b2sr_sssp_push(m, 0, wb, max_iters=5)
+        for delta in (0.0, 50.0):
+            d = to_np(B.b2sr_sssp_push(m, 0, wb, delta=delta))
+            np.testing.assert_array_equal(d.astype(np.float64), oracle.sssp(g, 0, w))
+            np.testing.assert_array_equal(d, to_np(B.b2sr_sssp(m, 0, wb)))
+            with pytest.raises(B.B2SRError):
+                B.b2sr_sssp_push(m, 0, wb, delta=delta, max_iters=5)

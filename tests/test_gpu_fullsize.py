@@ -98,7 +98,7 @@ def test_grid4096_sssp(B):
     rp, ci = csr_dev(g)
     with B.b2sr_from_csr(g.n, rp, ci, 8) as m:
         wb = B.b2sr_weights_from_csr(m, rp, ci, to_dev(w))
-        d = to_np(B.b2sr_sssp_push(m, 0, wb))      # the benchmark's driver (symmetric: own transpose)
+        d = to_np(B.b2sr_sssp_push(m, 0, wb, delta=400.0))   # the benchmark's driver and delta
     np.testing.assert_array_equal(d, oracle.sssp(g, 0, w).astype(np.float32))
 
 
