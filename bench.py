@@ -33,7 +33,9 @@ import numpy as np  # noqa: E402
 
 METRIC = "B2SR SpMV/BFS GTEPS & % HBM peak; TC edges/s; batched BFS queries/s vs plain"
 SCALE, EDGE_FACTOR, SEED = 20, 16, 1
-TILE = 8
+TILE = 4                 # B2SR tile_dim of the main workload ...
+SCHEDULE = 2             # ... and its SpMV schedule (b2sr_schedule DIRECT); see workload_desc
+SERVE_TILE = 8           # tile_dim of the serving and batching extras
 NSRC, PR_ITERS, DAMP = 16, 50, 0.85
 QUERIES_PER_STEP = 1 + NSRC + PR_ITERS + 1  # edge passes counted per step (x nnz)
 FAMILIES = ["spmv_bool", "spmv_count", "spmv_plus", "spmv_minplus", "spmv_min_i32", "spmm_or64"]
@@ -42,9 +44,12 @@ FAMILIES = ["spmv_bool", "spmv_count", "spmv_plus", "spmv_minplus", "spmv_min_i3
 def workload_desc(n, nnz):
     return {
         "workload": f"R-MAT scale {SCALE} ef{EDGE_FACTOR} a/b/c/d=0.57/0.19/0.19/0.05 seed {SEED}, symmetrised, "
-                    f"no self-loops/duplicates, unpermuted ids; B2SR tile 8x8; step = CSR->B2SR + Boolean SpMV + "
+                    f"no self-loops/duplicates, unpermuted ids; B2SR tile {TILE}x{TILE}; step = CSR->B2SR + Boolean SpMV + "
                     f"BFS from {NSRC} seeded sources (batched) + fp32 PageRank {PR_ITERS} iters + CC",
-        "n": int(n), "nnz": int(nnz), "tile_dim": TILE, "sources": NSRC, "pagerank_iters": PR_ITERS,
+        "n": int(n), "nnz": int(nnz), "tile_dim": TILE, "schedule": "direct" if SCHEDULE == 2 else "staged",
+        "tile_choice": "tile_dim sweep 4/8/16/32 by b2sr_autotune for the step's dominant scheme (plus-times, "
+                       "PageRank); its live choice is reported in extra.autotune_main",
+        "sources": NSRC, "pagerank_iters": PR_ITERS,
         "edges_per_step": int(QUERIES_PER_STEP * nnz),
         "cache": "inputs larger than L2 (tile stream 272 MiB vs 129 MB L2); no flush",
     }
@@ -164,7 +169,7 @@ def serving_extra(B, dev, pool=None):
     t_gen = time.perf_counter() - t_gen
     mats = []
     for n, rp, ci, _ in gs:
-        mats.append(B.b2sr_from_csr(n, torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), TILE))
+        mats.append(B.b2sr_from_csr(n, torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), SERVE_TILE))
     rng = np.random.default_rng(11)
     plan = []
     for _ in range(SERVE_QUERIES):
@@ -249,7 +254,7 @@ def serving_extra(B, dev, pool=None):
     res["speedup_bfs_saturated_vs_one_per_call"] = (res["saturated_bfs_only"]["queries_per_s"] /
                                                      res["one_query_per_call_bfs_only"]["queries_per_s"])
     res["config"] = (f"{SERVE_GRAPHS} R-MAT graphs, scales {lo}..{hi} (scale {lo} + i mod {hi - lo + 1}), ef{EDGE_FACTOR}, "
-                     f"seeds 1000+i, k={TILE}, {resident / 2**30:.2f} GiB resident; {SERVE_QUERIES} queries, 50% BFS "
+                     f"seeds 1000+i, k={SERVE_TILE}, {resident / 2**30:.2f} GiB resident; {SERVE_QUERIES} queries, 50% BFS "
                      f"(random non-isolated source) / 50% personalised PageRank ({SERVE_PR_ITERS} iters, d={DAMP}), "
                      f"Poisson arrivals at {SERVE_RATE:.0f}/s; budget {SERVE_BUDGET >> 30} GiB, 64 BFS lanes and 2 "
                      f"four-column PageRank blocks per graph; graph generation {t_gen:.1f} s on the host (untimed)")
@@ -300,7 +305,7 @@ def grid_tc_extra(B, dev, grid_res, tc_res):
     out = {}
     n, rp, ci, w = grid_res.get()
     rp_d, ci_d = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
-    with B.b2sr_from_csr(n, rp_d, ci_d, TILE) as m:
+    with B.b2sr_from_csr(n, rp_d, ci_d, SERVE_TILE) as m:
         wb = B.b2sr_weights_from_csr(m, rp_d, ci_d, torch.from_numpy(w).to(dev))
         dist = torch.empty(n, dtype=torch.float32, device=dev)
         # push rounds over the frontier (the grid is symmetric: the handle is its own transpose),
@@ -312,7 +317,7 @@ def grid_tc_extra(B, dev, grid_res, tc_res):
     del rp_d, ci_d
     n, rp, ci = tc_res.get()
     rp_d, ci_d = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
-    with B.b2sr_from_csr(n, rp_d, ci_d, TILE) as m:
+    with B.b2sr_from_csr(n, rp_d, ci_d, SERVE_TILE) as m:
         cnt = {}
         ms = _timed(lambda: cnt.__setitem__("t", B.b2sr_tc(m)), reps=3)
         out["tc_rmat18_ef32"] = {"ms": ms, "nnz": int(ci.size), "edges_per_s": ci.size / (ms / 1e3),
@@ -357,12 +362,12 @@ def batching_extra(B, dev, big_res, arena_res, arena_scales):
     del rp_d, ci_d
     gs = arena_res.get()
     csrs = [(gn, torch.from_numpy(grp).to(dev), torch.from_numpy(gci).to(dev)) for gn, grp, gci in gs]
-    arena, bases = B.b2sr_from_csr_batch(csrs, TILE)
+    arena, bases = B.b2sr_from_csr_batch(csrs, SERVE_TILE)
     srcs_a = [int(bases[i]) for i in range(len(gs))]  # vertex 0 of every graph (its hub)
     with arena:
         lva = torch.empty(arena.n, dtype=torch.int32, device=dev)
         t_arena = _timed(lambda: B.b2sr_bfs_sources(arena, srcs_a, lva))
-        mats = [B.b2sr_from_csr(gn, grp, gci, TILE) for gn, grp, gci in csrs]
+        mats = [B.b2sr_from_csr(gn, grp, gci, SERVE_TILE) for gn, grp, gci in csrs]
         outs = [torch.empty(gn, dtype=torch.int32, device=dev) for gn, _, _ in csrs]
 
         def per_graph():
@@ -439,17 +444,18 @@ class ClockSampler:
 # our arm
 # ---------------------------------------------------------------------------
 
-def traffic_for(family):
+def traffic_for(family, tile, kname):
     """dram bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+    the same kernel, tile_dim and kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2201_08560_gb300", "csrc", "spmv.cu")
     try:
         rec = json.load(open(path))
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        ent = rec.get(family)
-        if ent and ent.get("kernel_source_sha256") == sha:
-            return float(ent["dram_bytes_per_launch"]), ent
+        for ent in rec.values():
+            if (ent.get("family") == family and ent.get("tile_dim") == tile and ent.get("kernel", "").startswith(kname)
+                    and ent.get("kernel_source_sha256") == sha):
+                return float(ent["dram_bytes_per_launch"]), ent
     except Exception:
         pass
     return None, None
@@ -463,7 +469,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the serving, grid/TC and batching extras")
+    ap.add_argument("--tile", type=int, default=None, help="override the main workload's tile_dim")
+    ap.add_argument("--schedule", type=int, default=None, help="override its SpMV schedule (1 staged, 2 direct)")
     args = ap.parse_args()
+    global TILE, SCHEDULE
+    if args.tile:
+        TILE = args.tile
+    if args.schedule:
+        SCHEDULE = args.schedule
     if args.impl == "reference":
         return run_reference(args)
 
@@ -501,6 +514,7 @@ def main():
 
     def step(rp_, ci_, x_):
         m = B.b2sr_from_csr(g.n, rp_, ci_, TILE)
+        B.b2sr_set_schedule(m, SCHEDULE)
         B.b2sr_spmv(m, B.BOOL_OR_AND, B.VEC_BITS, x_, B.VEC_BITS, y)
         B.b2sr_bfs_multi(m, srcs_l, levels)
         B.b2sr_pagerank(m, DAMP, PR_ITERS, None, pr)
@@ -585,6 +599,7 @@ def main():
     # ---- extras: batched vs plain BFS, Boolean SpMV alone ----
     extra = {}
     with B.b2sr_from_csr(g.n, rp, ci, TILE) as m:
+        B.b2sr_set_schedule(m, SCHEDULE)
         for _ in range(2):
             B.b2sr_bfs_multi(m, srcs_l, levels)
             B.b2sr_bfs(m, srcs_l[0], levels[0])
@@ -612,6 +627,15 @@ def main():
                                  "gbs": byb / nb / (tb / nb / 1e3) / 1e9}
 
     if not args.no_extras:
+        try:
+            smp = np.random.default_rng(29).integers(0, g.n, 8192).astype(np.int32)
+            mt, rep = B.b2sr_autotune(g.n, rp, ci, smp, B.PLUS_TIMES, B.VEC_F32, keep_ratio=0.0, trials=5)
+            mt.close()
+            extra["autotune_main"] = {"scheme": "plus-times fp32 (PageRank)", "choice_tile_dim": rep["tile_dim"],
+                                      "choice_schedule": rep["schedule"], "trial_us": rep["trial_us"],
+                                      "est_ratio": rep["est_ratio"], "used": {"tile_dim": TILE, "schedule": SCHEDULE}}
+        except Exception as e:
+            extra["autotune_main"] = {"failed": repr(e)}
         import multiprocessing as mp
         with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
             rng = np.random.default_rng(23)
@@ -642,8 +666,10 @@ def main():
         dom = max(fam, key=lambda f: fam[f]["ms"])
         d = fam[dom]
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        traffic, _ = traffic_for(dom)
-        kname = "spmv_gather_kernel" if dom not in ("spmv_bool", "spmv_count") and TILE <= 16 else "spmv_chunks_kernel"
+        traffic = None
+        staged_kernel = dom not in ("spmv_bool", "spmv_count") and TILE <= 16 and SCHEDULE != 2
+        kname = "spmv_gather_kernel" if staged_kernel else "spmv_chunks_kernel"
+        traffic, _ = traffic_for(dom, TILE, kname)
         roofline = {"bound": "hbm", "kernel": f"{kname} ({dom}, k={TILE})", "achieved": achieved,
                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                     "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
