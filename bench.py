@@ -35,7 +35,8 @@ METRIC = "B2SR SpMV/BFS GTEPS & % HBM peak; TC edges/s; batched BFS queries/s vs
 SCALE, EDGE_FACTOR, SEED = 20, 16, 1
 TILE = 4                 # B2SR tile_dim of the main workload ...
 SCHEDULE = 2             # ... and its SpMV schedule (b2sr_schedule DIRECT); see workload_desc
-SERVE_TILE = 8           # tile_dim of the serving and batching extras
+SERVE_TILE = 4           # tile_dim of the served graphs (direct schedule, as the main workload)
+EXTRA_TILE = 8           # tile_dim of the grid SSSP, triangle-count and arena extras
 NSRC, PR_ITERS, DAMP = 16, 50, 0.85
 QUERIES_PER_STEP = 1 + NSRC + PR_ITERS + 1  # edge passes counted per step (x nnz)
 FAMILIES = ["spmv_bool", "spmv_count", "spmv_plus", "spmv_minplus", "spmv_min_i32", "spmm_or64"]
@@ -170,6 +171,7 @@ def serving_extra(B, dev, pool=None):
     mats = []
     for n, rp, ci, _ in gs:
         mats.append(B.b2sr_from_csr(n, torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), SERVE_TILE))
+        B.b2sr_set_schedule(mats[-1], SCHEDULE)
     rng = np.random.default_rng(11)
     plan = []
     for _ in range(SERVE_QUERIES):
@@ -254,7 +256,7 @@ def serving_extra(B, dev, pool=None):
     res["speedup_bfs_saturated_vs_one_per_call"] = (res["saturated_bfs_only"]["queries_per_s"] /
                                                      res["one_query_per_call_bfs_only"]["queries_per_s"])
     res["config"] = (f"{SERVE_GRAPHS} R-MAT graphs, scales {lo}..{hi} (scale {lo} + i mod {hi - lo + 1}), ef{EDGE_FACTOR}, "
-                     f"seeds 1000+i, k={SERVE_TILE}, {resident / 2**30:.2f} GiB resident; {SERVE_QUERIES} queries, 50% BFS "
+                     f"seeds 1000+i, k={SERVE_TILE} direct schedule, {resident / 2**30:.2f} GiB resident; {SERVE_QUERIES} queries, 50% BFS "
                      f"(random non-isolated source) / 50% personalised PageRank ({SERVE_PR_ITERS} iters, d={DAMP}), "
                      f"Poisson arrivals at {SERVE_RATE:.0f}/s; budget {SERVE_BUDGET >> 30} GiB, 64 BFS lanes and 2 "
                      f"four-column PageRank blocks per graph; graph generation {t_gen:.1f} s on the host (untimed)")
@@ -305,7 +307,7 @@ def grid_tc_extra(B, dev, grid_res, tc_res):
     out = {}
     n, rp, ci, w = grid_res.get()
     rp_d, ci_d = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
-    with B.b2sr_from_csr(n, rp_d, ci_d, SERVE_TILE) as m:
+    with B.b2sr_from_csr(n, rp_d, ci_d, EXTRA_TILE) as m:
         wb = B.b2sr_weights_from_csr(m, rp_d, ci_d, torch.from_numpy(w).to(dev))
         dist = torch.empty(n, dtype=torch.float32, device=dev)
         # push rounds over the frontier (the grid is symmetric: the handle is its own transpose),
@@ -317,7 +319,7 @@ def grid_tc_extra(B, dev, grid_res, tc_res):
     del rp_d, ci_d
     n, rp, ci = tc_res.get()
     rp_d, ci_d = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
-    with B.b2sr_from_csr(n, rp_d, ci_d, SERVE_TILE) as m:
+    with B.b2sr_from_csr(n, rp_d, ci_d, EXTRA_TILE) as m:
         cnt = {}
         ms = _timed(lambda: cnt.__setitem__("t", B.b2sr_tc(m)), reps=3)
         out["tc_rmat18_ef32"] = {"ms": ms, "nnz": int(ci.size), "edges_per_s": ci.size / (ms / 1e3),
@@ -362,12 +364,12 @@ def batching_extra(B, dev, big_res, arena_res, arena_scales):
     del rp_d, ci_d
     gs = arena_res.get()
     csrs = [(gn, torch.from_numpy(grp).to(dev), torch.from_numpy(gci).to(dev)) for gn, grp, gci in gs]
-    arena, bases = B.b2sr_from_csr_batch(csrs, SERVE_TILE)
+    arena, bases = B.b2sr_from_csr_batch(csrs, EXTRA_TILE)
     srcs_a = [int(bases[i]) for i in range(len(gs))]  # vertex 0 of every graph (its hub)
     with arena:
         lva = torch.empty(arena.n, dtype=torch.int32, device=dev)
         t_arena = _timed(lambda: B.b2sr_bfs_sources(arena, srcs_a, lva))
-        mats = [B.b2sr_from_csr(gn, grp, gci, SERVE_TILE) for gn, grp, gci in csrs]
+        mats = [B.b2sr_from_csr(gn, grp, gci, EXTRA_TILE) for gn, grp, gci in csrs]
         outs = [torch.empty(gn, dtype=torch.int32, device=dev) for gn, _, _ in csrs]
 
         def per_graph():
@@ -623,8 +625,8 @@ def main():
         tb, nb, byb = B.b2sr_timing_read("spmv_bool")
         B.b2sr_timing_enable(False)
         B.b2sr_timing_reset()
-        extra["spmv_bool_k8"] = {"kernel_us": tb / nb * 1e3, "gteps": g.nnz / (tb / nb / 1e3) / 1e9,
-                                 "gbs": byb / nb / (tb / nb / 1e3) / 1e9}
+        extra["spmv_bool"] = {"tile_dim": TILE, "kernel_us": tb / nb * 1e3, "gteps": g.nnz / (tb / nb / 1e3) / 1e9,
+                              "gbs": byb / nb / (tb / nb / 1e3) / 1e9}
 
     if not args.no_extras:
         try:

@@ -83,9 +83,12 @@ def test_more_than_64_queries_on_one_graph(B, resident):
             np.testing.assert_array_equal(to_np(lv)[: g.n], oracle.bfs(g, s))
 
 
+@pytest.mark.parametrize("sched", [1, 2], ids=["staged", "direct"])
 @pytest.mark.parametrize("src", [-1, 0, 7])
-def test_served_pagerank_bitwise_equals_driver(B, resident, src):
+def test_served_pagerank_bitwise_equals_driver(B, resident, src, sched):
     gs, ms = resident
+    for m in ms:
+        B.b2sr_set_schedule(m, sched)
     with B.Server(8 * GB) as srv:
         gids = [srv.add_graph(m) for m in ms]
         outs = []
@@ -102,6 +105,8 @@ def test_served_pagerank_bitwise_equals_driver(B, resident, src):
                                           solo_pagerank(B, m, g.n, s, 0.85, iters).view(np.uint32))
             np.testing.assert_allclose(got.astype(np.float64), oracle_pagerank(g, s, 0.85, iters),
                                        rtol=1e-5, atol=0)
+    for m in ms:
+        B.b2sr_set_schedule(m, 0)
 
 
 def test_results_same_alone_and_mixed(B, resident):
