@@ -2,7 +2,8 @@
 """Benchmark of the B2SR hot path on the R-MAT scale-20 workload.
 
 One step is one pass of the hot path over the workload: CSR -> B2SR
-conversion (tile_dim 8), one Boolean SpMV, BFS from 16 seeded sources (one
+conversion (tile_dim 4, direct SpMV schedule: the autotuner's choice for
+the step's dominant scheme on this graph), one Boolean SpMV, BFS from 16 seeded sources (one
 batched 64-lane launch sequence), PageRank (fp32, d = 0.85, 50 iterations)
 and connected components.  Throughput is GTEPS: the edges the step's queries
 must touch -- nnz for the SpMV, nnz per BFS source, nnz per PageRank
