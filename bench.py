@@ -141,6 +141,7 @@ SERVE_GRAPHS, SERVE_SCALES = 32, (14, 20)
 SERVE_QUERIES, SERVE_RATE, SERVE_PR_ITERS = 10000, 2000.0, 20
 SERVE_BUDGET = 64 << 30
 SERVE_BASELINE_QUERIES = 300
+SERVE_FIFO_QUERIES = 1000
 
 
 def _serve_graph(scale, seed):
@@ -222,9 +223,35 @@ def serving_extra(B, dev, pool=None):
         res["saturated"] = run(srv, gids, plan)
         bfs_only = [q for q in plan if q[0] == "bfs"]
         res["saturated_bfs_only"] = run(srv, gids, bfs_only)
+    # one query per driver call in arrival order (a FIFO) on the same Poisson stream's first queries
+    nf = SERVE_FIFO_QUERIES
+    tele = torch.zeros(max(n for n, _, _, _ in gs), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    lat = []
+    t0 = time.perf_counter()
+    for i, (kind, gi, src) in enumerate(plan[:nf]):
+        due = t0 + arrivals[i]
+        now = time.perf_counter()
+        if now < due:
+            time.sleep(due - now)
+        m = mats[gi]
+        if kind == "bfs":
+            B.b2sr_bfs(m, src, outs_i[i])
+        else:
+            t = tele[: m.n]
+            t[src] = 1.0
+            B.b2sr_pagerank(m, DAMP, SERVE_PR_ITERS, t, outs_f[i])
+            t[src] = 0.0
+        torch.cuda.synchronize()
+        lat.append(time.perf_counter() - due)
+    wall = time.perf_counter() - t0
+    lat_ms = np.sort(np.array(lat) * 1e3)
+    res["fifo_one_query_per_call"] = {"queries": nf, "queries_per_s": nf / wall,
+                                      "p50_ms": float(lat_ms[int(np.ceil(0.5 * nf)) - 1]),
+                                      "p99_ms": float(lat_ms[int(np.ceil(0.99 * nf)) - 1]),
+                                      "note": f"the first {nf} queries of the same Poisson stream, one driver call each"}
     # one query per driver call, same mix
     base = plan[:SERVE_BASELINE_QUERIES]
-    tele = torch.zeros(max(n for n, _, _, _ in gs), dtype=torch.float32, device=dev)
     for kind, gi, src in base[:20]:   # warm-up
         if kind == "bfs":
             B.b2sr_bfs(mats[gi], src, outs_i[0])
@@ -323,7 +350,9 @@ def grid_tc_extra(B, dev, grid_res, tc_res):
     with B.b2sr_from_csr(n, rp_d, ci_d, EXTRA_TILE) as m:
         cnt = {}
         ms = _timed(lambda: cnt.__setitem__("t", B.b2sr_tc(m)), reps=3)
-        out["tc_rmat18_ef32"] = {"ms": ms, "nnz": int(ci.size), "edges_per_s": ci.size / (ms / 1e3),
+        out["tc_rmat18_ef32"] = {"ms": ms, "nnz": int(ci.size), "l_edges": int(ci.size) // 2,
+                                 "edges_per_s": (ci.size // 2) / (ms / 1e3),
+                                 "edges_counted": "|L|, the strictly lower triangle's entries",
                                  "triangles": int(cnt["t"].item()), "n": int(n)}
     return out
 
@@ -615,6 +644,18 @@ def main():
             B.b2sr_bfs(m, s, levels[i])
         b.record(); b.synchronize()
         t_plain = a.elapsed_time(b)
+        # Graph500-style TEPS: undirected edges with both endpoints reached (a symmetric
+        # graph: every neighbour of a reached vertex is reached) over the search time
+        deg = (rp[1:] - rp[:-1]).to(torch.int64)
+        edges_src = [int((deg * (levels[i] >= 0)).sum().item()) // 2 for i in range(NSRC)]
+        teps = []
+        for i, s in enumerate(srcs_l):
+            a.record(); B.b2sr_bfs(m, s, levels[i]); b.record(); b.synchronize()
+            teps.append(edges_src[i] / (a.elapsed_time(b) / 1e3))
+        hmean = len(teps) / sum(1.0 / t for t in teps)
+        extra["bfs_graph500_teps"] = {"sources": NSRC, "single_source_harmonic_mean_gteps": hmean / 1e9,
+                                      "batched_gteps": sum(edges_src) / (t_batched / 1e3) / 1e9,
+                                      "edges_counted": "undirected edges with both endpoints reached, per source"}
         extra["bfs_16_sources"] = {"batched_ms": t_batched, "plain_ms": t_plain,
                                    "batched_queries_per_s": NSRC / (t_batched / 1e3),
                                    "plain_queries_per_s": NSRC / (t_plain / 1e3),

@@ -356,6 +356,19 @@ b2sr_status b2sr_bfs(b2sr_handle h, int32_t src, int32_t* levels, int max_iters,
 b2sr_status b2sr_bfs_sources(b2sr_handle h, const int32_t* srcs_host, int nsrc, int32_t* levels,
                              int max_iters, void* stream);
 
+/* Direction-optimising BFS (Sec. V BFS; the push/pull switching of Beamer et
+ * al., SC 2012).  A level either pulls (the Boolean SpMV of b2sr_bfs over
+ * every tile) or pushes (walks only the frontier's tile-rows of A^T and sets
+ * unvisited targets with atomic ORs); it starts pushing, pulls once the
+ * frontier's out-edges exceed the unexplored edges / 14, and pushes again
+ * once the frontier is below n / 24.  The choice is made on the device each
+ * level; levels equal b2sr_bfs's bit for bit.
+ *   hT  B2SR of A^T (tile-row J lists the out-edges of vertices kJ..kJ+k-1),
+ *       NULL for a symmetric matrix (h is its own transpose); same n as h
+ * Other arguments as b2sr_bfs; one host synchronisation per four levels. */
+b2sr_status b2sr_bfs_diropt(b2sr_handle h, b2sr_handle hT, int32_t src, int32_t* levels, int max_iters,
+                            void* stream);
+
 /* Multi-source BFS: up to 64 BFS runs of Sec. V advance together, their
  * frontiers packed as one uint64 per vertex (b2sr_spmm_bits64).
  *   srcs_host host int32[nsrc], 1 <= nsrc <= 64

@@ -84,6 +84,7 @@ def _load() -> ctypes.CDLL:
                                   ctypes.POINTER(TuneReport)]),
         "b2sr_bfs": (c_int, [p, i32, p, c_int, p]),
         "b2sr_bfs_multi": (c_int, [p, p, c_int, p, c_int, p]),
+        "b2sr_bfs_diropt": (c_int, [p, p, i32, p, c_int, p]),
         "b2sr_bfs_sources": (c_int, [p, p, c_int, p, c_int, p]),
         "b2sr_from_csr_batch": (c_int, [c_int, p, p, p, p, c_int, p, pp, p]),
         "b2sr_sssp": (c_int, [p, p, i32, p, c_int, p]),
@@ -340,6 +341,16 @@ def b2sr_bfs(m: Matrix, src: int, levels: Optional[torch.Tensor] = None, max_ite
     if levels is None:
         levels = torch.empty(max(m.n, 1), dtype=torch.int32, device=_dev())
     _check(lib.b2sr_bfs(m.handle, int(src), _ptr(levels), int(max_iters), _stream(stream)))
+    return levels[: m.n]
+
+
+def b2sr_bfs_diropt(m: Matrix, src: int, mT: Optional[Matrix] = None, levels: Optional[torch.Tensor] = None,
+                    max_iters: int = 0, stream=None) -> torch.Tensor:
+    """Direction-optimising BFS; mT is the transpose (None: m is symmetric)."""
+    if levels is None:
+        levels = torch.empty(max(m.n, 1), dtype=torch.int32, device=_dev())
+    _check(lib.b2sr_bfs_diropt(m.handle, None if mT is None else mT.handle, int(src), _ptr(levels), int(max_iters),
+                               _stream(stream)))
     return levels[: m.n]
 
 

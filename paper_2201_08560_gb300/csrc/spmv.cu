@@ -1115,16 +1115,28 @@ __global__ void spmv_edges_kernel(SEM sem, int32_t lead_end, int32_t trail_begin
     for (int64_t R = trail_begin + tid; R < ntr; R += stride) sem.store((int32_t)R, idv);
 }
 
+__global__ void clear_words_kernel(uint32_t* w, int64_t count, const int32_t* gate) {
+    if (gated_off(gate)) return;
+    for (int64_t i = threadIdx.x; i < count; i += blockDim.x) w[i] = 0u;
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 // Bitset outputs: bits past the last tile-row (>= nTileRow*k) are never
 // stored by a row, so the words holding them are cleared first.
 template <int K>
-static b2sr_status clear_bitset_tail(const b2sr_matrix* h, uint32_t* bits, cudaStream_t s) {
+static b2sr_status clear_bitset_tail(const b2sr_matrix* h, uint32_t* bits, cudaStream_t s, const int32_t* gate) {
     int64_t words = ceil_div(h->n, 32);
     int64_t first = ((int64_t)h->ntr * K) / 32;
-    if (first < words) B2SR_CUDA_TRY(cudaMemsetAsync(bits + first, 0, (words - first) * sizeof(uint32_t), s));
+    if (first >= words) return B2SR_OK;
+    if (!gate) {
+        B2SR_CUDA_TRY(cudaMemsetAsync(bits + first, 0, (words - first) * sizeof(uint32_t), s));
+        return B2SR_OK;
+    }
+    // gated: a closed gate must leave the output alone (the caller may have filled it another way)
+    clear_words_kernel<<<1, 32, 0, s>>>(bits + first, words - first, gate);
+    B2SR_LAUNCH_CHECK("clear_words_kernel");
     return B2SR_OK;
 }
 
@@ -1161,7 +1173,7 @@ static b2sr_status run_spmv(const b2sr_matrix* h, const SEM& sem, uint32_t* bits
                             const char* family, double vec_bytes, const int32_t* gate) {
     using V = typename SEM::V;
     SpmvGeom g{h->rowptr, h->colind, h->tiles, h->chunk_row, h->T, h->nchunks, h->ntr, gate};
-    if (bits_out) B2SR_TRY(clear_bitset_tail<K>(h, bits_out, s));
+    if (bits_out) B2SR_TRY(clear_bitset_tail<K>(h, bits_out, s, gate));
     B2SR_TRY((launch_edges<K, SEM>(h, sem, s, gate)));
     if (h->nchunks == 0) return B2SR_OK;
     DevBuf pbuf(s);
@@ -1354,7 +1366,7 @@ static b2sr_status run_spmv_bool_fixed(const b2sr_matrix* h, const SemBool<K>& s
                                               std::to_string(2 * half) + " scratch bytes, the fixed array holds " +
                                               std::to_string(kNoallocScratchBytes));
     SpmvGeom g{h->rowptr, h->colind, h->tiles, h->chunk_row, h->T, h->nchunks, h->ntr, nullptr};
-    B2SR_TRY(clear_bitset_tail<K>(h, y, s));
+    B2SR_TRY(clear_bitset_tail<K>(h, y, s, nullptr));
     B2SR_TRY((launch_edges<K, SEM>(h, sem, s, nullptr)));
     if (h->nchunks == 0) return B2SR_OK;
     // every partial the fixup reads is written by the chunk kernel of the

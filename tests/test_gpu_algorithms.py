@@ -262,3 +262,36 @@ def test_sssp_push_symmetric_uses_own_handle(B):
             np.testing.assert_array_equal(d, to_np(B.b2sr_sssp(m, 0, wb)))
             with pytest.raises(B.B2SRError):
                 B.b2sr_sssp_push(m, 0, wb, delta=delta, max_iters=5)
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("gi", range(len(GRAPH_IDS)), ids=GRAPH_IDS)
+def test_bfs_diropt(B, k, gi):
+    """Direction-optimising BFS equals the oracle's levels (and b2sr_bfs's),
+    with the transpose given explicitly and, for symmetric graphs, implied."""
+    g = oracle.canonicalize(small_graphs()[gi])
+    rp, ci = to_dev(g.rowptr), to_dev(g.colind)
+    gT, _ = transposed(g, np.zeros(g.colind.size, np.float32))
+    with B.b2sr_from_csr(g.n, rp, ci, k) as m, \
+            B.b2sr_from_csr(g.n, to_dev(gT.rowptr), to_dev(gT.colind), 4 if k != 4 else 8) as mT:
+        for src in sorted({0, g.n // 2, g.n - 1}):
+            ref = oracle.bfs(g, src)
+            np.testing.assert_array_equal(to_np(B.b2sr_bfs_diropt(m, src, mT)), ref)
+            symmetric = np.array_equal(gT.rowptr, g.rowptr) and np.array_equal(gT.colind, g.colind)
+            if symmetric:
+                np.testing.assert_array_equal(to_np(B.b2sr_bfs_diropt(m, src)), ref)
+
+
+def test_bfs_diropt_switches_direction(B):
+    """On R-MAT the search pushes, pulls through the dense middle levels and
+    pushes again; on a long path it pushes throughout.  Either way: the oracle's
+    levels, and the level cap still applies."""
+    for g in (graphs.rmat(14, 16, seed=3), graphs.path(3000), graphs.grid2d(90, 70)):
+        rp, ci = csr_dev(g)
+        with B.b2sr_from_csr(g.n, rp, ci, 8) as m:
+            np.testing.assert_array_equal(to_np(B.b2sr_bfs_diropt(m, 0)), oracle.bfs(g, 0))
+    g = graphs.path(100)
+    rp, ci = csr_dev(g)
+    with B.b2sr_from_csr(g.n, rp, ci, 8) as m:
+        with pytest.raises(B.B2SRError):
+            B.b2sr_bfs_diropt(m, 0, max_iters=10)
