@@ -48,8 +48,14 @@ enum : int {
     C_MF_NEXT,
     C_MU,          // out-edges of unvisited vertices
     C_FOUND,
+    C_NLONG,       // long tile-rows (>= kLongRow tiles) in the current long list
+    C_NLONG_NEXT,
     C_WORDS
 };
+
+// Tile-rows of A^T with at least this many tiles are pushed by every warp
+// together (a hub's out-edges), the others by one warp each.
+constexpr int32_t kLongRow = 2048;
 
 template <int K>
 __device__ __forceinline__ uint32_t tile_row_of(const uint32_t* w, int r) {
@@ -83,6 +89,7 @@ __global__ void dirop_decide_kernel(long long* ctl, int32_t n) {
     ctl[C_MF_NEXT] = 0;
     ctl[C_FOUND] = 0;
     ctl[C_NNEXT] = 0;
+    ctl[C_NLONG_NEXT] = 0;
 }
 
 // Push: a warp per frontier tile-row J of A^T; lanes over its tiles; every
@@ -91,21 +98,22 @@ template <int K>
 __global__ void __launch_bounds__(256) dirop_push_kernel(const int32_t* __restrict__ rowptr,
                                                          const int32_t* __restrict__ colind,
                                                          const uint8_t* __restrict__ tiles,
-                                                         const int32_t* __restrict__ list, const uint32_t* frontier,
+                                                         const int32_t* __restrict__ list,
+                                                         const int32_t* __restrict__ longs, const uint32_t* frontier,
                                                          const uint32_t* visited, uint32_t* next, const long long* ctl) {
     constexpr int TB = K * (K <= 8 ? 1 : (K == 16 ? 2 : 4));
     constexpr int TW = (TB + 3) / 4;
     if (!ctl[C_PUSH]) return;
-    const int64_t ncur = ctl[C_NCUR];
+    const int64_t ncur = ctl[C_NCUR], nlong = ctl[C_NLONG];
     const int lane = (int)lane_id();
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < ncur; e += warps) {
-        const int32_t J = list[e];
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // every warp takes a slice of each long tile-row, the short ones a warp each
+    auto push_tiles = [&](int32_t J, int64_t t_begin, int64_t t_end, int64_t stride) {
         const uint32_t amask = segment<K>(frontier, J);
-        const int32_t t0 = rowptr[J], t1 = rowptr[J + 1];
-        for (int32_t t = t0 + lane; t < t1; t += 32) {
+        for (int64_t t = t_begin + lane; t < t_end; t += stride) {
             uint32_t wd[TW];
-            const uint32_t* tp = reinterpret_cast<const uint32_t*>(tiles + (int64_t)t * TB);
+            const uint32_t* tp = reinterpret_cast<const uint32_t*>(tiles + t * TB);
 #pragma unroll
             for (int q = 0; q < TW; ++q) wd[q] = __ldg(tp + q);
             uint32_t cols = 0u;  // union of the frontier rows' bits: targets I*K + c
@@ -115,13 +123,20 @@ __global__ void __launch_bounds__(256) dirop_push_kernel(const int32_t* __restri
             if (!cols) continue;
             const int32_t I = __ldg(colind + t);
             const int64_t base = (int64_t)I * K;
-            const uint32_t vis = segment<K>(visited, I);
-            cols &= ~vis;
+            cols &= ~segment<K>(visited, I);
             if (!cols) continue;
             // the K bits of segment I sit in one 32-bit word of the bitset
-            const int sh = (int)(base & 31);
-            atomicOr(next + (base >> 5), cols << sh);
+            atomicOr(next + (base >> 5), cols << (int)(base & 31));
         }
+    };
+    for (int64_t e = 0; e < nlong; ++e) {
+        const int32_t J = longs[e];
+        push_tiles(J, rowptr[J] + gw * 32, rowptr[J + 1], warps * 32);
+    }
+    for (int64_t e = gw; e < ncur; e += warps) {
+        const int32_t J = list[e];
+        const int32_t t0 = rowptr[J], t1 = rowptr[J + 1];
+        if (t1 - t0 < kLongRow) push_tiles(J, t0, t1, 32);
     }
 }
 
@@ -130,7 +145,7 @@ __global__ void __launch_bounds__(256) dirop_push_kernel(const int32_t* __restri
 template <int K>
 __global__ void dirop_update_kernel(const uint32_t* __restrict__ next, uint32_t* visited, int32_t* levels,
                                     int64_t words, int32_t n, const int32_t* __restrict__ deg, int32_t* nlist,
-                                    long long* ctl) {
+                                    const int32_t* __restrict__ rowptrT, int32_t* nlong, long long* ctl) {
     if (!ctl[C_ACTIVE]) return;
     const int32_t lv = (int32_t)ctl[C_LEVEL] + 1;
     long long nf = 0, mf = 0;
@@ -154,8 +169,12 @@ __global__ void dirop_update_kernel(const uint32_t* __restrict__ next, uint32_t*
         for (int sgm = 0; sgm < 32 / (K < 32 ? K : 32); ++sgm) {
             constexpr uint32_t kSegMask = K == 32 ? 0xFFFFFFFFu : ((1u << (K & 31)) - 1u);
             const uint32_t part = (b >> ((sgm * K) & 31)) & kSegMask;
-            if (part) nlist[atomicAdd(reinterpret_cast<unsigned long long*>(ctl + C_NNEXT), 1ull)] =
-                (int32_t)((w * 32) / K + sgm);
+            if (part) {
+                const int32_t J = (int32_t)((w * 32) / K + sgm);
+                nlist[atomicAdd(reinterpret_cast<unsigned long long*>(ctl + C_NNEXT), 1ull)] = J;
+                if (rowptrT[J + 1] - rowptrT[J] >= kLongRow)
+                    nlong[atomicAdd(reinterpret_cast<unsigned long long*>(ctl + C_NLONG_NEXT), 1ull)] = J;
+            }
         }
     }
     // block-level sums, then one atomic per block
@@ -179,12 +198,13 @@ __global__ void dirop_advance_kernel(long long* ctl) {
     ctl[C_NF] = ctl[C_NF_NEXT];
     ctl[C_MF] = ctl[C_MF_NEXT];
     ctl[C_NCUR] = ctl[C_NNEXT];
+    ctl[C_NLONG] = ctl[C_NLONG_NEXT];
 }
 
 // levels = -1, src = 0; frontier = visited = {src}; list = {src / kT}
 __global__ void dirop_init_kernel(int32_t* levels, int32_t n, int64_t words, uint32_t* fa, uint32_t* fb,
-                                  uint32_t* vis, int32_t src, int32_t kT, int32_t* list, long long* ctl,
-                                  const int32_t* deg, long long nnz) {
+                                  uint32_t* vis, int32_t src, int32_t kT, int32_t* list, int32_t* longs,
+                                  const int32_t* rowptrT, long long* ctl, const int32_t* deg, long long nnz) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n || i < words;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (i < n) levels[i] = i == src ? 0 : -1;
@@ -202,6 +222,11 @@ __global__ void dirop_init_kernel(int32_t* levels, int32_t n, int64_t words, uin
             ctl[C_NF] = 1;
             ctl[C_MF] = deg[src];
             ctl[C_MU] = nnz - deg[src];
+            const int32_t J = src / kT;
+            if (rowptrT[J + 1] - rowptrT[J] >= kLongRow) {
+                longs[0] = J;
+                ctl[C_NLONG] = 1;
+            }
         }
     }
 }
@@ -226,16 +251,19 @@ b2sr_status bfs_dirop(b2sr_matrix* h, b2sr_matrix* hT, int32_t src, int32_t* lev
     const size_t bw = round_up((size_t)words * 4 + 4, 256);
     const size_t lw = round_up((size_t)hT->ntr * 4 + 4, 256);
     DevBuf buf(s);
-    B2SR_TRY(buf.alloc(3 * bw + 2 * lw + 256));
+    B2SR_TRY(buf.alloc(3 * bw + 4 * lw + 256));
     char* base = buf.as<char>();
     uint32_t* fa = reinterpret_cast<uint32_t*>(base);
     uint32_t* fb = reinterpret_cast<uint32_t*>(base + bw);
     uint32_t* vis = reinterpret_cast<uint32_t*>(base + 2 * bw);
     int32_t* la = reinterpret_cast<int32_t*>(base + 3 * bw);
     int32_t* lb = reinterpret_cast<int32_t*>(base + 3 * bw + lw);
-    long long* ctl = reinterpret_cast<long long*>(base + 3 * bw + 2 * lw);
+    int32_t* ga = reinterpret_cast<int32_t*>(base + 3 * bw + 2 * lw);  // long tile-rows
+    int32_t* gb = reinterpret_cast<int32_t*>(base + 3 * bw + 3 * lw);
+    long long* ctl = reinterpret_cast<long long*>(base + 3 * bw + 4 * lw);
     dirop_init_kernel<<<grid_for(std::max<int64_t>(n, words)), 256, 0, s>>>(levels, n, words, fa, fb, vis, src,
-                                                                             hT->k, la, ctl, h->outdeg, h->nnz);
+                                                                             hT->k, la, ga, hT->rowptr, ctl,
+                                                                             h->outdeg, h->nnz);
     B2SR_LAUNCH_CHECK("dirop_init_kernel");
     // the loop's exit flag and the pull gate: the low words of C_ACTIVE and C_PULL (little-endian)
     const int32_t* active32 = reinterpret_cast<const int32_t*>(ctl + C_ACTIVE);
@@ -251,16 +279,19 @@ b2sr_status bfs_dirop(b2sr_matrix* h, b2sr_matrix* hT, int32_t src, int32_t* lev
                                     uint32_t* nx = (r & 1) ? fa : fb;
                                     int32_t* cur = (r & 1) ? lb : la;
                                     int32_t* nxt = (r & 1) ? la : lb;
+                                    int32_t* curl = (r & 1) ? gb : ga;
+                                    int32_t* nxtl = (r & 1) ? ga : gb;
                                     dirop_decide_kernel<<<1, 32, 0, cs>>>(ctl, n);
                                     B2SR_LAUNCH_CHECK("dirop_decide_kernel");
                                     B2SR_CUDA_TRY(cudaMemsetAsync(nx, 0, words * 4, cs));
                                     dirop_push_kernel<KT><<<push_grid, 256, 0, cs>>>(hT->rowptr, hT->colind, hT->tiles,
-                                                                                    cur, f, vis, nx, ctl);
+                                                                                    cur, curl, f, vis, nx, ctl);
                                     B2SR_LAUNCH_CHECK("dirop_push_kernel");
                                     B2SR_TRY(spmv_dispatch(h, B2SR_BOOL_OR_AND, B2SR_VEC_BITS, f, B2SR_VEC_BITS, nx,
                                                            vis, 1, nullptr, cs, pull_gate));
                                     dirop_update_kernel<KT><<<grid_for(words), 256, 0, cs>>>(nx, vis, levels, words, n,
-                                                                                            h->outdeg, nxt, ctl);
+                                                                                            h->outdeg, nxt,
+                                                                                            hT->rowptr, nxtl, ctl);
                                     B2SR_LAUNCH_CHECK("dirop_update_kernel");
                                     dirop_advance_kernel<<<1, 32, 0, cs>>>(ctl);
                                     B2SR_LAUNCH_CHECK("dirop_advance_kernel");
