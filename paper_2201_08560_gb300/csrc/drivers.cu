@@ -129,7 +129,9 @@ __global__ void msbfs_init_kernel(int32_t* levels, int32_t n, int nsrc, unsigned
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)n * nsrc || i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (i < (int64_t)n * nsrc) levels[i] = -1;
-        if (i < n) { X[i] = 0ull; vis[i] = 0ull; }
+        // unused lanes count as visited, so a vertex every source has reached is
+        // all ones in the mask and the SpMM can skip its rows
+        if (i < n) { X[i] = 0ull; vis[i] = nsrc < 64 ? ~((1ull << nsrc) - 1ull) : 0ull; }
     }
 }
 

@@ -214,6 +214,20 @@ struct SemBool {
     __device__ V comb(V a, V b) const { return a | b; }
     __device__ J jcomb(J a, J b) const { return a | b; }
     __device__ uint32_t xseg(int32_t Jc) const { return ld_bits(x, (int64_t)Jc * K, K); }
+    // Every output row in [r0, r1) is masked out (a complemented mask with all
+    // those bits set): the result there is false whatever the tiles hold.
+    // Rows past n store nothing.  Warp-collective.
+    __device__ bool saturated(int64_t r0, int64_t r1) const {
+        if (!mask || !comp) return false;
+        r1 = min(r1, (int64_t)n);
+        bool ok = true;
+        for (int64_t w = (r0 >> 5) + lane_id(); w * 32 < r1; w += 32) {
+            const int64_t lo = max(r0, w * 32), hi = min(r1, w * 32 + 32);
+            const uint32_t need = (hi - lo >= 32) ? 0xFFFFFFFFu : (((1u << (hi - lo)) - 1u) << (lo - w * 32));
+            ok &= (__ldg(mask + w) & need) == need;
+        }
+        return __all_sync(0xffffffffu, ok);
+    }
     template <class A>
     __device__ void tile(A& acc, const uint32_t* w, uint32_t xs) const {
         if constexpr (K <= 8) {
@@ -270,6 +284,7 @@ struct SemCount {
     __device__ V comb(V a, V b) const { return a + b; }
     __device__ J jcomb(J a, J b) const { return a + b; }
     __device__ uint32_t xseg(int32_t Jc) const { return ld_bits(x, (int64_t)Jc * K, K); }
+    __device__ bool saturated(int64_t, int64_t) const { return false; }
     template <class A>
     __device__ void tile(A& acc, const uint32_t* w, uint32_t xs) const {
 #pragma unroll
@@ -309,6 +324,7 @@ struct SemPlus {
     __device__ J jcomb(J a, J b) const { return csum_add(a, b); }
     __device__ V apply(V acc, G xv, float) const { return acc + xv; }
     __device__ V contrib(G xv, float) const { return xv; }
+    __device__ bool saturated(int64_t, int64_t) const { return false; }
     __device__ void store_row(int32_t R, int r, V v) const {
         int64_t i = (int64_t)R * K + r;
         if (i < n) y[i] = mask_allows(mask, comp, i) ? v : 0.0f;
@@ -351,6 +367,7 @@ struct SemPlus4 {
     }
     __device__ V apply(V acc, G xv, float) const { return comb(acc, xv); }
     __device__ V contrib(G xv, float) const { return xv; }
+    __device__ bool saturated(int64_t, int64_t) const { return false; }
     __device__ void store_row(int32_t R, int r, V v) const {
         int64_t i = (int64_t)R * K + r;
         if (i < n) y[i] = mask_allows(mask, comp, i) ? v : ident();
@@ -388,6 +405,7 @@ struct SemMinPlus {
     __device__ J jcomb(J a, J b) const { return fminf(a, b); }
     __device__ V apply(V acc, G xv, float wv) const { return fminf(acc, xv + wv); }
     __device__ V contrib(G xv, float wv) const { return xv + wv; }
+    __device__ bool saturated(int64_t, int64_t) const { return false; }
     __device__ void store_row(int32_t R, int r, V v) const {
         int64_t i = (int64_t)R * K + r;
         if (i < n) y[i] = mask_allows(mask, comp, i) ? fminf(__ldg(x + i), v) : INFINITY;
@@ -422,6 +440,7 @@ struct SemMinI32 {
     __device__ J jcomb(J a, J b) const { return min(a, b); }
     __device__ V apply(V acc, G xv, float) const { return min(acc, xv); }
     __device__ V contrib(G xv, float) const { return xv; }
+    __device__ bool saturated(int64_t, int64_t) const { return false; }
     __device__ void store_row(int32_t R, int r, V v) const {
         int64_t i = (int64_t)R * K + r;
         if (i < n) y[i] = mask_allows(mask, comp, i) ? min(__ldg(x + i), v) : INT_MAX;
@@ -456,6 +475,15 @@ struct SemOr64 {
     __device__ J jcomb(J a, J b) const { return a | b; }
     __device__ V apply(V acc, G xv, float) const { return acc | xv; }
     __device__ V contrib(G xv, float) const { return xv; }
+    // Every output row in [r0, r1) is fully masked out (complemented mask of
+    // all ones): zero whatever the tiles hold.  Warp-collective.
+    __device__ bool saturated(int64_t r0, int64_t r1) const {
+        if (!mask || !comp) return false;
+        r1 = min(r1, (int64_t)n);
+        bool ok = true;
+        for (int64_t i = r0 + lane_id(); i < r1; i += 32) ok &= __ldg(mask + i) == ~0ull;
+        return __all_sync(0xffffffffu, ok);
+    }
     __device__ void store_row(int32_t R, int r, V v) const {
         int64_t i = (int64_t)R * K + r;
         if (i < n) {
@@ -723,7 +751,21 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
 
     uint4 tv[S::TILE_V4];
     int32_t col[P];
-    load_lane_tiles<K>(g, ls.tl, tv, col);
+    // a chunk whose every output row is masked out reads no tiles (zero words:
+    // the walk still stores its rows and partials, all the identity)
+    bool sat = false;
+    {
+        const int32_t ra = __ldg(g.chunk_row + c), rb = __ldg(g.chunk_row + c + 1);
+        if (rb - ra <= 8) sat = sem.saturated((int64_t)ra * K, ((int64_t)rb + 1) * K);
+    }
+    if (!sat) {
+        load_lane_tiles<K>(g, ls.tl, tv, col);
+    } else {
+#pragma unroll
+        for (int q = 0; q < S::TILE_V4; ++q) tv[q] = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int i = 0; i < P; ++i) col[i] = 0;
+    }
     const uint32_t* words = reinterpret_cast<const uint32_t*>(tv);
     uint32_t xs[SEM::kGather ? 1 : P];
     if constexpr (!SEM::kGather) {
@@ -826,7 +868,21 @@ __global__ void __launch_bounds__(kSpmvThreads, (gather_min_blocks<K, SEM>())) s
 
     uint4 tv[S::TILE_V4];
     int32_t col[P];
-    load_lane_tiles<K>(g, ls.tl, tv, col);
+    // a chunk whose every output row is masked out reads no tiles (zero words:
+    // the walk still stores its rows and partials, all the identity)
+    bool sat = false;
+    {
+        const int32_t ra = __ldg(g.chunk_row + c), rb = __ldg(g.chunk_row + c + 1);
+        if (rb - ra <= 8) sat = sem.saturated((int64_t)ra * K, ((int64_t)rb + 1) * K);
+    }
+    if (!sat) {
+        load_lane_tiles<K>(g, ls.tl, tv, col);
+    } else {
+#pragma unroll
+        for (int q = 0; q < S::TILE_V4; ++q) tv[q] = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int i = 0; i < P; ++i) col[i] = 0;
+    }
     const uint32_t* words = reinterpret_cast<const uint32_t*>(tv);
 
     // set bits of the lane's tiles and their slots in the warp's staging area
