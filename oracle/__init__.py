@@ -56,6 +56,9 @@ def _load():
                 "orc_spmv_minplus": (None, [i32, p, p, p, p, p, p, ctypes.c_int]),
                 "orc_spmv_min_i32": (None, [i32, p, p, p, p, p, ctypes.c_int]),
                 "orc_spmm_or64": (None, [i32, p, p, p, p, p, ctypes.c_int]),
+                "orc_spmv_max": (None, [i32, p, p, p, p, p, ctypes.c_int]),
+                "orc_mis_greedy": (ctypes.c_int, [i32, p, p, p, p]),
+                "orc_color_levels": (ctypes.c_int, [i32, p, p, p, p]),
                 "orc_masked_count": (i64, [i32, p, p, p, p, p, p]),
                 "orc_triangle_count": (i64, [i32, p, p]),
                 "orc_spgemm_bool": (i64, [i32, p, p, p, p, p, p]),
@@ -209,6 +212,37 @@ def spmv_min_i32(g, x, mask=None, complement=False):
     _load().orc_spmv_min_i32(G.n, _ptr(G.rowptr), _ptr(G.colind), _ptr(xi), _ptr(y), _ptr(m),
                              _mask_mode(mask, complement))
     return y
+
+
+def spmv_max(g, x, mask=None, complement=False):
+    """Max-times (Table 4): y_i = max over row i of x_j, -inf if empty or masked out."""
+    G = _G(g)
+    xd = _c(x, np.float64)
+    y = np.zeros(G.n, dtype=np.float64)
+    m = None if mask is None else _c(mask, np.uint32)
+    _load().orc_spmv_max(G.n, _ptr(G.rowptr), _ptr(G.colind), _ptr(xd), _ptr(y), _ptr(m),
+                         _mask_mode(mask, complement))
+    return y
+
+
+def mis_greedy(g, prio):
+    """Maximal independent set, greedy in decreasing priority (ties: larger id)."""
+    G = _G(g)
+    pr = _c(prio, np.float64)
+    out = np.zeros(G.n, dtype=np.int32)
+    if _load().orc_mis_greedy(G.n, _ptr(G.rowptr), _ptr(G.colind), _ptr(pr), _ptr(out)) != 0:
+        raise MemoryError("oracle")
+    return out
+
+
+def color_levels(g, prio):
+    """Colour = 1 + the largest colour among higher-priority neighbours (0 if none)."""
+    G = _G(g)
+    pr = _c(prio, np.float64)
+    out = np.zeros(G.n, dtype=np.int32)
+    if _load().orc_color_levels(G.n, _ptr(G.rowptr), _ptr(G.colind), _ptr(pr), _ptr(out)) != 0:
+        raise MemoryError("oracle")
+    return out
 
 
 def spmm_or64(g, X, M=None, complement=False):

@@ -276,6 +276,19 @@ void orc_spmv_min_i32(int32_t n, const int32_t* rowptr, const int32_t* colind, c
     }
 }
 
+/* Max-times over fp64 values (Table 4's tropical max-times; with a binary A
+ * every product is x_j):  y_i = max_{j in row i} x_j, -inf for an empty row
+ * or a masked-out output. */
+void orc_spmv_max(int32_t n, const int32_t* rowptr, const int32_t* colind, const double* x, double* y,
+                  const uint32_t* mask, int mask_mode) {
+    for (int64_t i = 0; i < n; ++i) {
+        double m = -INFINITY;
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+            if (x[colind[e]] > m) m = x[colind[e]];
+        y[i] = mask_allows(mask, mask_mode, i) ? m : -INFINITY;
+    }
+}
+
 /* Boolean SpMM with 64 frontiers packed per vertex (multi-source BFS step):
  * Y_i = OR_{j in row i} X_j, then AND with M_i (mode 1) or ~M_i (mode 2). */
 void orc_spmm_or64(int32_t n, const int32_t* rowptr, const int32_t* colind, const uint64_t* X,
@@ -585,5 +598,72 @@ int orc_sample_profile(int32_t n, const int32_t* rowptr, const int32_t* colind,
         tiles_est[q] = t_hat;
     }
     free(buf);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Maximal independent set and colouring by priority (Table 4: MIS, GC)      */
+/* ------------------------------------------------------------------------ */
+
+/* Vertices in decreasing priority (ties: larger id first), the order both
+ * functions below follow.  qsort with the priorities in a file-scope pointer
+ * (the oracle runs on one thread). */
+static const double* g_prio;
+
+static int cmp_prio_desc(const void* pa, const void* pb) {
+    int64_t a = *(const int64_t*)pa, b = *(const int64_t*)pb;
+    if (g_prio[a] != g_prio[b]) return g_prio[a] > g_prio[b] ? -1 : 1;
+    return a > b ? -1 : (a < b ? 1 : 0);
+}
+
+static int64_t* by_priority_desc(int32_t n, const double* prio) {
+    int64_t* order = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!order) return NULL;
+    for (int64_t i = 0; i < n; ++i) order[i] = i;
+    g_prio = prio;
+    qsort(order, (size_t)n, sizeof(int64_t), cmp_prio_desc);
+    return order;
+}
+
+/* Greedy maximal independent set in decreasing priority: a vertex joins
+ * unless a neighbour already joined.  (With distinct priorities this is the
+ * set the synchronous local-maximum rounds of Luby's algorithm reach.)
+ * in_set[v] = 1 or 0.  The matrix is read as undirected (symmetric). */
+int orc_mis_greedy(int32_t n, const int32_t* rowptr, const int32_t* colind, const double* prio,
+                   int32_t* in_set) {
+    int64_t* order = by_priority_desc(n, prio);
+    if (!order) return ORC_ENOMEM;
+    for (int64_t i = 0; i < n; ++i) in_set[i] = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t v = order[k];
+        int blocked = 0;
+        for (int64_t e = rowptr[v]; e < rowptr[v + 1] && !blocked; ++e)
+            if (colind[e] != v && in_set[colind[e]]) blocked = 1;
+        in_set[v] = !blocked;
+    }
+    free(order);
+    return ORC_OK;
+}
+
+/* Colouring by priority levels: colour(v) = 0 if no neighbour has a higher
+ * priority, else 1 + the largest colour among higher-priority neighbours
+ * (the round in which v becomes a local maximum among uncoloured vertices).
+ * Neighbours never share a colour. */
+int orc_color_levels(int32_t n, const int32_t* rowptr, const int32_t* colind, const double* prio,
+                     int32_t* color) {
+    int64_t* order = by_priority_desc(n, prio);
+    if (!order) return ORC_ENOMEM;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t v = order[k];
+        int32_t c = 0;
+        for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+            int64_t u = colind[e];
+            if (u == v) continue;
+            if (prio[u] > prio[v] || (prio[u] == prio[v] && u > v))
+                if (color[u] + 1 > c) c = color[u] + 1;
+        }
+        color[v] = c;
+    }
+    free(order);
     return ORC_OK;
 }
