@@ -73,7 +73,8 @@ typedef struct b2sr_matrix* b2sr_handle;
 typedef enum {
     B2SR_BOOL_OR_AND = 0, /* Boolean semiring ({0,1}, OR, AND), Table 4 */
     B2SR_PLUS_TIMES = 1,  /* arithmetic semiring (R, +, x), Table 4 */
-    B2SR_MIN_PLUS = 2     /* tropical min-plus (R u {+inf}, min, +), Table 4 */
+    B2SR_MIN_PLUS = 2,    /* tropical min-plus (R u {+inf}, min, +), Table 4 */
+    B2SR_MAX_TIMES = 3    /* tropical max-times (R u {-inf}, max, x), Table 4 */
 } b2sr_semiring;
 
 typedef enum {
@@ -213,12 +214,17 @@ b2sr_status b2sr_weights_from_csr(b2sr_handle h, const int32_t* rowptr, const in
  *   MIN_PLUS,    I32  -> I32   y_i = min(x_i, min_{j: A_ij=1} x_j): every
  *                              weight 0, the CC min step (Sec. V, CC);
  *                              weights must be NULL
+ *   MAX_TIMES,   F32  -> F32   y_i = max_{j: A_ij=1} x_j (A_ij = 1 is the
+ *                              multiplicative identity), -inf for a row with
+ *                              no entries: the local-maximum step of MIS and
+ *                              colouring (Table 4, bin-full-full); no
+ *                              diagonal term; weights must be NULL
  *   x       device; bitset (ceil(n/32) words), int32[n] or float[n]
  *   y       device; same shapes; must not alias x or mask
  *   mask    device bitset or NULL; if given, y_i is kept where the mask bit
  *           is 1 (mask_complement = 0) or 0 (mask_complement = 1); excluded
  *           outputs get the semiring's additive identity (0 / false / +inf /
- *           INT32_MAX)
+ *           INT32_MAX / -inf)
  *   weights device float[nnz] in set-bit order (b2sr_weights_from_csr) or NULL
  * Floating-point sums use a fixed order, so results are bitwise reproducible
  * run to run.  B2SR_ERR_INVALID_ARG for other combinations. */
@@ -418,6 +424,35 @@ b2sr_status b2sr_pagerank(b2sr_handle h, float d, int iters, const float* telepo
  * min step of b2sr_spmv).  labels device int32[n]: the smallest vertex id in
  * each vertex's component.  Undirected (symmetric) matrices. */
 b2sr_status b2sr_cc(b2sr_handle h, int32_t* labels, int max_iters, void* stream);
+
+/* Maximal independent set (the MIS row of Table 4: the local-maximum test on
+ * the max-times semiring, the removal of neighbours on the Boolean semiring;
+ * the paper names the operation without an algorithm, and this is Luby's
+ * synchronous rounds with fixed priorities).  Each vertex carries the key
+ * (priority, id), compared by priority and then by the larger id.  A round
+ * takes every undecided vertex whose key is the largest among itself and its
+ * undecided neighbours into the set and decides it and its neighbours.  The
+ * result is the greedy set in decreasing key order: v is in it iff no
+ * neighbour with a larger key is.
+ *   priority device float[n], not NaN (+0 and -0 are equal)
+ *   in_set   device int32[n]: 1 for members, 0 otherwise
+ * Symmetric matrices (undirected graphs); self-loops are ignored.  Rounds run
+ * as a CUDA graph of 4 gated rounds.  B2SR_ERR_INVALID_ARG for a NaN
+ * priority; B2SR_ERR_NOT_CONVERGED if vertices are still undecided after
+ * max_iters rounds (<= 0: n), checked every 4 rounds. */
+b2sr_status b2sr_mis(b2sr_handle h, const float* priority, int32_t* in_set, int max_iters, void* stream);
+
+/* Graph colouring by rounds of local maxima (the GC row of Table 4, on the
+ * max-times semiring; no algorithm in the paper).  With the keys of b2sr_mis,
+ * round r gives colour r to every uncoloured vertex whose key is the largest
+ * among itself and its uncoloured neighbours: colour(v) = 0 if no neighbour
+ * has a larger key, else 1 + the largest colour among the neighbours that
+ * do.  Each colour class is an independent set.
+ *   priority device float[n], not NaN
+ *   colors   device int32[n]
+ * Symmetric matrices; self-loops are ignored.  Rounds run as a CUDA graph of
+ * 8 gated rounds.  Errors as b2sr_mis. */
+b2sr_status b2sr_color(b2sr_handle h, const float* priority, int32_t* colors, int max_iters, void* stream);
 
 /* Triangle count (Sec. V TC): sum(L .* (L L^T)) for L = b2sr_lower(h), by
  * b2sr_spgemm_masked_count.  Symmetric matrices.  count device int64[1]. */

@@ -17,7 +17,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libb2sr.so")
 
-BOOL_OR_AND, PLUS_TIMES, MIN_PLUS = 0, 1, 2
+BOOL_OR_AND, PLUS_TIMES, MIN_PLUS, MAX_TIMES = 0, 1, 2, 3
 VEC_BITS, VEC_I32, VEC_F32, VEC_BITS64 = 0, 1, 2, 3
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_TILE", 3: "OOM", 4: "CUDA", 5: "NOT_CONVERGED",
           6: "ADMISSION_REFUSED", 7: "ABORTED"}
@@ -91,6 +91,8 @@ def _load() -> ctypes.CDLL:
         "b2sr_sssp_push": (c_int, [p, p, i32, p, f32, c_int, p]),
         "b2sr_pagerank": (c_int, [p, f32, c_int, p, p, p]),
         "b2sr_cc": (c_int, [p, p, c_int, p]),
+        "b2sr_mis": (c_int, [p, p, p, c_int, p]),
+        "b2sr_color": (c_int, [p, p, p, c_int, p]),
         "b2sr_tc": (c_int, [p, p, p]),
         "b2sr_server_create": (c_int, [i64, c_int, c_int, pp]),
         "b2sr_server_add_graph": (c_int, [p, p, ctypes.POINTER(i32)]),
@@ -395,6 +397,34 @@ def b2sr_cc(m: Matrix, labels: Optional[torch.Tensor] = None, max_iters: int = 0
         labels = torch.empty(max(m.n, 1), dtype=torch.int32, device=_dev())
     _check(lib.b2sr_cc(m.handle, _ptr(labels), int(max_iters), _stream(stream)))
     return labels[: m.n]
+
+
+def _priority(m: Matrix, priority: torch.Tensor) -> torch.Tensor:
+    if priority.dtype != torch.float32 or not priority.is_cuda or priority.numel() < m.n:
+        raise ValueError("priority must be a float32 CUDA tensor of n entries")
+    return priority.contiguous()
+
+
+def b2sr_mis(m: Matrix, priority: torch.Tensor, in_set: Optional[torch.Tensor] = None, max_iters: int = 0,
+             stream=None) -> torch.Tensor:
+    """Maximal independent set: 1 for members (the greedy set in decreasing
+    (priority, id) order)."""
+    pr = _priority(m, priority)
+    if in_set is None:
+        in_set = torch.empty(max(m.n, 1), dtype=torch.int32, device=_dev())
+    _check(lib.b2sr_mis(m.handle, _ptr(pr), _ptr(in_set), int(max_iters), _stream(stream)))
+    return in_set[: m.n]
+
+
+def b2sr_color(m: Matrix, priority: torch.Tensor, colors: Optional[torch.Tensor] = None, max_iters: int = 0,
+               stream=None) -> torch.Tensor:
+    """Colouring by rounds of local maxima: colour = the round in which a
+    vertex is the largest (priority, id) among its uncoloured neighbours."""
+    pr = _priority(m, priority)
+    if colors is None:
+        colors = torch.empty(max(m.n, 1), dtype=torch.int32, device=_dev())
+    _check(lib.b2sr_color(m.handle, _ptr(pr), _ptr(colors), int(max_iters), _stream(stream)))
+    return colors[: m.n]
 
 
 def b2sr_sssp_push(mT: Matrix, src: int, weights_t: Optional[torch.Tensor] = None,

@@ -181,12 +181,13 @@ static bool scheme_ok(b2sr_semiring sr, b2sr_vec in, b2sr_vec* out) {
     if (sr == B2SR_PLUS_TIMES && in == B2SR_VEC_BITS) { *out = B2SR_VEC_I32; return true; }
     if (sr == B2SR_PLUS_TIMES && in == B2SR_VEC_F32) { *out = B2SR_VEC_F32; return true; }
     if (sr == B2SR_MIN_PLUS && (in == B2SR_VEC_F32 || in == B2SR_VEC_I32)) { *out = in; return true; }
+    if (sr == B2SR_MAX_TIMES && in == B2SR_VEC_F32) { *out = B2SR_VEC_F32; return true; }
     return false;
 }
 
 static bool has_staged(int k, b2sr_semiring sr, b2sr_vec in) {
     return k <= 16 && in != B2SR_VEC_BITS &&
-           (sr == B2SR_PLUS_TIMES || sr == B2SR_MIN_PLUS || in == B2SR_VEC_BITS64);
+           (sr == B2SR_PLUS_TIMES || sr == B2SR_MIN_PLUS || sr == B2SR_MAX_TIMES || in == B2SR_VEC_BITS64);
 }
 
 static int64_t vec_words(int32_t n, b2sr_vec kind) {

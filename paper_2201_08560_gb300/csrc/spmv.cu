@@ -92,6 +92,24 @@ __device__ __forceinline__ bool mask_allows(const uint32_t* __restrict__ mask, i
     return comp ? !b : b;
 }
 
+// Every output row in [r0, r1) is excluded by a bitset mask (bits all 0, or
+// all 1 for a complemented mask): the masked store writes the semiring's
+// identity there whatever the tiles hold.  Rows past n store nothing.
+// Warp-collective.
+__device__ __forceinline__ bool rows_masked_out(const uint32_t* __restrict__ mask, int comp, int32_t n, int64_t r0,
+                                                int64_t r1) {
+    if (!mask) return false;
+    r1 = min(r1, (int64_t)n);
+    bool ok = true;
+    for (int64_t w = (r0 >> 5) + lane_id(); w * 32 < r1; w += 32) {
+        const int64_t lo = max(r0, w * 32), hi = min(r1, w * 32 + 32);
+        const uint32_t need = (hi - lo >= 32) ? 0xFFFFFFFFu : (((1u << (hi - lo)) - 1u) << (lo - w * 32));
+        const uint32_t m = comp ? __ldg(mask + w) : ~__ldg(mask + w);
+        ok &= (m & need) == need;
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
 // ---------------------------------------------------------------------------
 // accumulator storage: registers (static row index) or shared memory (one
 // column per lane, any row index)
@@ -214,20 +232,7 @@ struct SemBool {
     __device__ V comb(V a, V b) const { return a | b; }
     __device__ J jcomb(J a, J b) const { return a | b; }
     __device__ uint32_t xseg(int32_t Jc) const { return ld_bits(x, (int64_t)Jc * K, K); }
-    // Every output row in [r0, r1) is masked out (a complemented mask with all
-    // those bits set): the result there is false whatever the tiles hold.
-    // Rows past n store nothing.  Warp-collective.
-    __device__ bool saturated(int64_t r0, int64_t r1) const {
-        if (!mask || !comp) return false;
-        r1 = min(r1, (int64_t)n);
-        bool ok = true;
-        for (int64_t w = (r0 >> 5) + lane_id(); w * 32 < r1; w += 32) {
-            const int64_t lo = max(r0, w * 32), hi = min(r1, w * 32 + 32);
-            const uint32_t need = (hi - lo >= 32) ? 0xFFFFFFFFu : (((1u << (hi - lo)) - 1u) << (lo - w * 32));
-            ok &= (__ldg(mask + w) & need) == need;
-        }
-        return __all_sync(0xffffffffu, ok);
-    }
+    __device__ bool saturated(int64_t r0, int64_t r1) const { return rows_masked_out(mask, comp, n, r0, r1); }
     template <class A>
     __device__ void tile(A& acc, const uint32_t* w, uint32_t xs) const {
         if constexpr (K <= 8) {
@@ -284,7 +289,7 @@ struct SemCount {
     __device__ V comb(V a, V b) const { return a + b; }
     __device__ J jcomb(J a, J b) const { return a + b; }
     __device__ uint32_t xseg(int32_t Jc) const { return ld_bits(x, (int64_t)Jc * K, K); }
-    __device__ bool saturated(int64_t, int64_t) const { return false; }
+    __device__ bool saturated(int64_t r0, int64_t r1) const { return rows_masked_out(mask, comp, n, r0, r1); }
     template <class A>
     __device__ void tile(A& acc, const uint32_t* w, uint32_t xs) const {
 #pragma unroll
@@ -324,7 +329,7 @@ struct SemPlus {
     __device__ J jcomb(J a, J b) const { return csum_add(a, b); }
     __device__ V apply(V acc, G xv, float) const { return acc + xv; }
     __device__ V contrib(G xv, float) const { return xv; }
-    __device__ bool saturated(int64_t, int64_t) const { return false; }
+    __device__ bool saturated(int64_t r0, int64_t r1) const { return rows_masked_out(mask, comp, n, r0, r1); }
     __device__ void store_row(int32_t R, int r, V v) const {
         int64_t i = (int64_t)R * K + r;
         if (i < n) y[i] = mask_allows(mask, comp, i) ? v : 0.0f;
@@ -367,7 +372,7 @@ struct SemPlus4 {
     }
     __device__ V apply(V acc, G xv, float) const { return comb(acc, xv); }
     __device__ V contrib(G xv, float) const { return xv; }
-    __device__ bool saturated(int64_t, int64_t) const { return false; }
+    __device__ bool saturated(int64_t r0, int64_t r1) const { return rows_masked_out(mask, comp, n, r0, r1); }
     __device__ void store_row(int32_t R, int r, V v) const {
         int64_t i = (int64_t)R * K + r;
         if (i < n) y[i] = mask_allows(mask, comp, i) ? v : ident();
@@ -405,7 +410,7 @@ struct SemMinPlus {
     __device__ J jcomb(J a, J b) const { return fminf(a, b); }
     __device__ V apply(V acc, G xv, float wv) const { return fminf(acc, xv + wv); }
     __device__ V contrib(G xv, float wv) const { return xv + wv; }
-    __device__ bool saturated(int64_t, int64_t) const { return false; }
+    __device__ bool saturated(int64_t r0, int64_t r1) const { return rows_masked_out(mask, comp, n, r0, r1); }
     __device__ void store_row(int32_t R, int r, V v) const {
         int64_t i = (int64_t)R * K + r;
         if (i < n) y[i] = mask_allows(mask, comp, i) ? fminf(__ldg(x + i), v) : INFINITY;
@@ -440,10 +445,85 @@ struct SemMinI32 {
     __device__ J jcomb(J a, J b) const { return min(a, b); }
     __device__ V apply(V acc, G xv, float) const { return min(acc, xv); }
     __device__ V contrib(G xv, float) const { return xv; }
-    __device__ bool saturated(int64_t, int64_t) const { return false; }
+    __device__ bool saturated(int64_t r0, int64_t r1) const { return rows_masked_out(mask, comp, n, r0, r1); }
     __device__ void store_row(int32_t R, int r, V v) const {
         int64_t i = (int64_t)R * K + r;
         if (i < n) y[i] = mask_allows(mask, comp, i) ? min(__ldg(x + i), v) : INT_MAX;
+    }
+    template <class A>
+    __device__ void store(int32_t R, const A& acc) const {
+#pragma unroll
+        for (int r = 0; r < K; ++r) store_row(R, r, acc.get(r));
+    }
+};
+
+// bmv_bin_full_full over tropical max-times (Table 4: the local-maximum step
+// of MIS and colouring): y_i = max over neighbours j of x_j (A_ij = 1 is the
+// multiplicative identity, so x_j passes unchanged); -inf where no neighbour
+// or masked out.  max is exact, so the result does not depend on the order.
+template <int K>
+struct SemMaxF32 {
+    using V = float;
+    using G = float;
+    using J = float;
+    static constexpr int NV = K;
+    static constexpr bool kGather = true;
+    static constexpr bool kMayWeight = false;
+    static constexpr bool weighted = false;
+    const float* x;
+    float* y;
+    const uint32_t* mask;
+    int comp;
+    int32_t n;
+    __device__ const float* src() const { return x; }
+    __device__ const float* wts() const { return nullptr; }
+    __device__ const int32_t* voffs() const { return nullptr; }
+    __device__ V ident() const { return -INFINITY; }
+    __device__ V comb(V a, V b) const { return fmaxf(a, b); }
+    __device__ J jcomb(J a, J b) const { return fmaxf(a, b); }
+    __device__ V apply(V acc, G xv, float) const { return fmaxf(acc, xv); }
+    __device__ V contrib(G xv, float) const { return xv; }
+    __device__ bool saturated(int64_t r0, int64_t r1) const { return rows_masked_out(mask, comp, n, r0, r1); }
+    __device__ void store_row(int32_t R, int r, V v) const {
+        int64_t i = (int64_t)R * K + r;
+        if (i < n) y[i] = mask_allows(mask, comp, i) ? v : -INFINITY;
+    }
+    template <class A>
+    __device__ void store(int32_t R, const A& acc) const {
+#pragma unroll
+        for (int r = 0; r < K; ++r) store_row(R, r, acc.get(r));
+    }
+};
+
+// max over neighbours of 64-bit keys (priority bits above the vertex id: the
+// local-maximum test of MIS and colouring with ties broken by id); 0 is
+// below every key and stands for "no undecided neighbour"
+template <int K>
+struct SemMaxKey {
+    using V = unsigned long long;
+    using G = unsigned long long;
+    using J = unsigned long long;
+    static constexpr int NV = K;
+    static constexpr bool kGather = true;
+    static constexpr bool kMayWeight = false;
+    static constexpr bool weighted = false;
+    const unsigned long long* x;
+    unsigned long long* y;
+    const uint32_t* mask;
+    int comp;
+    int32_t n;
+    __device__ const unsigned long long* src() const { return x; }
+    __device__ const float* wts() const { return nullptr; }
+    __device__ const int32_t* voffs() const { return nullptr; }
+    __device__ V ident() const { return 0ull; }
+    __device__ V comb(V a, V b) const { return a > b ? a : b; }
+    __device__ J jcomb(J a, J b) const { return a > b ? a : b; }
+    __device__ V apply(V acc, G xv, float) const { return acc > xv ? acc : xv; }
+    __device__ V contrib(G xv, float) const { return xv; }
+    __device__ bool saturated(int64_t r0, int64_t r1) const { return rows_masked_out(mask, comp, n, r0, r1); }
+    __device__ void store_row(int32_t R, int r, V v) const {
+        int64_t i = (int64_t)R * K + r;
+        if (i < n) y[i] = mask_allows(mask, comp, i) ? v : 0ull;
     }
     template <class A>
     __device__ void store(int32_t R, const A& acc) const {
@@ -1314,6 +1394,14 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
             return run_spmv<K>(h, sem, nullptr, s, "spmv_min_i32", 8.0 * h->n + (mask ? h->n / 8.0 : 0.0), gate);
         });
     }
+    if (sr == B2SR_MAX_TIMES && in_kind == B2SR_VEC_F32 && out_kind == B2SR_VEC_F32) {
+        if (weights) return fail(B2SR_ERR_INVALID_ARG, "weights apply to MIN_PLUS only");
+        return with_k(h->k, [&](auto kc) -> b2sr_status {
+            constexpr int K = decltype(kc)::value;
+            SemMaxF32<K> sem{static_cast<const float*>(x), static_cast<float*>(y), mask, comp, h->n};
+            return run_spmv<K>(h, sem, nullptr, s, "spmv_max", 8.0 * h->n + (mask ? h->n / 8.0 : 0.0), gate);
+        });
+    }
     return fail(B2SR_ERR_INVALID_ARG, "unsupported semiring / vector kind combination");
 }
 
@@ -1324,6 +1412,16 @@ b2sr_status spmm64_dispatch(b2sr_matrix* h, const uint64_t* X, uint64_t* Y, cons
         SemOr64<K> sem{reinterpret_cast<const unsigned long long*>(X), reinterpret_cast<unsigned long long*>(Y),
                        reinterpret_cast<const unsigned long long*>(M), comp ? 1 : 0, h->n};
         return run_spmv<K>(h, sem, nullptr, s, "spmm_or64", (M ? 24.0 : 16.0) * h->n, gate);
+    });
+}
+
+b2sr_status spmv_maxkey_dispatch(b2sr_matrix* h, const uint64_t* x, uint64_t* y, const uint32_t* mask, int comp,
+                                 cudaStream_t s, const int32_t* gate) {
+    return with_k(h->k, [&](auto kc) -> b2sr_status {
+        constexpr int K = decltype(kc)::value;
+        SemMaxKey<K> sem{reinterpret_cast<const unsigned long long*>(x), reinterpret_cast<unsigned long long*>(y), mask,
+                         comp ? 1 : 0, h->n};
+        return run_spmv<K>(h, sem, nullptr, s, "spmv_maxkey", 16.0 * h->n + (mask ? h->n / 8.0 : 0.0), gate);
     });
 }
 
