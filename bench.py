@@ -673,6 +673,27 @@ def main():
         B.b2sr_timing_reset()
         extra["spmv_bool"] = {"tile_dim": TILE, "kernel_us": tb / nb * 1e3, "gteps": g.nnz / (tb / nb / 1e3) / 1e9,
                               "gbs": byb / nb / (tb / nb / 1e3) / 1e9}
+        # max-times (Table 4): the SpMV alone, then MIS and colouring by rounds of local maxima
+        xf = torch.from_numpy(np.random.default_rng(37).normal(size=g.n).astype(np.float32)).to(dev)
+        yf = torch.empty(g.n, dtype=torch.float32, device=dev)
+        B.b2sr_timing_enable(True)
+        for _ in range(10):
+            B.b2sr_spmv(m, B.MAX_TIMES, B.VEC_F32, xf, B.VEC_F32, yf)
+        torch.cuda.synchronize()
+        tm, nm, bym = B.b2sr_timing_read("spmv_max")
+        B.b2sr_timing_enable(False)
+        B.b2sr_timing_reset()
+        prio = torch.from_numpy(np.random.default_rng(31).permutation(g.n).astype(np.float32) + 1.0).to(dev)
+        ins = torch.empty(g.n, dtype=torch.int32, device=dev)
+        cols = torch.empty(g.n, dtype=torch.int32, device=dev)
+        t_mis = _timed(lambda: B.b2sr_mis(m, prio, ins), reps=3)
+        t_col = _timed(lambda: B.b2sr_color(m, prio, cols, method=B.COLOR_PUSH), reps=3)
+        t_col_mt = _timed(lambda: B.b2sr_color(m, prio, cols, method=B.COLOR_MAX_TIMES), reps=1)
+        extra["max_times_mis_colouring"] = {
+            "tile_dim": TILE, "spmv_max_kernel_us": tm / nm * 1e3, "spmv_max_gbs": bym / nm / (tm / nm / 1e3) / 1e9,
+            "priority": "random permutation of 1..n (seed 31)", "mis_ms": t_mis, "mis_size": int(ins.sum().item()),
+            "colouring_push_ms": t_col, "colouring_max_times_rounds_ms": t_col_mt,
+            "colours": int(cols.max().item()) + 1}
 
     if not args.no_extras:
         try:

@@ -442,17 +442,30 @@ b2sr_status b2sr_cc(b2sr_handle h, int32_t* labels, int max_iters, void* stream)
  * max_iters rounds (<= 0: n), checked every 4 rounds. */
 b2sr_status b2sr_mis(b2sr_handle h, const float* priority, int32_t* in_set, int max_iters, void* stream);
 
-/* Graph colouring by rounds of local maxima (the GC row of Table 4, on the
- * max-times semiring; no algorithm in the paper).  With the keys of b2sr_mis,
- * round r gives colour r to every uncoloured vertex whose key is the largest
- * among itself and its uncoloured neighbours: colour(v) = 0 if no neighbour
- * has a larger key, else 1 + the largest colour among the neighbours that
- * do.  Each colour class is an independent set.
+/* How b2sr_color computes the colours (the result is the same). */
+typedef enum {
+    B2SR_COLOR_AUTO = 0,      /* the push form */
+    B2SR_COLOR_MAX_TIMES = 1, /* rounds of max-times SpMVs (Table 4, GC) */
+    B2SR_COLOR_PUSH = 2       /* counters pushed along the frontier's rows */
+} b2sr_color_method;
+
+/* Graph colouring by priority levels (the GC row of Table 4; no algorithm in
+ * the paper).  With the keys of b2sr_mis, colour(v) = 0 if no neighbour has a
+ * larger key, else 1 + the largest colour among the neighbours that do; each
+ * colour class is an independent set.  MAX_TIMES: round r gives colour r to
+ * every uncoloured vertex whose key is the largest among itself and its
+ * uncoloured neighbours (a max-times SpMV per round, 8 rounds per CUDA-graph
+ * replay).  PUSH: cnt[v] = neighbours with a larger key, counted in one pass;
+ * the vertices coloured r push along their rows and a vertex whose count
+ * reaches 0 takes colour r + 1 (the levels of a topological sort; each edge
+ * read twice in all, 16 rounds per replay).
  *   priority device float[n], not NaN
  *   colors   device int32[n]
- * Symmetric matrices; self-loops are ignored.  Rounds run as a CUDA graph of
- * 8 gated rounds.  Errors as b2sr_mis. */
-b2sr_status b2sr_color(b2sr_handle h, const float* priority, int32_t* colors, int max_iters, void* stream);
+ * Symmetric matrices; self-loops are ignored.  B2SR_ERR_INVALID_ARG for a NaN
+ * priority or an unknown method; B2SR_ERR_NOT_CONVERGED if vertices are still
+ * uncoloured after max_iters rounds (<= 0: n), checked at each replay. */
+b2sr_status b2sr_color(b2sr_handle h, const float* priority, int32_t* colors, b2sr_color_method method,
+                       int max_iters, void* stream);
 
 /* Triangle count (Sec. V TC): sum(L .* (L L^T)) for L = b2sr_lower(h), by
  * b2sr_spgemm_masked_count.  Symmetric matrices.  count device int64[1]. */

@@ -92,7 +92,7 @@ def _load() -> ctypes.CDLL:
         "b2sr_pagerank": (c_int, [p, f32, c_int, p, p, p]),
         "b2sr_cc": (c_int, [p, p, c_int, p]),
         "b2sr_mis": (c_int, [p, p, p, c_int, p]),
-        "b2sr_color": (c_int, [p, p, p, c_int, p]),
+        "b2sr_color": (c_int, [p, p, p, c_int, c_int, p]),
         "b2sr_tc": (c_int, [p, p, p]),
         "b2sr_server_create": (c_int, [i64, c_int, c_int, pp]),
         "b2sr_server_add_graph": (c_int, [p, p, ctypes.POINTER(i32)]),
@@ -416,14 +416,17 @@ def b2sr_mis(m: Matrix, priority: torch.Tensor, in_set: Optional[torch.Tensor] =
     return in_set[: m.n]
 
 
-def b2sr_color(m: Matrix, priority: torch.Tensor, colors: Optional[torch.Tensor] = None, max_iters: int = 0,
-               stream=None) -> torch.Tensor:
-    """Colouring by rounds of local maxima: colour = the round in which a
-    vertex is the largest (priority, id) among its uncoloured neighbours."""
+COLOR_AUTO, COLOR_MAX_TIMES, COLOR_PUSH = 0, 1, 2
+
+
+def b2sr_color(m: Matrix, priority: torch.Tensor, colors: Optional[torch.Tensor] = None,
+               method: int = COLOR_AUTO, max_iters: int = 0, stream=None) -> torch.Tensor:
+    """Colouring by priority levels: 0 without a larger (priority, id)
+    neighbour, else 1 + the largest colour among the larger neighbours."""
     pr = _priority(m, priority)
     if colors is None:
         colors = torch.empty(max(m.n, 1), dtype=torch.int32, device=_dev())
-    _check(lib.b2sr_color(m.handle, _ptr(pr), _ptr(colors), int(max_iters), _stream(stream)))
+    _check(lib.b2sr_color(m.handle, _ptr(pr), _ptr(colors), int(method), int(max_iters), _stream(stream)))
     return colors[: m.n]
 
 

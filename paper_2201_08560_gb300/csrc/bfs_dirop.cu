@@ -18,6 +18,7 @@
 
 #include "b2sr_internal.cuh"
 #include "captured.cuh"
+#include "tile_bits.cuh"
 
 namespace b2sr {
 b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, const void* x, b2sr_vec out_kind,
@@ -57,21 +58,6 @@ enum : int {
 // together (a hub's out-edges), the others by one warp each.
 constexpr int32_t kLongRow = 2048;
 
-template <int K>
-__device__ __forceinline__ uint32_t tile_row_of(const uint32_t* w, int r) {
-    if (K == 32) return w[r];
-    if (K == 16) return (w[r >> 1] >> (16 * (r & 1))) & 0xFFFFu;
-    return (w[r >> 2] >> (8 * (r & 3))) & 0xFFu;
-}
-
-template <int K>
-__device__ __forceinline__ uint32_t segment(const uint32_t* bits, int32_t J) {
-    if (K == 32) return bits[J];
-    if (K == 16) return reinterpret_cast<const uint16_t*>(bits)[J];
-    if (K == 8) return reinterpret_cast<const uint8_t*>(bits)[J];
-    return (reinterpret_cast<const uint8_t*>(bits)[J >> 1] >> ((J & 1) * 4)) & 0xFu;
-}
-
 __global__ void dirop_decide_kernel(long long* ctl, int32_t n) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (!ctl[C_ACTIVE]) {
@@ -110,7 +96,7 @@ __global__ void __launch_bounds__(256) dirop_push_kernel(const int32_t* __restri
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     // every warp takes a slice of each long tile-row, the short ones a warp each
     auto push_tiles = [&](int32_t J, int64_t t_begin, int64_t t_end, int64_t stride) {
-        const uint32_t amask = segment<K>(frontier, J);
+        const uint32_t amask = seg_bits<K>(frontier, J);
         for (int64_t t = t_begin + lane; t < t_end; t += stride) {
             uint32_t wd[TW];
             const uint32_t* tp = reinterpret_cast<const uint32_t*>(tiles + t * TB);
@@ -119,11 +105,11 @@ __global__ void __launch_bounds__(256) dirop_push_kernel(const int32_t* __restri
             uint32_t cols = 0u;  // union of the frontier rows' bits: targets I*K + c
 #pragma unroll
             for (int r = 0; r < K; ++r)
-                if ((amask >> r) & 1u) cols |= tile_row_of<K>(wd, r);
+                if ((amask >> r) & 1u) cols |= tile_row<K>(wd, r);
             if (!cols) continue;
             const int32_t I = __ldg(colind + t);
             const int64_t base = (int64_t)I * K;
-            cols &= ~segment<K>(visited, I);
+            cols &= ~seg_bits<K>(visited, I);
             if (!cols) continue;
             // the K bits of segment I sit in one 32-bit word of the bitset
             atomicOr(next + (base >> 5), cols << (int)(base & 31));

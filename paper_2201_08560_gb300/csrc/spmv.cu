@@ -27,6 +27,7 @@
 #include <type_traits>
 
 #include "b2sr_internal.cuh"
+#include "tile_bits.cuh"
 
 namespace b2sr {
 
@@ -44,13 +45,6 @@ struct ChunkShape {
     static constexpr int TILE_V4 = P * TB / 16;  // uint4 loads per lane for its tiles
     static constexpr int ROW_BITS = K <= 8 ? 8 : K;  // bits per row slot in a word
 };
-
-template <int K>
-__device__ __forceinline__ uint32_t row_word(const uint32_t* w, int r) {
-    if (K == 32) return w[r];
-    if (K == 16) return (w[r >> 1] >> (16 * (r & 1))) & 0xFFFFu;
-    return (w[r >> 2] >> (8 * (r & 3))) & 0xFFu;
-}
 
 // Bit r of the result is set iff row r of the tile shares a bit with xs (the
 // k-bit segment of the input vector under the tile's column).
@@ -94,11 +88,14 @@ __device__ __forceinline__ bool mask_allows(const uint32_t* __restrict__ mask, i
 
 // Every output row in [r0, r1) is excluded by a bitset mask (bits all 0, or
 // all 1 for a complemented mask): the masked store writes the semiring's
-// identity there whatever the tiles hold.  Rows past n store nothing.
-// Warp-collective.
+// identity there whatever the tiles hold.  Rows past n store nothing; spans
+// of more than 2048 rows are not tested (false).
+// Warp-collective.  Semirings whose masked calls sit on a level loop (BFS,
+// MIS, colouring) use it; in the others the test's registers cost more
+// occupancy than the skip saves, and saturated() is constant false.
 __device__ __forceinline__ bool rows_masked_out(const uint32_t* __restrict__ mask, int comp, int32_t n, int64_t r0,
                                                 int64_t r1) {
-    if (!mask) return false;
+    if (!mask || r1 - r0 > 2048) return false;  // at most two mask words a lane
     r1 = min(r1, (int64_t)n);
     bool ok = true;
     for (int64_t w = (r0 >> 5) + lane_id(); w * 32 < r1; w += 32) {
@@ -289,11 +286,11 @@ struct SemCount {
     __device__ V comb(V a, V b) const { return a + b; }
     __device__ J jcomb(J a, J b) const { return a + b; }
     __device__ uint32_t xseg(int32_t Jc) const { return ld_bits(x, (int64_t)Jc * K, K); }
-    __device__ bool saturated(int64_t r0, int64_t r1) const { return rows_masked_out(mask, comp, n, r0, r1); }
+    __device__ bool saturated(int64_t, int64_t) const { return false; }
     template <class A>
     __device__ void tile(A& acc, const uint32_t* w, uint32_t xs) const {
 #pragma unroll
-        for (int r = 0; r < K; ++r) acc.set(r, acc.get(r) + __popc(row_word<K>(w, r) & xs));
+        for (int r = 0; r < K; ++r) acc.set(r, acc.get(r) + __popc(tile_row<K>(w, r) & xs));
     }
     template <class A>
     __device__ void store(int32_t R, const A& acc) const {
@@ -329,7 +326,7 @@ struct SemPlus {
     __device__ J jcomb(J a, J b) const { return csum_add(a, b); }
     __device__ V apply(V acc, G xv, float) const { return acc + xv; }
     __device__ V contrib(G xv, float) const { return xv; }
-    __device__ bool saturated(int64_t r0, int64_t r1) const { return rows_masked_out(mask, comp, n, r0, r1); }
+    __device__ bool saturated(int64_t, int64_t) const { return false; }
     __device__ void store_row(int32_t R, int r, V v) const {
         int64_t i = (int64_t)R * K + r;
         if (i < n) y[i] = mask_allows(mask, comp, i) ? v : 0.0f;
@@ -372,7 +369,7 @@ struct SemPlus4 {
     }
     __device__ V apply(V acc, G xv, float) const { return comb(acc, xv); }
     __device__ V contrib(G xv, float) const { return xv; }
-    __device__ bool saturated(int64_t r0, int64_t r1) const { return rows_masked_out(mask, comp, n, r0, r1); }
+    __device__ bool saturated(int64_t, int64_t) const { return false; }
     __device__ void store_row(int32_t R, int r, V v) const {
         int64_t i = (int64_t)R * K + r;
         if (i < n) y[i] = mask_allows(mask, comp, i) ? v : ident();
@@ -410,7 +407,7 @@ struct SemMinPlus {
     __device__ J jcomb(J a, J b) const { return fminf(a, b); }
     __device__ V apply(V acc, G xv, float wv) const { return fminf(acc, xv + wv); }
     __device__ V contrib(G xv, float wv) const { return xv + wv; }
-    __device__ bool saturated(int64_t r0, int64_t r1) const { return rows_masked_out(mask, comp, n, r0, r1); }
+    __device__ bool saturated(int64_t, int64_t) const { return false; }
     __device__ void store_row(int32_t R, int r, V v) const {
         int64_t i = (int64_t)R * K + r;
         if (i < n) y[i] = mask_allows(mask, comp, i) ? fminf(__ldg(x + i), v) : INFINITY;
@@ -445,7 +442,7 @@ struct SemMinI32 {
     __device__ J jcomb(J a, J b) const { return min(a, b); }
     __device__ V apply(V acc, G xv, float) const { return min(acc, xv); }
     __device__ V contrib(G xv, float) const { return xv; }
-    __device__ bool saturated(int64_t r0, int64_t r1) const { return rows_masked_out(mask, comp, n, r0, r1); }
+    __device__ bool saturated(int64_t, int64_t) const { return false; }
     __device__ void store_row(int32_t R, int r, V v) const {
         int64_t i = (int64_t)R * K + r;
         if (i < n) y[i] = mask_allows(mask, comp, i) ? min(__ldg(x + i), v) : INT_MAX;
@@ -483,7 +480,7 @@ struct SemMaxF32 {
     __device__ J jcomb(J a, J b) const { return fmaxf(a, b); }
     __device__ V apply(V acc, G xv, float) const { return fmaxf(acc, xv); }
     __device__ V contrib(G xv, float) const { return xv; }
-    __device__ bool saturated(int64_t r0, int64_t r1) const { return rows_masked_out(mask, comp, n, r0, r1); }
+    __device__ bool saturated(int64_t, int64_t) const { return false; }
     __device__ void store_row(int32_t R, int r, V v) const {
         int64_t i = (int64_t)R * K + r;
         if (i < n) y[i] = mask_allows(mask, comp, i) ? v : -INFINITY;
@@ -558,7 +555,7 @@ struct SemOr64 {
     // Every output row in [r0, r1) is fully masked out (complemented mask of
     // all ones): zero whatever the tiles hold.  Warp-collective.
     __device__ bool saturated(int64_t r0, int64_t r1) const {
-        if (!mask || !comp) return false;
+        if (!mask || !comp || r1 - r0 > 9 * K) return false;  // up to nine tile-rows
         r1 = min(r1, (int64_t)n);
         bool ok = true;
         for (int64_t i = r0 + lane_id(); i < r1; i += 32) ok &= __ldg(mask + i) == ~0ull;
@@ -836,7 +833,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
     bool sat = false;
     {
         const int32_t ra = __ldg(g.chunk_row + c), rb = __ldg(g.chunk_row + c + 1);
-        if (rb - ra <= 8) sat = sem.saturated((int64_t)ra * K, ((int64_t)rb + 1) * K);
+        sat = sem.saturated((int64_t)ra * K, ((int64_t)rb + 1) * K);
     }
     if (!sat) {
         load_lane_tiles<K>(g, ls.tl, tv, col);
@@ -953,7 +950,7 @@ __global__ void __launch_bounds__(kSpmvThreads, (gather_min_blocks<K, SEM>())) s
     bool sat = false;
     {
         const int32_t ra = __ldg(g.chunk_row + c), rb = __ldg(g.chunk_row + c + 1);
-        if (rb - ra <= 8) sat = sem.saturated((int64_t)ra * K, ((int64_t)rb + 1) * K);
+        sat = sem.saturated((int64_t)ra * K, ((int64_t)rb + 1) * K);
     }
     if (!sat) {
         load_lane_tiles<K>(g, ls.tl, tv, col);

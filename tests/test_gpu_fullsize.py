@@ -1,10 +1,12 @@
 """GPU parity at the benchmark sizes, through the same entry points and
 launch configuration the benchmark times:
 
-  * R-MAT scale 20 ef16 (the main workload, k = 8): the B2SR arrays, the
-    Boolean, plus-times and int-min SpMVs, PageRank (50 iterations) and CC
-    against the oracle in full; the 16-source batched BFS on three sampled
-    sources in full;
+  * R-MAT scale 20 ef16 (the main workload, at k = 4 with the direct
+    schedule as the benchmark runs it, and at k = 8 with the default one): the
+    B2SR arrays, the Boolean, plus-times and int-min SpMVs, PageRank (50
+    iterations) and CC against the oracle in full; the 16-source batched BFS
+    on three sampled sources in full; MIS and colouring with a random
+    priority permutation in full;
   * the 4096 x 4096 grid with lattice weights: push SSSP from the corner, in
     full and bit-exact (every path sum is exact in fp32);
   * R-MAT scale 18 ef32: the triangle count against the oracle's count stored
@@ -38,10 +40,17 @@ def B():
 
 
 @pytest.fixture(scope="module")
-def rmat20(B):
-    g = graphs.rmat(20, 16, seed=1)
+def rmat20_graph():
+    return graphs.rmat(20, 16, seed=1)
+
+
+@pytest.fixture(scope="module", params=[(4, 2), (8, 0)], ids=["k4-direct", "k8"])
+def rmat20(B, rmat20_graph, request):
+    g = rmat20_graph
+    k, sched = request.param
     rp, ci = csr_dev(g)
-    m = B.b2sr_from_csr(g.n, rp, ci, 8)
+    m = B.b2sr_from_csr(g.n, rp, ci, k)
+    B.b2sr_set_schedule(m, sched)
     yield g, m
     m.close()
 
@@ -49,7 +58,7 @@ def rmat20(B):
 def test_rmat20_b2sr_arrays(B, rmat20):
     g, m = rmat20
     trp, tci, tiles = B.b2sr_export(m)
-    otrp, otci, otiles = oracle.b2sr(g, 8)
+    otrp, otci, otiles = oracle.b2sr(g, m.tile_dim)
     assert m.n_tiles == len(otci) and m.nnz == len(g.colind)
     np.testing.assert_array_equal(to_np(trp), otrp)
     np.testing.assert_array_equal(to_np(tci), otci)
@@ -90,6 +99,16 @@ def test_rmat20_pagerank50(B, rmat20):
 def test_rmat20_cc(B, rmat20):
     g, m = rmat20
     np.testing.assert_array_equal(to_np(B.b2sr_cc(m)), oracle.cc(g))
+
+
+def test_rmat20_mis_and_colouring(B, rmat20):
+    g, m = rmat20
+    pr = np.random.default_rng(31).permutation(g.n).astype(np.float32) + 1.0   # the benchmark's priorities
+    p = torch.from_numpy(pr).cuda()
+    np.testing.assert_array_equal(to_np(B.b2sr_mis(m, p)), oracle.mis_greedy(g, pr.astype(np.float64)))
+    ref = oracle.color_levels(g, pr.astype(np.float64))
+    np.testing.assert_array_equal(to_np(B.b2sr_color(m, p, method=B.COLOR_PUSH)), ref)
+    np.testing.assert_array_equal(to_np(B.b2sr_color(m, p, method=B.COLOR_MAX_TIMES)), ref)
 
 
 def test_grid4096_sssp(B):

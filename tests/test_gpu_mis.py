@@ -111,13 +111,24 @@ def test_mis(B, mats, k, gi, kind, sched):
 @pytest.mark.parametrize("gi", range(len(GRAPH_IDS)), ids=GRAPH_IDS)
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("sched", SCHEDS, ids=["staged", "direct"])
-def test_color(B, mats, k, gi, kind, sched):
+def test_color_max_times(B, mats, k, gi, kind, sched):
     g, m = mats(gi, k, sym=True)
     B.b2sr_set_schedule(m, sched)
     pr = priorities(g.n, kind, gi + 13)
-    got = to_np(B.b2sr_color(m, to_dev(pr)))
+    got = to_np(B.b2sr_color(m, to_dev(pr), method=B.COLOR_MAX_TIMES))
     np.testing.assert_array_equal(got, oracle.color_levels(g, pr.astype(np.float64)))
     B.b2sr_set_schedule(m, 0)
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("gi", range(len(GRAPH_IDS)), ids=GRAPH_IDS)
+@pytest.mark.parametrize("kind", KINDS)
+def test_color_push(B, mats, k, gi, kind):
+    g, m = mats(gi, k, sym=True)
+    pr = priorities(g.n, kind, gi + 13)
+    ref = oracle.color_levels(g, pr.astype(np.float64))
+    np.testing.assert_array_equal(to_np(B.b2sr_color(m, to_dev(pr), method=B.COLOR_PUSH)), ref)
+    np.testing.assert_array_equal(to_np(B.b2sr_color(m, to_dev(pr))), ref)          # AUTO
 
 
 @pytest.mark.parametrize("k", [4, 8])
@@ -127,9 +138,12 @@ def test_mis_and_color_rmat16(B, k):
     pr = priorities(g.n, "distinct", 3)
     with B.b2sr_from_csr(g.n, rp, ci, k) as m:
         s = to_np(B.b2sr_mis(m, to_dev(pr)))
-        c = to_np(B.b2sr_color(m, to_dev(pr)))
+        c = to_np(B.b2sr_color(m, to_dev(pr), method=B.COLOR_PUSH))
+        c2 = to_np(B.b2sr_color(m, to_dev(pr), method=B.COLOR_MAX_TIMES))
     np.testing.assert_array_equal(s, oracle.mis_greedy(g, pr.astype(np.float64)))
-    np.testing.assert_array_equal(c, oracle.color_levels(g, pr.astype(np.float64)))
+    ref = oracle.color_levels(g, pr.astype(np.float64))
+    np.testing.assert_array_equal(c, ref)
+    np.testing.assert_array_equal(c2, ref)
 
 
 def test_mis_color_errors(B, mats):
@@ -141,15 +155,20 @@ def test_mis_color_errors(B, mats):
         B.b2sr_mis(m, to_dev(bad))
     with pytest.raises(B.B2SRError, match="INVALID"):
         B.b2sr_color(m, to_dev(bad))
+    with pytest.raises(B.B2SRError, match="INVALID"):
+        B.b2sr_color(m, to_dev(bad), method=B.COLOR_MAX_TIMES)
+    with pytest.raises(B.B2SRError, match="INVALID"):
+        B.b2sr_color(m, to_dev(pr), method=7)
     with pytest.raises(ValueError):
         B.b2sr_mis(m, to_dev(pr.astype(np.float64)))
     path = graphs.path(300)                              # falling priorities: 300 colours
     rp, ci = csr_dev(path)
     with B.b2sr_from_csr(path.n, rp, ci, 8) as mp:
         fall = (1000.0 - np.arange(300)).astype(np.float32)
-        with pytest.raises(B.B2SRError, match="NOT_CONVERGED"):
-            B.b2sr_color(mp, to_dev(fall), max_iters=16)
-        np.testing.assert_array_equal(to_np(B.b2sr_color(mp, to_dev(fall))), np.arange(300))
+        for method in (B.COLOR_MAX_TIMES, B.COLOR_PUSH):
+            with pytest.raises(B.B2SRError, match="NOT_CONVERGED"):
+                B.b2sr_color(mp, to_dev(fall), method=method, max_iters=16)
+            np.testing.assert_array_equal(to_np(B.b2sr_color(mp, to_dev(fall), method=method)), np.arange(300))
         np.testing.assert_array_equal(to_np(B.b2sr_mis(mp, to_dev(fall))), np.arange(300) % 2 == 0)
 
 
