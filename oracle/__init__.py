@@ -57,6 +57,9 @@ def _load():
                 "orc_spmv_min_i32": (None, [i32, p, p, p, p, p, ctypes.c_int]),
                 "orc_spmm_or64": (None, [i32, p, p, p, p, p, ctypes.c_int]),
                 "orc_spmv_max": (None, [i32, p, p, p, p, p, ctypes.c_int]),
+                "orc_b2sr_planes": (ctypes.c_int, [i32, p, p, p, ctypes.c_int, ctypes.c_int, p, p, p]),
+                "orc_spmv_wcount": (None, [i32, p, p, p, p, p, p, ctypes.c_int]),
+                "orc_spmv_wplus": (None, [i32, p, p, p, p, p, p, ctypes.c_int]),
                 "orc_mis_greedy": (ctypes.c_int, [i32, p, p, p, p]),
                 "orc_color_levels": (ctypes.c_int, [i32, p, p, p, p]),
                 "orc_masked_count": (i64, [i32, p, p, p, p, p, p]),
@@ -222,6 +225,48 @@ def spmv_max(g, x, mask=None, complement=False):
     m = None if mask is None else _c(mask, np.uint32)
     _load().orc_spmv_max(G.n, _ptr(G.rowptr), _ptr(G.colind), _ptr(xd), _ptr(y), _ptr(m),
                          _mask_mode(mask, complement))
+    return y
+
+
+def b2sr_planes(g, w, bits: int, k: int):
+    """Bit-planes of integer weights w (CSR order of g, each < 2^bits) over the
+    tile index of b2sr(g, k): uint array [T, bits, k] of the tile word dtype."""
+    G = _G(g)
+    wv = _c(w, np.uint32)
+    if wv.size != int(G.rowptr[-1]):
+        raise ValueError("one weight per CSR entry")
+    wv = wv if wv.size else np.zeros(1, np.uint32)
+    trp, tci, _ = b2sr(G, k)
+    T = len(tci)
+    out = np.zeros(max(T, 1) * bits * k * WORD_BYTES[k], dtype=np.uint8)
+    rc = _load().orc_b2sr_planes(G.n, _ptr(G.rowptr), _ptr(G.colind), _ptr(wv), int(bits), int(k), _ptr(trp),
+                                 _ptr(tci if T else np.zeros(1, np.int32)), _ptr(out))
+    if rc != 0:
+        raise ValueError("weights do not fit the bit width")
+    return out[: T * bits * k * WORD_BYTES[k]].view(WORD_DTYPE[k]).reshape(T, bits, k).copy()
+
+
+def spmv_wcount(g, w, x_bits, mask=None, complement=False):
+    """y_i = sum_{j in row i, x_j = 1} w_ij (int64)."""
+    G = _G(g)
+    wv = _c(w, np.uint32) if len(w) else np.zeros(1, np.uint32)
+    x = _c(x_bits, np.uint32)
+    y = np.zeros(G.n, dtype=np.int64)
+    m = None if mask is None else _c(mask, np.uint32)
+    _load().orc_spmv_wcount(G.n, _ptr(G.rowptr), _ptr(G.colind), _ptr(wv), _ptr(x), _ptr(y), _ptr(m),
+                            _mask_mode(mask, complement))
+    return y
+
+
+def spmv_wplus(g, w, x, mask=None, complement=False):
+    """y_i = sum_{j in row i} w_ij x_j (fp64)."""
+    G = _G(g)
+    wv = _c(w, np.uint32) if len(w) else np.zeros(1, np.uint32)
+    xd = _c(x, np.float64)
+    y = np.zeros(G.n, dtype=np.float64)
+    m = None if mask is None else _c(mask, np.uint32)
+    _load().orc_spmv_wplus(G.n, _ptr(G.rowptr), _ptr(G.colind), _ptr(wv), _ptr(xd), _ptr(y), _ptr(m),
+                           _mask_mode(mask, complement))
     return y
 
 

@@ -303,6 +303,69 @@ void orc_spmm_or64(int32_t n, const int32_t* rowptr, const int32_t* colind, cons
 }
 
 /* ------------------------------------------------------------------------ */
+/* Short-bit-width weights as bit-planes (Sec. VII: an integer weight matrix  */
+/* W = sum_p 2^p A_p, each A_p binary)                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Bit-planes of integer weights w (CSR order, each < 2^bits) over the tile
+ * index of the pattern's B2SR (tile_rowptr, tile_colind as built by
+ * orc_b2sr_fill): plane p of tile t holds bit (r, c) iff the entry at row
+ * kI+r, column kJ+c has bit p set in its weight.  Layout: tile by tile,
+ * plane by plane, k words of word_bytes(k) each.  Duplicate entries OR. */
+int orc_b2sr_planes(int32_t n, const int32_t* rowptr, const int32_t* colind, const uint32_t* w, int bits, int k,
+                    const int32_t* tile_rowptr, const int32_t* tile_colind, uint8_t* planes) {
+    int wb = word_bytes(k);
+    if (wb == 0 || bits < 1 || bits > 16) return ORC_EINVAL;
+    int64_t ntr = ((int64_t)n + k - 1) / k;
+    int64_t T = tile_rowptr[ntr];
+    int64_t plane_bytes = (int64_t)k * wb;
+    memset(planes, 0, (size_t)(T * bits * plane_bytes));
+    for (int64_t row = 0; row < n; ++row) {
+        int64_t I = row / k, t0 = tile_rowptr[I], t1 = tile_rowptr[I + 1];
+        for (int64_t e = rowptr[row]; e < rowptr[row + 1]; ++e) {
+            if (w[e] >> bits) return ORC_EINVAL;
+            int32_t J = colind[e] / k;
+            int64_t lo = t0, hi = t1;
+            while (lo < hi) {
+                int64_t mid = (lo + hi) / 2;
+                if (tile_colind[mid] < J) lo = mid + 1; else hi = mid;
+            }
+            if (lo == t1 || tile_colind[lo] != J) return ORC_EINVAL;
+            int64_t r = row % k, c = colind[e] % k;
+            for (int p = 0; p < bits; ++p)
+                if ((w[e] >> p) & 1u) {
+                    uint8_t* word = planes + ((lo * bits + p) * k + r) * wb;
+                    word[c >> 3] |= (uint8_t)(1u << (c & 7));
+                }
+        }
+    }
+    return ORC_OK;
+}
+
+/* Weighted count (bmv_bin_bin_full over W): y_i = sum_{j in row i, x_j = 1}
+ * w_ij in int64; masked-out rows 0. */
+void orc_spmv_wcount(int32_t n, const int32_t* rowptr, const int32_t* colind, const uint32_t* w,
+                     const uint32_t* x, int64_t* y, const uint32_t* mask, int mask_mode) {
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t s = 0;
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+            if (bit_get(x, colind[e])) s += w[e];
+        y[i] = mask_allows(mask, mask_mode, i) ? s : 0;
+    }
+}
+
+/* Weighted plus-times (bmv_bin_full_full over W): y_i = sum_{j in row i}
+ * w_ij x_j in fp64, CSR order; masked-out rows 0. */
+void orc_spmv_wplus(int32_t n, const int32_t* rowptr, const int32_t* colind, const uint32_t* w,
+                    const double* x, double* y, const uint32_t* mask, int mask_mode) {
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) s += (double)w[e] * x[colind[e]];
+        y[i] = mask_allows(mask, mask_mode, i) ? s : 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* SpGEMM (Table 3 and the Boolean product)                                   */
 /* ------------------------------------------------------------------------ */
 
