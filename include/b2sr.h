@@ -81,8 +81,9 @@ typedef enum {
     B2SR_VEC_BITS = 0, /* bitset, ceil(n/32) uint32 words */
     B2SR_VEC_I32 = 1,  /* int32[n] */
     B2SR_VEC_F32 = 2,  /* float[n] */
-    B2SR_VEC_BITS64 = 3 /* uint64[n]: 64 Boolean vectors, one bit each per vertex
-                           (the b2sr_spmm_bits64 scheme; accepted by b2sr_autotune only) */
+    B2SR_VEC_BITS64 = 3, /* uint64[n]: 64 Boolean vectors, one bit each per vertex
+                            (the b2sr_spmm_bits64 scheme; accepted by b2sr_autotune only) */
+    B2SR_VEC_I64 = 4     /* int64[n] (the weighted count of b2sr_spmv_planes) */
 } b2sr_vec;
 
 /* SpMV kernel schedule for the value schemes (plus-times on floats, min-plus,
@@ -186,6 +187,16 @@ b2sr_status b2sr_destroy(b2sr_handle h);
  * (Sec. V, TC).  Synchronises `stream` once. */
 b2sr_status b2sr_lower(b2sr_handle h, void* stream, b2sr_handle* out);
 
+/* B2SR of the transpose A^T, as a new handle with the same tile_dim (Sec.
+ * III-A: the tile index is transposed by taking TileRowPtr/TileColInd from
+ * CSR to CSC order; Sec. III-B: the tiles take the other packing, i.e. each
+ * k x k bit tile is transposed).  vxm, y^T = x^T A, is b2sr_spmv on the
+ * result; b2sr_sssp_push and b2sr_bfs_diropt take it as their transpose on
+ * directed graphs.  Enqueued on `stream`, synchronised before returning (the
+ * handle's sizes are read back).  The caller destroys *out.
+ * B2SR_ERR_OOM past 2^32 tiles or on allocation failure. */
+b2sr_status b2sr_transpose(b2sr_handle h, void* stream, b2sr_handle* out);
+
 /* Reorders per-entry fp32 weights given in CSR order (the CSR that built h,
  * any row order, no repeated entries) into set-bit order: tile by tile, row
  * word by row word, bit by bit.  That is the `weights` layout b2sr_spmv and
@@ -231,6 +242,41 @@ b2sr_status b2sr_weights_from_csr(b2sr_handle h, const int32_t* rowptr, const in
 b2sr_status b2sr_spmv(b2sr_handle h, b2sr_semiring semiring, b2sr_vec in_kind, const void* x,
                       b2sr_vec out_kind, void* y, const uint32_t* mask, int mask_complement,
                       const float* weights, void* stream);
+
+/* Short-bit-width integer weights as bit-planes (Sec. VII: a weighted
+ * graph whose weights are small integers is the sum W = sum_p 2^p A_p of
+ * binary matrices, each of which B2SR holds).  Plane p of tile t is a k x k
+ * bit tile in h's packing (bit (r, c) set iff the entry at row kI+r, column
+ * kJ+c has bit p set in its weight), over h's tile index; planes are stored
+ * tile by tile, plane by plane: byte offset (t * bits + p) * tile_bytes,
+ * tile_bytes = k * word_bytes (4, 8, 32, 128 for k = 4, 8, 16, 32).
+ *   rowptr, colind  device; the CSR that built h (any row order, no repeated
+ *                   entries)
+ *   w_csr    device uint32[nnz], CSR order, each < 2^bits
+ *   bits     1..16
+ *   planes   device, 4-byte aligned, n_tiles * bits * tile_bytes bytes,
+ *            written (zeroed first); owned by the caller
+ * B2SR_ERR_INVALID_ARG if an entry is not in h or a weight needs more bits.
+ * Synchronises the stream. */
+b2sr_status b2sr_planes_from_csr(b2sr_handle h, const int32_t* rowptr, const int32_t* colind,
+                                 const uint32_t* w_csr, int bits, void* planes, void* stream);
+
+/* SpMV over bit-plane weights (Sec. VII extension; the bin-bin-full and
+ * bin-full-full schemes of Table 2 applied per plane):
+ *   BITS -> I64   y_i = sum_J sum_p 2^p popc(P_p,IJ[r] & x_J) = sum_{j: x_j=1} w_ij,
+ *                 exact in int64
+ *   F32  -> F32   y_i = sum_j w_ij x_j with w_ij = sum_p 2^p (P_p)_ij formed
+ *                 exactly per entry; compensated fp32 sums in a fixed order
+ *                 (bitwise reproducible)
+ *   planes   device, as written by b2sr_planes_from_csr with the same bits
+ *   x, y     device; y must not alias x or mask
+ *   mask     device bitset or NULL (mask_complement as b2sr_spmv); excluded
+ *            outputs are 0
+ * A warp per tile-row, a 512-thread block per tile-row of more than 2,048
+ * tiles.  B2SR_ERR_INVALID_ARG for other vector kinds or bits outside 1..16. */
+b2sr_status b2sr_spmv_planes(b2sr_handle h, const void* planes, int bits, b2sr_vec in_kind, const void* x,
+                             b2sr_vec out_kind, void* y, const uint32_t* mask, int mask_complement,
+                             void* stream);
 
 /* Boolean SpMM with 64 frontiers packed per vertex (multi-source BFS step; a
  * batched form of bmv_bin_bin_bin_masked, Table 2, with the complemented

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libb2sr.so")
 
 BOOL_OR_AND, PLUS_TIMES, MIN_PLUS, MAX_TIMES = 0, 1, 2, 3
-VEC_BITS, VEC_I32, VEC_F32, VEC_BITS64 = 0, 1, 2, 3
+VEC_BITS, VEC_I32, VEC_F32, VEC_BITS64, VEC_I64 = 0, 1, 2, 3, 4
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_TILE", 3: "OOM", 4: "CUDA", 5: "NOT_CONVERGED",
           6: "ADMISSION_REFUSED", 7: "ABORTED"}
 WORD_BYTES = {4: 1, 8: 1, 16: 2, 32: 4}
@@ -71,6 +71,9 @@ def _load() -> ctypes.CDLL:
         "b2sr_export": (c_int, [p, p, p, p, p]),
         "b2sr_destroy": (c_int, [p]),
         "b2sr_lower": (c_int, [p, p, pp]),
+        "b2sr_transpose": (c_int, [p, p, pp]),
+        "b2sr_planes_from_csr": (c_int, [p, p, p, p, c_int, p, p]),
+        "b2sr_spmv_planes": (c_int, [p, p, c_int, c_int, p, c_int, p, p, c_int, p]),
         "b2sr_weights_from_csr": (c_int, [p, p, p, p, p, p]),
         "b2sr_spmv": (c_int, [p, c_int, c_int, p, c_int, p, p, c_int, p, p]),
         "b2sr_spmm_bits64": (c_int, [p, p, p, p, c_int, p]),
@@ -263,6 +266,32 @@ def b2sr_export(m: Matrix, stream=None):
     tiles = torch.empty(max(m.n_tiles * m.tile_dim * WORD_BYTES[m.tile_dim], 1), dtype=torch.uint8, device=dev)
     _check(lib.b2sr_export(m.handle, _ptr(trp), _ptr(tci), _ptr(tiles), _stream(stream)))
     return trp, tci[: m.n_tiles], tiles[: m.n_tiles * m.tile_dim * WORD_BYTES[m.tile_dim]]
+
+
+def b2sr_planes_from_csr(m: Matrix, rowptr: torch.Tensor, colind: torch.Tensor, w_csr: torch.Tensor, bits: int,
+                         stream=None) -> torch.Tensor:
+    """Bit-planes of integer weights (uint32 values in an int32 tensor, CSR
+    order): uint8 tensor of n_tiles * bits * tile_bytes bytes."""
+    tb = m.tile_dim * (1 if m.tile_dim <= 8 else m.tile_dim // 8)
+    out = torch.empty(max(m.n_tiles * bits * tb, 4), dtype=torch.uint8, device=w_csr.device)
+    _check(lib.b2sr_planes_from_csr(m.handle, _ptr(rowptr), _ptr(colind), _ptr(w_csr), int(bits), _ptr(out),
+                                    _stream(stream)))
+    return out
+
+
+def b2sr_spmv_planes(m: Matrix, planes: torch.Tensor, bits: int, in_kind: int, x: torch.Tensor, out_kind: int,
+                     y: torch.Tensor, mask: Optional[torch.Tensor] = None, mask_complement: bool = False,
+                     stream=None) -> torch.Tensor:
+    _check(lib.b2sr_spmv_planes(m.handle, _ptr(planes), int(bits), int(in_kind), _ptr(x), int(out_kind), _ptr(y),
+                                _ptr(mask), int(bool(mask_complement)), _stream(stream)))
+    return y
+
+
+def b2sr_transpose(m: Matrix, stream=None) -> Matrix:
+    """B2SR of A^T (CSC order of the tile index, each tile's bits transposed)."""
+    h = ctypes.c_void_p()
+    _check(lib.b2sr_transpose(m.handle, _stream(stream), ctypes.byref(h)))
+    return Matrix(h)
 
 
 def b2sr_lower(m: Matrix, stream=None) -> Matrix:

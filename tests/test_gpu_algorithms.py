@@ -295,3 +295,52 @@ def test_bfs_diropt_switches_direction(B):
     with B.b2sr_from_csr(g.n, rp, ci, 8) as m:
         with pytest.raises(B.B2SRError):
             B.b2sr_bfs_diropt(m, 0, max_iters=10)
+
+
+# ---------------------------------------------------------------------------
+# B2SR of the transpose (Sec. III-A CSR -> CSC of the tile index, Sec. III-B
+# transposed tile packing)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("gi", range(len(GRAPH_IDS)), ids=GRAPH_IDS)
+def test_transpose_arrays_and_vxm(B, k, gi):
+    g = oracle.canonicalize(small_graphs()[gi])
+    gt, _ = transposed(g, np.zeros(g.colind.size, np.float32))
+    rp, ci = csr_dev(g)
+    with B.b2sr_from_csr(g.n, rp, ci, k) as m, B.b2sr_transpose(m) as mt:
+        assert (mt.n, mt.tile_dim, mt.nnz) == (m.n, m.tile_dim, m.nnz)
+        trp, tci, tiles = B.b2sr_export(mt)
+        otrp, otci, otiles = oracle.b2sr(gt, k)
+        assert mt.n_tiles == len(otci)
+        np.testing.assert_array_equal(to_np(trp), otrp)
+        ob = otiles.reshape(-1).view(np.uint8)
+        np.testing.assert_array_equal(to_np(tci)[: len(otci)], otci)
+        np.testing.assert_array_equal(to_np(tiles)[: ob.size], ob)
+        # transposing twice gives the original arrays back
+        with B.b2sr_transpose(mt) as mtt:
+            a, b = B.b2sr_export(mtt), B.b2sr_export(m)
+            nb = ob.size
+            assert torch.equal(a[0], b[0])
+            assert torch.equal(a[1][: m.n_tiles], b[1][: m.n_tiles])
+            assert torch.equal(a[2][:nb], b[2][:nb])
+        # vxm: x^T A = A^T x
+        xb = graphs.random_bits(g.n, 0.3, seed=gi + 2)
+        y = torch.empty(max(B.bitset_words(g.n), 1), dtype=torch.int32, device="cuda")
+        B.b2sr_spmv(mt, B.BOOL_OR_AND, B.VEC_BITS, to_dev(xb), B.VEC_BITS, y)
+        np.testing.assert_array_equal(to_np(y, np.uint32)[: B.bitset_words(g.n)], oracle.spmv_bool(gt, xb))
+        x = (np.random.default_rng(gi).integers(0, 1000, g.n) / 4).astype(np.float32)   # exact sums
+        yf = torch.empty(max(g.n, 1), dtype=torch.float32, device="cuda")
+        B.b2sr_spmv(mt, B.PLUS_TIMES, B.VEC_F32, to_dev(x), B.VEC_F32, yf)
+        np.testing.assert_array_equal(to_np(yf)[: g.n], oracle.spmv_plus(gt, x.astype(np.float64)).astype(np.float32))
+
+
+@pytest.mark.parametrize("k", [4, 8, 32])
+def test_push_drivers_on_device_transpose(B, k):
+    """Directed graphs: the push drivers read A^T made on the device."""
+    g = oracle.canonicalize(graphs.random_directed(700, 0.01, seed=5))
+    rp, ci = csr_dev(g)
+    with B.b2sr_from_csr(g.n, rp, ci, k) as m, B.b2sr_transpose(m) as mt:
+        for s in (0, 17, 350):
+            np.testing.assert_array_equal(to_np(B.b2sr_bfs_diropt(m, s, mt)), oracle.bfs(g, s))
+            np.testing.assert_array_equal(to_np(B.b2sr_sssp_push(mt, s)), oracle.sssp(g, s).astype(np.float32))
