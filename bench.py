@@ -689,6 +689,27 @@ def main():
         t_mis = _timed(lambda: B.b2sr_mis(m, prio, ins), reps=3)
         t_col = _timed(lambda: B.b2sr_color(m, prio, cols, method=B.COLOR_PUSH), reps=3)
         t_col_mt = _timed(lambda: B.b2sr_color(m, prio, cols, method=B.COLOR_MAX_TIMES), reps=1)
+        # B2SR of the transpose (Sec. III-A) and 8-bit weights as bit-planes (Sec. VII)
+        t_tr = _timed(lambda: B.b2sr_transpose(m).close(), reps=3)
+        wq = torch.from_numpy(np.random.default_rng(41).integers(0, 256, g.nnz).astype(np.int32)).to(dev)
+        t_pl = _timed(lambda: B.b2sr_planes_from_csr(m, rp, ci, wq, 8), reps=1)
+        planes = B.b2sr_planes_from_csr(m, rp, ci, wq, 8)
+        yl = torch.empty(g.n, dtype=torch.int64, device=dev)
+        B.b2sr_timing_enable(True)
+        for _ in range(10):
+            B.b2sr_spmv_planes(m, planes, 8, B.VEC_BITS, x, B.VEC_I64, yl)
+            B.b2sr_spmv_planes(m, planes, 8, B.VEC_F32, xf, B.VEC_F32, yf)
+        torch.cuda.synchronize()
+        tpc, npc, bpc = B.b2sr_timing_read("spmv_planes_count")
+        tpp, npp, bpp = B.b2sr_timing_read("spmv_planes_plus")
+        B.b2sr_timing_enable(False)
+        B.b2sr_timing_reset()
+        del planes
+        extra["transpose_and_bit_planes"] = {
+            "tile_dim": TILE, "transpose_ms": t_tr, "weights": "uniform 8-bit integers (seed 41)",
+            "planes_from_csr_ms": t_pl, "planes_count_us": tpc / npc * 1e3,
+            "planes_count_gbs": bpc / npc / (tpc / npc / 1e3) / 1e9, "planes_plus_us": tpp / npp * 1e3,
+            "planes_plus_gbs": bpp / npp / (tpp / npp / 1e3) / 1e9}
         extra["max_times_mis_colouring"] = {
             "tile_dim": TILE, "spmv_max_kernel_us": tm / nm * 1e3, "spmv_max_gbs": bym / nm / (tm / nm / 1e3) / 1e9,
             "priority": "random permutation of 1..n (seed 31)", "mis_ms": t_mis, "mis_size": int(ins.sum().item()),
