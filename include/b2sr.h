@@ -272,7 +272,7 @@ b2sr_status b2sr_planes_from_csr(b2sr_handle h, const int32_t* rowptr, const int
  *   x, y     device; y must not alias x or mask
  *   mask     device bitset or NULL (mask_complement as b2sr_spmv); excluded
  *            outputs are 0
- * A warp per tile-row, a 512-thread block per tile-row of more than 2,048
+ * A warp per tile-row, a 256-thread block per tile-row of more than 256
  * tiles.  B2SR_ERR_INVALID_ARG for other vector kinds or bits outside 1..16. */
 b2sr_status b2sr_spmv_planes(b2sr_handle h, const void* planes, int bits, b2sr_vec in_kind, const void* x,
                              b2sr_vec out_kind, void* y, const uint32_t* mask, int mask_complement,

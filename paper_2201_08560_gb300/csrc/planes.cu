@@ -9,7 +9,7 @@
 //   bits in  -> int64 out:  y_i = sum_J sum_p 2^p popc(P_p,IJ[r] & x_J)   (exact)
 //   fp32 in  -> fp32 out:   y_i = sum_j w_ij x_j, w_ij = sum_p 2^p P_p[i][j]
 // Work: a warp per tile-row (lanes stride over its tiles), or a whole
-// 512-thread block for tile-rows of more than kLongRow tiles (hubs).  Sums
+// 256-thread block for tile-rows of more than kLongRow (256) tiles.  Sums
 // have a fixed order (lane-sequential, then a fixed tree); the fp32 sums are
 // compensated (TwoSum), so their error does not grow with the row's length.
 #include <algorithm>
@@ -22,8 +22,8 @@ namespace b2sr {
 
 namespace {
 
-constexpr int32_t kLongRow = 2048;
-constexpr int kLongThreads = 512;
+constexpr int32_t kLongRow = 256;
+constexpr int kLongThreads = 256;
 
 int grid_for(int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)sm_count() * 8));
@@ -99,6 +99,26 @@ __device__ __forceinline__ bool row_kept(const uint32_t* mask, int comp, int64_t
     return comp ? !b : b;
 }
 
+constexpr int kMaxBits = 16;
+
+// The words of every plane of tile t (planes past `bits` read as zero), with
+// the loads issued together rather than one plane after another.
+template <int TW, int TB>
+__device__ __forceinline__ void load_planes(const uint8_t* __restrict__ planes, int bits, int64_t t,
+                                            uint32_t (&pw)[kMaxBits][TW]) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(planes + t * bits * TB);  // plane p at src + p * TW
+#pragma unroll
+    for (int p = 0; p < kMaxBits; ++p)
+#pragma unroll
+        for (int q = 0; q < TW; ++q) pw[p][q] = 0u;
+#pragma unroll
+    for (int p = 0; p < kMaxBits; ++p) {
+        if (p >= bits) break;
+#pragma unroll
+        for (int q = 0; q < TW; ++q) pw[p][q] = __ldg(src + p * TW + q);
+    }
+}
+
 // The contributions of tile t to the K rows of its tile-row.
 template <int K, bool BITS>
 struct PlaneRows {
@@ -110,6 +130,77 @@ struct PlaneRows {
         for (int r = 0; r < K; ++r) acc[r] = Acc{};
     }
 
+    // k <= 8: a tile's planes held in registers, so that two tiles' loads
+    // can be in flight together (fetch both, then accumulate both)
+    struct Fetched {
+        uint32_t pw[kMaxBits][(tile_bytes_k<K>() + 3) / 4];
+        int32_t J;
+        uint32_t xs;
+    };
+
+    __device__ __forceinline__ void fetch(const uint8_t* __restrict__ planes, int bits, int64_t t, int32_t J,
+                                          const uint32_t* xb, Fetched& f) const {
+        constexpr int TB = tile_bytes_k<K>();
+        constexpr int TW = TB / 4;
+        f.J = J;
+        f.xs = BITS ? seg_bits<K>(xb, J) : 1u;
+        if (f.xs) {
+            load_planes<TW, TB>(planes, bits, t, f.pw);
+        } else {
+#pragma unroll
+            for (int p = 0; p < kMaxBits; ++p)
+#pragma unroll
+                for (int q = 0; q < TW; ++q) f.pw[p][q] = 0u;
+        }
+    }
+
+    __device__ __forceinline__ void accumulate(const Fetched& f, int bits, const float* xf) {
+        if constexpr (BITS) {
+            if (!f.xs) return;
+#pragma unroll
+            for (int p = 0; p < kMaxBits; ++p) {
+                if (p >= bits) break;
+#pragma unroll
+                for (int r = 0; r < K; ++r) acc[r] += (long long)__popc(tile_row<K>(f.pw[p], r) & f.xs) << p;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+                uint32_t rows[kMaxBits];
+                uint32_t any = 0u;
+#pragma unroll
+                for (int p = 0; p < kMaxBits; ++p) {
+                    rows[p] = tile_row<K>(f.pw[p], r);
+                    any |= rows[p];
+                }
+                while (any) {
+                    const int c = __ffs(any) - 1;
+                    any &= any - 1;
+                    uint32_t wv = 0u;
+#pragma unroll
+                    for (int p = 0; p < kMaxBits; ++p) wv |= ((rows[p] >> c) & 1u) << p;
+                    acc[r] = two_sum_add(acc[r], __fmul_rn((float)wv, __ldg(xf + (int64_t)f.J * K + c)));
+                }
+            }
+        }
+    }
+
+    // tiles ta and (if has_b) tb, in that order
+    __device__ __forceinline__ void add_pair(const uint8_t* __restrict__ planes, int bits, int64_t ta, int32_t Ja,
+                                             bool has_b, int64_t tb, int32_t Jb, const uint32_t* xb,
+                                             const float* xf) {
+        if constexpr (K <= 8) {
+            Fetched fa, fb;
+            fetch(planes, bits, ta, Ja, xb, fa);
+            if (has_b) fetch(planes, bits, tb, Jb, xb, fb);
+            accumulate(fa, bits, xf);
+            if (has_b) accumulate(fb, bits, xf);
+        } else {
+            add_tile(planes, bits, ta, Ja, xb, xf);
+            if (has_b) add_tile(planes, bits, tb, Jb, xb, xf);
+        }
+    }
+
     __device__ void add_tile(const uint8_t* __restrict__ planes, int bits, int64_t t, int32_t J, const uint32_t* xb,
                              const float* xf) {
         constexpr int TB = tile_bytes_k<K>();
@@ -117,18 +208,51 @@ struct PlaneRows {
         if constexpr (BITS) {
             const uint32_t xs = seg_bits<K>(xb, J);
             if (!xs) return;
-            for (int p = 0; p < bits; ++p) {
-                const uint32_t* pw = reinterpret_cast<const uint32_t*>(planes + (t * bits + p) * TB);
-                uint32_t wd[TW];
+            if constexpr (K <= 8) {
+                // all planes of the tile loaded at once (independent loads)
+                uint32_t pw[kMaxBits][TW];
+                load_planes<TW, TB>(planes, bits, t, pw);
 #pragma unroll
-                for (int q = 0; q < TW; ++q) wd[q] = __ldg(pw + q);
+                for (int p = 0; p < kMaxBits; ++p) {
+                    if (p >= bits) break;
 #pragma unroll
-                for (int r = 0; r < K; ++r) acc[r] += (long long)__popc(tile_row<K>(wd, r) & xs) << p;
+                    for (int r = 0; r < K; ++r) acc[r] += (long long)__popc(tile_row<K>(pw[p], r) & xs) << p;
+                }
+            } else {
+                for (int p = 0; p < bits; ++p) {
+                    const uint32_t* pw = reinterpret_cast<const uint32_t*>(planes + (t * bits + p) * TB);
+                    uint32_t wd[TW];
+#pragma unroll
+                    for (int q = 0; q < TW; ++q) wd[q] = __ldg(pw + q);
+#pragma unroll
+                    for (int r = 0; r < K; ++r) acc[r] += (long long)__popc(tile_row<K>(wd, r) & xs) << p;
+                }
+            }
+        } else if constexpr (K <= 8) {
+            uint32_t pw[kMaxBits][TW];
+            load_planes<TW, TB>(planes, bits, t, pw);
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+                // row r of every plane: the bits and the integer weight of each column
+                uint32_t rows[kMaxBits];
+                uint32_t any = 0u;
+#pragma unroll
+                for (int p = 0; p < kMaxBits; ++p) {
+                    rows[p] = tile_row<K>(pw[p], r);
+                    any |= rows[p];
+                }
+                while (any) {
+                    const int c = __ffs(any) - 1;
+                    any &= any - 1;
+                    uint32_t wv = 0u;
+#pragma unroll
+                    for (int p = 0; p < kMaxBits; ++p) wv |= ((rows[p] >> c) & 1u) << p;
+                    acc[r] = two_sum_add(acc[r], __fmul_rn((float)wv, __ldg(xf + (int64_t)J * K + c)));
+                }
             }
         } else {
 #pragma unroll
             for (int r = 0; r < K; ++r) {
-                // row r of every plane: the bits and the integer weight of each column
                 uint32_t any = 0u;
                 for (int p = 0; p < bits; ++p) {
                     const uint32_t* pw = reinterpret_cast<const uint32_t*>(planes + (t * bits + p) * TB);
@@ -198,7 +322,10 @@ __global__ void __launch_bounds__(256) planes_rows_kernel(const int32_t* __restr
         if (t1 - t0 > kLongRow) continue;
         PlaneRows<K, BITS> pr;
         pr.zero();
-        for (int32_t t = t0 + lane; t < t1; t += 32) pr.add_tile(planes, bits, t, __ldg(tci + t), xb, xf);
+        for (int32_t t = t0 + lane; t < t1; t += 64) {
+            const bool has_b = t + 32 < t1;
+            pr.add_pair(planes, bits, t, __ldg(tci + t), has_b, t + 32, has_b ? __ldg(tci + t + 32) : 0, xb, xf);
+        }
 #pragma unroll
         for (int r = 0; r < K; ++r) {
             const auto v = warp_sum(pr.acc[r]);
@@ -232,7 +359,11 @@ __global__ void __launch_bounds__(kLongThreads) planes_long_kernel(const int32_t
         const int32_t t0 = __ldg(trp + I), t1 = __ldg(trp + I + 1);
         PlaneRows<K, BITS> pr;
         pr.zero();
-        for (int32_t t = t0 + threadIdx.x; t < t1; t += kLongThreads) pr.add_tile(planes, bits, t, __ldg(tci + t), xb, xf);
+        for (int32_t t = t0 + threadIdx.x; t < t1; t += 2 * kLongThreads) {
+            const bool has_b = t + kLongThreads < t1;
+            pr.add_pair(planes, bits, t, __ldg(tci + t), has_b, t + kLongThreads,
+                        has_b ? __ldg(tci + t + kLongThreads) : 0, xb, xf);
+        }
 #pragma unroll
         for (int r = 0; r < K; ++r) {
             const Acc v = warp_sum(pr.acc[r]);
@@ -322,7 +453,7 @@ extern "C" b2sr_status b2sr_spmv_planes(b2sr_handle h, const void* planes, int b
     return with_tile(h->k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
         const int rows_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(h->ntr, 8), sm_count() * 8));
-        const int long_grid = sm_count() * 2;
+        const int long_grid = sm_count() * 8;
         const uint32_t* xb = static_cast<const uint32_t*>(x);
         const float* xf = static_cast<const float*>(x);
         double bytes = 4.0 * ((double)h->ntr + 1.0) + (double)h->T * (4.0 + (double)bits * tile_bytes(h->k)) +

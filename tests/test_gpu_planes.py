@@ -67,7 +67,7 @@ def test_planes_masked(B, k, masked):
 
 @pytest.mark.parametrize("k", [4, 8])
 def test_planes_hub_rows(B, k):
-    """R-MAT scale 16: tile-rows of more than 2,048 tiles go to the block kernel."""
+    """R-MAT scale 16: tile-rows of more than 256 tiles go to the block kernel."""
     check(B, graphs.rmat(16, 16, seed=9), k, 8, 5)
 
 
