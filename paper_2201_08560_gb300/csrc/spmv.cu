@@ -382,7 +382,11 @@ struct SemPlus4 {
 };
 
 // bmv_bin_full_full over min-plus (relaxation, Sec. V SSSP): float in/out;
-// weights in set-bit order (voff[t] = set bits before tile t), or w = 1
+// weights in set-bit order (voff[t] = set bits before tile t), or w = 1.  The
+// chunk kernels store the minimum over the neighbours; the diagonal's self
+// term min(x_i, .) is applied by spmv_self_kernel once the rows are joined
+// (kept out of the chunk kernels, where its extra load per row cost registers
+// and spills)
 template <int K>
 struct SemMinPlus {
     using V = float;
@@ -390,6 +394,7 @@ struct SemMinPlus {
     using J = float;
     static constexpr int NV = K;
     static constexpr bool kGather = true;
+    static constexpr bool kSelfTerm = true;  // x_i joins y_i in spmv_self_kernel
     static constexpr bool kMayWeight = true;
     const float* x;
     float* y;
@@ -410,7 +415,7 @@ struct SemMinPlus {
     __device__ bool saturated(int64_t, int64_t) const { return false; }
     __device__ void store_row(int32_t R, int r, V v) const {
         int64_t i = (int64_t)R * K + r;
-        if (i < n) y[i] = mask_allows(mask, comp, i) ? fminf(__ldg(x + i), v) : INFINITY;
+        if (i < n) y[i] = mask_allows(mask, comp, i) ? v : INFINITY;
     }
     template <class A>
     __device__ void store(int32_t R, const A& acc) const {
@@ -419,7 +424,8 @@ struct SemMinPlus {
     }
 };
 
-// min over neighbours of int32 labels (min-plus with weight 0: the CC step)
+// min over neighbours of int32 labels (min-plus with weight 0: the CC step);
+// the self term x_i is applied after the join, as for SemMinPlus
 template <int K>
 struct SemMinI32 {
     using V = int32_t;
@@ -427,6 +433,7 @@ struct SemMinI32 {
     using J = int32_t;
     static constexpr int NV = K;
     static constexpr bool kGather = true;
+    static constexpr bool kSelfTerm = true;
     static constexpr bool kMayWeight = false;
     static constexpr bool weighted = false;
     const int32_t* x;
@@ -445,7 +452,7 @@ struct SemMinI32 {
     __device__ bool saturated(int64_t, int64_t) const { return false; }
     __device__ void store_row(int32_t R, int r, V v) const {
         int64_t i = (int64_t)R * K + r;
-        if (i < n) y[i] = mask_allows(mask, comp, i) ? min(__ldg(x + i), v) : INT_MAX;
+        if (i < n) y[i] = mask_allows(mask, comp, i) ? v : INT_MAX;
     }
     template <class A>
     __device__ void store(int32_t R, const A& acc) const {
@@ -1248,6 +1255,26 @@ __global__ void spmv_edges_kernel(SEM sem, int32_t lead_end, int32_t trail_begin
     for (int64_t R = trail_begin + tid; R < ntr; R += stride) sem.store((int32_t)R, idv);
 }
 
+// semirings whose result includes the diagonal's self term (min-plus)
+template <class S, class = void>
+struct HasSelfTerm : std::false_type {};
+template <class S>
+struct HasSelfTerm<S, std::void_t<decltype(S::kSelfTerm)>> : std::bool_constant<S::kSelfTerm> {};
+
+template <class T>
+__device__ __forceinline__ T min_self(T a, T b) {
+    if constexpr (std::is_same<T, float>::value) return fminf(a, b);
+    else return min(a, b);
+}
+
+// y_i = min(x_i, y_i) on the rows the mask keeps (the min-plus self term)
+template <class SEM>
+__global__ void spmv_self_kernel(SEM sem, const int32_t* gate) {
+    if (gated_off(gate)) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sem.n; i += (int64_t)gridDim.x * blockDim.x)
+        if (mask_allows(sem.mask, sem.comp, i)) sem.y[i] = min_self(sem.y[i], __ldg(sem.x + i));
+}
+
 __global__ void clear_words_kernel(uint32_t* w, int64_t count, const int32_t* gate) {
     if (gated_off(gate)) return;
     for (int64_t i = threadIdx.x; i < count; i += blockDim.x) w[i] = 0u;
@@ -1301,14 +1328,11 @@ static double spmv_bytes(const b2sr_matrix* h, double vec_bytes) {
     return 4.0 * ((double)h->ntr + 1.0) + (double)h->T * (4.0 + tile_bytes(h->k)) + vec_bytes;
 }
 
+// the chunk kernel (staged or direct) and the cross-chunk join
 template <int K, class SEM>
-static b2sr_status run_spmv(const b2sr_matrix* h, const SEM& sem, uint32_t* bits_out, cudaStream_t s,
-                            const char* family, double vec_bytes, const int32_t* gate) {
+static b2sr_status run_chunks(const b2sr_matrix* h, const SEM& sem, cudaStream_t s, const char* family,
+                              double vec_bytes, const int32_t* gate, const SpmvGeom& g) {
     using V = typename SEM::V;
-    SpmvGeom g{h->rowptr, h->colind, h->tiles, h->chunk_row, h->T, h->nchunks, h->ntr, gate};
-    if (bits_out) B2SR_TRY(clear_bitset_tail<K>(h, bits_out, s, gate));
-    B2SR_TRY((launch_edges<K, SEM>(h, sem, s, gate)));
-    if (h->nchunks == 0) return B2SR_OK;
     DevBuf pbuf(s);
     Partials<V> part;
     B2SR_TRY((alloc_partials<V, SEM::NV>(pbuf, h->nchunks, &part)));
@@ -1332,6 +1356,22 @@ static b2sr_status run_spmv(const b2sr_matrix* h, const SEM& sem, uint32_t* bits
     }
     return launch_fixup<K, SEM>(h, sem, part, s, gate);
 }
+
+template <int K, class SEM>
+static b2sr_status run_spmv(const b2sr_matrix* h, const SEM& sem, uint32_t* bits_out, cudaStream_t s,
+                            const char* family, double vec_bytes, const int32_t* gate) {
+    SpmvGeom g{h->rowptr, h->colind, h->tiles, h->chunk_row, h->T, h->nchunks, h->ntr, gate};
+    if (bits_out) B2SR_TRY(clear_bitset_tail<K>(h, bits_out, s, gate));
+    B2SR_TRY((launch_edges<K, SEM>(h, sem, s, gate)));
+    if (h->nchunks > 0) B2SR_TRY((run_chunks<K, SEM>(h, sem, s, family, vec_bytes, gate, g)));
+    if constexpr (HasSelfTerm<SEM>::value) {
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(h->n, 256), (int64_t)sm_count() * 8));
+        spmv_self_kernel<SEM><<<grid, 256, 0, s>>>(sem, gate);
+        B2SR_LAUNCH_CHECK("spmv_self_kernel");
+    }
+    return B2SR_OK;
+}
+
 
 template <class F>
 static b2sr_status with_k(int k, F&& f) {
