@@ -887,7 +887,17 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
                             b &= b - 1;
                             const int r = q * (32 / S::ROW_BITS) + bit / S::ROW_BITS;
                             const float wv = sem.weighted ? __ldg(wt + qb) : 1.0f;
-                            acc.set(r, sem.apply(acc.get(r), __ldg(xt + bit % S::ROW_BITS), wv));
+                            const G xv = __ldg(xt + bit % S::ROW_BITS);
+                            if constexpr (sizeof(V) == 8 && NV <= 8) {
+                                // 8-byte accumulators: a predicated update of
+                                // each row keeps the indices constant (a
+                                // runtime index puts the array in local memory)
+#pragma unroll
+                                for (int v = 0; v < NV; ++v)
+                                    if (v == r) acc.set(v, sem.apply(acc.get(v), xv, wv));
+                            } else {
+                                acc.set(r, sem.apply(acc.get(r), xv, wv));
+                            }
                             ++qb;
                         }
                     }
