@@ -238,6 +238,78 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint64_t* __
     }
 }
 
+// Keys only: the same ranking, then the block's keys are placed in shared
+// memory in output order (digit by digit) and written out by consecutive
+// threads, so each digit's run goes to global memory in whole sectors.
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_staged(const uint64_t* __restrict__ keys, int64_t N,
+                                                                     int shift, int64_t nb,
+                                                                     const int64_t* __restrict__ offsets,
+                                                                     uint64_t* __restrict__ keys_out) {
+    __shared__ uint32_t cnt[kSortWarps][257];
+    __shared__ uint32_t dstart[256];  // block-local start of each digit's run
+    __shared__ uint32_t wsum[kSortWarps];
+    __shared__ uint64_t stage[kSortTile];
+    const int w = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    for (int d = lane; d < 257; d += 32) cnt[w][d] = 0;
+    __syncwarp();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)w * 32 * kSortItems;
+    uint64_t key[kSortItems];
+    uint32_t rank[kSortItems];
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const int64_t i = base + j * 32 + lane;
+        const bool valid = i < N;
+        key[j] = valid ? keys[i] : 0;
+        const unsigned d = valid ? (unsigned)((key[j] >> shift) & 0xFFu) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = cnt[w][d];
+        rank[j] = before + __popc(peers & lt);
+        __syncwarp();
+        if (lane == 31u - __clz(peers)) cnt[w][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps; the digit's block total
+    const int d = threadIdx.x;  // 256 threads, 256 digits
+    uint32_t total = 0;
+    for (int ww = 0; ww < kSortWarps; ++ww) {
+        const uint32_t t = cnt[ww][d];
+        cnt[ww][d] = total;
+        total += t;
+    }
+    // exclusive scan of the totals over the digits (warp scans, then warp sums)
+    uint32_t inc = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+        if ((int)lane >= o) inc += v;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    uint32_t before_w = 0;
+    for (int ww = 0; ww < w; ++ww) before_w += wsum[ww];
+    dstart[d] = before_w + inc - total;
+    __syncthreads();
+    uint32_t nvalid = 0;
+    for (int ww = 0; ww < kSortWarps; ++ww) nvalid += wsum[ww];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const int64_t i = base + j * 32 + lane;
+        if (i < N) {
+            const unsigned dd = (unsigned)((key[j] >> shift) & 0xFFu);
+            stage[dstart[dd] + cnt[w][dd] + rank[j]] = key[j];
+        }
+    }
+    __syncthreads();
+    for (uint32_t p = threadIdx.x; p < nvalid; p += kSortThreads) {
+        const uint64_t k = stage[p];
+        const unsigned dd = (unsigned)((k >> shift) & 0xFFu);
+        keys_out[offsets[(int64_t)dd * nb + blockIdx.x] + (p - dstart[dd])] = k;
+    }
+}
+
 template <bool PAIRS>
 static b2sr_status radix_sort_impl(uint64_t* keys, uint64_t* ktmp, uint32_t* vals, uint32_t* vtmp,
                                    int64_t N, int lo_bit, int hi_bit, cudaStream_t s,
@@ -257,9 +329,14 @@ static b2sr_status radix_sort_impl(uint64_t* keys, uint64_t* ktmp, uint32_t* val
         radix_hist<<<(unsigned)nb, kSortThreads, 0, s>>>(kin, N, shift, nb, counts.as<int64_t>());
         B2SR_LAUNCH_CHECK("radix_hist");
         B2SR_TRY(exclusive_scan_i64(counts.as<int64_t>(), offs.as<int64_t>(), 256 * nb, s));
-        radix_scatter<PAIRS><<<(unsigned)nb, kSortThreads, 0, s>>>(kin, vin, N, shift, nb,
-                                                                   offs.as<int64_t>(), kout, vout);
-        B2SR_LAUNCH_CHECK("radix_scatter");
+        if (PAIRS) {
+            radix_scatter<PAIRS><<<(unsigned)nb, kSortThreads, 0, s>>>(kin, vin, N, shift, nb,
+                                                                       offs.as<int64_t>(), kout, vout);
+            B2SR_LAUNCH_CHECK("radix_scatter");
+        } else {
+            radix_scatter_staged<<<(unsigned)nb, kSortThreads, 0, s>>>(kin, N, shift, nb, offs.as<int64_t>(), kout);
+            B2SR_LAUNCH_CHECK("radix_scatter_staged");
+        }
         uint64_t* t = kin; kin = kout; kout = t;
         uint32_t* tv = vin; vin = vout; vout = tv;
     }
