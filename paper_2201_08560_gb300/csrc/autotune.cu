@@ -23,12 +23,6 @@ b2sr_status spmm64_dispatch(b2sr_matrix* h, const uint64_t* X, uint64_t* Y, cons
 
 static const int kTileDims[4] = {4, 8, 16, 32};
 
-static int bits_for_u(int64_t v) {  // bits to hold values in [0, v)
-    int b = 1;
-    while (b < 62 && (int64_t(1) << b) < v) ++b;
-    return b;
-}
-
 // segment g = q * ns + s: rows [r0, r1) of the tile-row of sample s at k = 4 << q
 __device__ __forceinline__ void seg_rows(int64_t g, int64_t ns, const int32_t* __restrict__ sample, int32_t n,
                                          int32_t* r0, int32_t* r1, int* k) {
@@ -96,10 +90,6 @@ __global__ void profile_heads_kernel(const uint64_t* __restrict__ keys, int64_t 
     if (threadIdx.x < 4 && c[threadIdx.x]) atomicAdd(cnt + threadIdx.x, c[threadIdx.x]);
 }
 
-static int grid_for(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)sm_count() * 8));
-}
-
 b2sr_status sample_profile(int32_t n, const int32_t* rowptr, const int32_t* colind, int64_t nnz,
                            const int32_t* sample_host, int64_t ns, double* est, double* tiles_est, cudaStream_t s) {
     int64_t cnt_host[4] = {0, 0, 0, 0};
@@ -137,7 +127,7 @@ b2sr_status sample_profile(int32_t n, const int32_t* rowptr, const int32_t* coli
             profile_keys_kernel<<<grid_for(G * 32), 256, 0, s>>>(rowptr, colind, dsample, ns, n, len, off, keys);
             B2SR_LAUNCH_CHECK("profile_keys_kernel");
             uint64_t* sorted = nullptr;
-            B2SR_TRY(radix_sort_u64(keys, keys + N, N, 0, 31 + bits_for_u(G), s, &sorted));
+            B2SR_TRY(radix_sort_u64(keys, keys + N, N, 0, 31 + bits_for(G), s, &sorted));
             profile_heads_kernel<<<grid_for(N), 256, 0, s>>>(sorted, N, ns, cnt);
             B2SR_LAUNCH_CHECK("profile_heads_kernel");
         }

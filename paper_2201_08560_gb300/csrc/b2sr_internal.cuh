@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
+#include <type_traits>
 
 #include "b2sr.h"
 
@@ -97,6 +99,32 @@ struct DevBuf {
 };
 
 int sm_count();
+
+// Blocks of 256 threads for a grid-stride loop over n items, at most
+// blocks_per_sm per SM (and at least one block).
+inline int grid_for(int64_t n, int blocks_per_sm = 8) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)sm_count() * blocks_per_sm));
+}
+inline int grid_wide(int64_t n) { return grid_for(n, 16); }
+
+// Bits needed to hold the values [0, v).
+inline int bits_for(int64_t v) {
+    int b = 1;
+    while (b < 62 && ((int64_t)1 << b) < v) ++b;
+    return b;
+}
+
+// Calls f(std::integral_constant<int, k>) for a supported tile_dim k.
+template <class F>
+b2sr_status with_tile(int k, F&& f) {
+    switch (k) {
+        case 4: return f(std::integral_constant<int, 4>());
+        case 8: return f(std::integral_constant<int, 8>());
+        case 16: return f(std::integral_constant<int, 16>());
+        case 32: return f(std::integral_constant<int, 32>());
+        default: return fail(B2SR_ERR_UNSUPPORTED_TILE, "tile_dim must be 4, 8, 16 or 32");
+    }
+}
 
 }  // namespace b2sr
 

@@ -30,10 +30,6 @@ namespace {
 constexpr int64_t kAlpha = 14;  // Beamer et al.'s switching constants
 constexpr int64_t kBeta = 24;
 
-int grid_for(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)sm_count() * 8));
-}
-
 // ctl layout (int64 words)
 enum : int {
     C_ACTIVE = 0,  // 1 while the search goes on
@@ -214,17 +210,6 @@ __global__ void dirop_init_kernel(int32_t* levels, int32_t n, int64_t words, uin
                 ctl[C_NLONG] = 1;
             }
         }
-    }
-}
-
-template <class F>
-b2sr_status with_tile(int k, F&& f) {
-    switch (k) {
-        case 4: return f(std::integral_constant<int, 4>());
-        case 8: return f(std::integral_constant<int, 8>());
-        case 16: return f(std::integral_constant<int, 16>());
-        case 32: return f(std::integral_constant<int, 32>());
-        default: return fail(B2SR_ERR_UNSUPPORTED_TILE, "bad tile_dim");
     }
 }
 

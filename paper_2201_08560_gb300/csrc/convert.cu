@@ -240,12 +240,6 @@ b2sr_status new_handle_from_tiles(int32_t n, int k, int64_t T, int32_t* rowptr, 
     return B2SR_OK;
 }
 
-static int bits_for(int64_t v) {  // bits to hold values in [0, v)
-    int b = 1;
-    while ((int64_t(1) << b) < v) ++b;
-    return b;
-}
-
 // ---------------------------------------------------------------------------
 // set-bit offsets and column counts (cached on the handle)
 // ---------------------------------------------------------------------------
@@ -301,21 +295,6 @@ __global__ void col_count_kernel(const int32_t* __restrict__ colind, const uint8
     }
 }
 
-template <class F>
-static b2sr_status dispatch_k(int k, F&& f) {
-    switch (k) {
-        case 4: return f(std::integral_constant<int, 4>());
-        case 8: return f(std::integral_constant<int, 8>());
-        case 16: return f(std::integral_constant<int, 16>());
-        case 32: return f(std::integral_constant<int, 32>());
-        default: return fail(B2SR_ERR_UNSUPPORTED_TILE, "tile_dim must be 4, 8, 16 or 32");
-    }
-}
-
-static int grid_for(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)sm_count() * 16));
-}
-
 b2sr_status ensure_voff(b2sr_matrix* h, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(*static_cast<std::mutex*>(h->mtx));
     if (h->voff) return B2SR_OK;
@@ -325,9 +304,9 @@ b2sr_status ensure_voff(b2sr_matrix* h, cudaStream_t s) {
     b2sr_status st = cnt.alloc((h->T + 1) * sizeof(int32_t));
     if (st == B2SR_OK) st = scan.alloc((h->T + 1) * sizeof(int64_t));
     if (st == B2SR_OK) {
-        st = dispatch_k(h->k, [&](auto kc) -> b2sr_status {
+        st = with_tile(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
-            if (h->T > 0) tile_popc_kernel<K><<<grid_for(h->T), 256, 0, s>>>(h->tiles, h->T, cnt.as<int32_t>());
+            if (h->T > 0) tile_popc_kernel<K><<<grid_wide(h->T), 256, 0, s>>>(h->tiles, h->T, cnt.as<int32_t>());
             B2SR_LAUNCH_CHECK("tile_popc_kernel");
             return B2SR_OK;
         });
@@ -337,7 +316,7 @@ b2sr_status ensure_voff(b2sr_matrix* h, cudaStream_t s) {
         st = exclusive_scan_i32_to_i64(cnt.as<int32_t>(), scan.as<int64_t>(), h->T + 1, s);
     }
     if (st == B2SR_OK) {
-        i64_to_i32_kernel<<<grid_for(h->T + 1), 256, 0, s>>>(scan.as<int64_t>(), h->T + 1, voff);
+        i64_to_i32_kernel<<<grid_wide(h->T + 1), 256, 0, s>>>(scan.as<int64_t>(), h->T + 1, voff);
         note_launch();
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -358,9 +337,9 @@ b2sr_status ensure_outdeg(b2sr_matrix* h, cudaStream_t s) {
     B2SR_TRY(dalloc(&deg, (size_t)h->ntr * h->k, s));
     cudaError_t e = cudaMemsetAsync(deg, 0, (size_t)h->ntr * h->k * sizeof(int32_t), s);
     if (e != cudaSuccess) { dfree(deg, s); return cuda_fail(e, "memset outdeg"); }
-    b2sr_status st = dispatch_k(h->k, [&](auto kc) -> b2sr_status {
+    b2sr_status st = with_tile(h->k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
-        if (h->T > 0) col_count_kernel<K><<<grid_for(h->T), 256, 0, s>>>(h->colind, h->tiles, h->T, h->n, deg);
+        if (h->T > 0) col_count_kernel<K><<<grid_wide(h->T), 256, 0, s>>>(h->colind, h->tiles, h->T, h->n, deg);
         B2SR_LAUNCH_CHECK("col_count_kernel");
         return B2SR_OK;
     });
@@ -531,7 +510,7 @@ extern "C" b2sr_status b2sr_from_csr(int32_t n, const int32_t* rowptr, const int
         DevBuf bad(s);
         B2SR_TRY(bad.alloc(sizeof(int)));
         B2SR_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
-        validate_csr_kernel<<<grid_for(std::max<int64_t>(n, nnz)), 256, 0, s>>>(n, rowptr, colind, nnz, bad.as<int>());
+        validate_csr_kernel<<<grid_wide(std::max<int64_t>(n, nnz)), 256, 0, s>>>(n, rowptr, colind, nnz, bad.as<int>());
         B2SR_LAUNCH_CHECK("validate_csr_kernel");
         int hbad = 0;
         B2SR_CUDA_TRY(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -552,7 +531,7 @@ extern "C" b2sr_status b2sr_from_csr(int32_t n, const int32_t* rowptr, const int
         B2SR_TRY(radix_sort_u64(keys.as<uint64_t>(), ktmp.as<uint64_t>(), nnz, 10, 10 + 2 * sbits, s, &sorted));
         B2SR_TRY(flag.alloc(nnz * sizeof(int32_t)));
         B2SR_TRY(tidx.alloc(nnz * sizeof(int64_t)));
-        mark_heads_kernel<<<grid_for(nnz), 256, 0, s>>>(sorted, nnz, flag.as<int32_t>());
+        mark_heads_kernel<<<grid_wide(nnz), 256, 0, s>>>(sorted, nnz, flag.as<int32_t>());
         B2SR_LAUNCH_CHECK("mark_heads_kernel");
         B2SR_TRY(exclusive_scan_i32_to_i64(flag.as<int32_t>(), tidx.as<int64_t>(), nnz, s));
         int64_t last = 0;
@@ -584,14 +563,14 @@ extern "C" b2sr_status b2sr_from_csr(int32_t n, const int32_t* rowptr, const int
         st = tilerow.alloc(std::max<int64_t>(T, 1) * sizeof(int32_t));
         if (st != B2SR_OK) return release(st);
         if (nnz > 0) {
-            fill_tiles_kernel<<<grid_for(nnz), 256, 0, s>>>(sorted, flag.as<int32_t>(), tidx.as<int64_t>(), nnz, k,
+            fill_tiles_kernel<<<grid_wide(nnz), 256, 0, s>>>(sorted, flag.as<int32_t>(), tidx.as<int64_t>(), nnz, k,
                                                             sbits, o_colind, tilerow.as<int32_t>(),
                                                             reinterpret_cast<uint32_t*>(o_tiles));
             note_launch();
             e = cudaGetLastError();
             if (e != cudaSuccess) return release(cuda_fail(e, "fill_tiles_kernel"));
         }
-        build_rowptr_kernel<<<grid_for(T + 1), 256, 0, s>>>(tilerow.as<int32_t>(), T, ntr, o_rowptr);
+        build_rowptr_kernel<<<grid_wide(T + 1), 256, 0, s>>>(tilerow.as<int32_t>(), T, ntr, o_rowptr);
         note_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return release(cuda_fail(e, "build_rowptr_kernel"));
@@ -614,12 +593,12 @@ extern "C" b2sr_status b2sr_to_csr(b2sr_handle h, int32_t* rowptr, int32_t* coli
     B2SR_TRY(cnt.alloc(((size_t)n + 1) * sizeof(int32_t)));
     B2SR_TRY(off.alloc(((size_t)n + 1) * sizeof(int64_t)));
     B2SR_CUDA_TRY(cudaMemsetAsync(cnt.as<int32_t>() + n, 0, sizeof(int32_t), s));
-    B2SR_TRY(dispatch_k(h->k, [&](auto kc) -> b2sr_status {
+    B2SR_TRY(with_tile(h->k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
-        if (n > 0) row_nnz_kernel<K><<<grid_for(n), 256, 0, s>>>(h->rowptr, h->tiles, n, cnt.as<int32_t>());
+        if (n > 0) row_nnz_kernel<K><<<grid_wide(n), 256, 0, s>>>(h->rowptr, h->tiles, n, cnt.as<int32_t>());
         B2SR_LAUNCH_CHECK("row_nnz_kernel");
         B2SR_TRY(exclusive_scan_i32_to_i64(cnt.as<int32_t>(), off.as<int64_t>(), (int64_t)n + 1, s));
-        row_fill_kernel<K><<<grid_for((int64_t)n + 1), 256, 0, s>>>(h->rowptr, h->colind, h->tiles, n,
+        row_fill_kernel<K><<<grid_wide((int64_t)n + 1), 256, 0, s>>>(h->rowptr, h->colind, h->tiles, n,
                                                                    off.as<int64_t>(), rowptr, colind);
         B2SR_LAUNCH_CHECK("row_fill_kernel");
         return B2SR_OK;
@@ -644,9 +623,9 @@ extern "C" b2sr_status b2sr_lower(b2sr_handle h, void* stream, b2sr_handle* out)
     B2SR_TRY(off.alloc(((size_t)ntr + 1) * sizeof(int64_t)));
     B2SR_CUDA_TRY(cudaMemsetAsync(cnt.as<int32_t>() + ntr, 0, sizeof(int32_t), s));
     int64_t T = 0;
-    B2SR_TRY(dispatch_k(k, [&](auto kc) -> b2sr_status {
+    B2SR_TRY(with_tile(k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
-        if (ntr > 0) lower_count_kernel<K><<<grid_for(ntr), 256, 0, s>>>(h->rowptr, h->colind, h->tiles, ntr, cnt.as<int32_t>());
+        if (ntr > 0) lower_count_kernel<K><<<grid_wide(ntr), 256, 0, s>>>(h->rowptr, h->colind, h->tiles, ntr, cnt.as<int32_t>());
         B2SR_LAUNCH_CHECK("lower_count_kernel");
         return B2SR_OK;
     }));
@@ -668,9 +647,9 @@ extern "C" b2sr_status b2sr_lower(b2sr_handle h, void* stream, b2sr_handle* out)
     cudaError_t e = cudaMemsetAsync(lci, 0, (size_t)cap * sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(lt, 0, (size_t)cap * tile_bytes(k), s);
     if (e != cudaSuccess) return release(cuda_fail(e, "memset lower"));
-    st = dispatch_k(k, [&](auto kc) -> b2sr_status {
+    st = with_tile(k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
-        lower_fill_kernel<K><<<grid_for((int64_t)ntr + 1), 256, 0, s>>>(h->rowptr, h->colind, h->tiles, ntr,
+        lower_fill_kernel<K><<<grid_wide((int64_t)ntr + 1), 256, 0, s>>>(h->rowptr, h->colind, h->tiles, ntr,
                                                                        off.as<int64_t>(), lrp, lci, lt);
         B2SR_LAUNCH_CHECK("lower_fill_kernel");
         return B2SR_OK;
@@ -693,9 +672,9 @@ extern "C" b2sr_status b2sr_weights_from_csr(b2sr_handle h, const int32_t* rowpt
     DevBuf bad(s);
     B2SR_TRY(bad.alloc(sizeof(int)));
     B2SR_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
-    B2SR_TRY(dispatch_k(h->k, [&](auto kc) -> b2sr_status {
+    B2SR_TRY(with_tile(h->k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
-        weights_kernel<K><<<grid_for(h->nnz), 256, 0, s>>>(h->n, rowptr, colind, w_csr, h->nnz, h->rowptr,
+        weights_kernel<K><<<grid_wide(h->nnz), 256, 0, s>>>(h->n, rowptr, colind, w_csr, h->nnz, h->rowptr,
                                                            h->colind, h->tiles, h->voff, w_bits, bad.as<int>());
         B2SR_LAUNCH_CHECK("weights_kernel");
         return B2SR_OK;

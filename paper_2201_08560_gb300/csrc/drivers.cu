@@ -26,10 +26,6 @@ b2sr_status spmm64_dispatch(b2sr_matrix* h, const uint64_t* X, uint64_t* Y, cons
 b2sr_status masked_count(const b2sr_matrix* A, const b2sr_matrix* B, const b2sr_matrix* M, int64_t* count,
                          cudaStream_t s);
 
-static int grid_for(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)sm_count() * 8));
-}
-
 // active <- found (only while active); level counter advances with it
 __global__ void advance_kernel(int32_t* active, const int32_t* found, int32_t* level) {
     if (threadIdx.x == 0 && blockIdx.x == 0 && *active) {

@@ -44,10 +44,6 @@ b2sr_status spmv_maxkey_dispatch(b2sr_matrix* h, const uint64_t* x, uint64_t* y,
 
 namespace {
 
-int grid_for(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)sm_count() * 8));
-}
-
 __device__ __forceinline__ uint64_t priority_key(float p, int32_t v) {
     uint32_t b = __float_as_uint(p);
     if ((b & 0x7FFFFFFFu) == 0u) b = 0u;                        // -0 orders as +0
@@ -377,17 +373,6 @@ static b2sr_status color_rounds(b2sr_matrix* h, const float* prio, int32_t* colo
                             return B2SR_OK;
                         },
                         &rounds);
-}
-
-template <class F>
-static b2sr_status with_tile(int k, F&& f) {
-    switch (k) {
-        case 4: return f(std::integral_constant<int, 4>());
-        case 8: return f(std::integral_constant<int, 8>());
-        case 16: return f(std::integral_constant<int, 16>());
-        case 32: return f(std::integral_constant<int, 32>());
-        default: return fail(B2SR_ERR_UNSUPPORTED_TILE, "bad tile_dim");
-    }
 }
 
 static b2sr_status color_push(b2sr_matrix* h, const float* prio, int32_t* colors, int max_iters, cudaStream_t s) {

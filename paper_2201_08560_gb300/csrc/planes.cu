@@ -25,10 +25,6 @@ namespace {
 constexpr int32_t kLongRow = 256;
 constexpr int kLongThreads = 256;
 
-int grid_for(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)sm_count() * 8));
-}
-
 template <int K>
 constexpr int tile_bytes_k() { return K * (K <= 8 ? 1 : K / 8); }
 
@@ -178,7 +174,10 @@ struct PlaneRows {
                     any &= any - 1;
                     uint32_t wv = 0u;
 #pragma unroll
-                    for (int p = 0; p < kMaxBits; ++p) wv |= ((rows[p] >> c) & 1u) << p;
+                    for (int p = 0; p < kMaxBits; ++p) {
+                        if (p >= bits) break;
+                        wv |= ((rows[p] >> c) & 1u) << p;
+                    }
                     acc[r] = two_sum_add(acc[r], __fmul_rn((float)wv, __ldg(xf + (int64_t)f.J * K + c)));
                 }
             }
@@ -201,6 +200,8 @@ struct PlaneRows {
         }
     }
 
+    // k >= 16: plane by plane from global memory (a tile's planes are too
+    // many registers to hold at once)
     __device__ void add_tile(const uint8_t* __restrict__ planes, int bits, int64_t t, int32_t J, const uint32_t* xb,
                              const float* xf) {
         constexpr int TB = tile_bytes_k<K>();
@@ -208,47 +209,13 @@ struct PlaneRows {
         if constexpr (BITS) {
             const uint32_t xs = seg_bits<K>(xb, J);
             if (!xs) return;
-            if constexpr (K <= 8) {
-                // all planes of the tile loaded at once (independent loads)
-                uint32_t pw[kMaxBits][TW];
-                load_planes<TW, TB>(planes, bits, t, pw);
+            for (int p = 0; p < bits; ++p) {
+                const uint32_t* pw = reinterpret_cast<const uint32_t*>(planes + (t * bits + p) * TB);
+                uint32_t wd[TW];
 #pragma unroll
-                for (int p = 0; p < kMaxBits; ++p) {
-                    if (p >= bits) break;
+                for (int q = 0; q < TW; ++q) wd[q] = __ldg(pw + q);
 #pragma unroll
-                    for (int r = 0; r < K; ++r) acc[r] += (long long)__popc(tile_row<K>(pw[p], r) & xs) << p;
-                }
-            } else {
-                for (int p = 0; p < bits; ++p) {
-                    const uint32_t* pw = reinterpret_cast<const uint32_t*>(planes + (t * bits + p) * TB);
-                    uint32_t wd[TW];
-#pragma unroll
-                    for (int q = 0; q < TW; ++q) wd[q] = __ldg(pw + q);
-#pragma unroll
-                    for (int r = 0; r < K; ++r) acc[r] += (long long)__popc(tile_row<K>(wd, r) & xs) << p;
-                }
-            }
-        } else if constexpr (K <= 8) {
-            uint32_t pw[kMaxBits][TW];
-            load_planes<TW, TB>(planes, bits, t, pw);
-#pragma unroll
-            for (int r = 0; r < K; ++r) {
-                // row r of every plane: the bits and the integer weight of each column
-                uint32_t rows[kMaxBits];
-                uint32_t any = 0u;
-#pragma unroll
-                for (int p = 0; p < kMaxBits; ++p) {
-                    rows[p] = tile_row<K>(pw[p], r);
-                    any |= rows[p];
-                }
-                while (any) {
-                    const int c = __ffs(any) - 1;
-                    any &= any - 1;
-                    uint32_t wv = 0u;
-#pragma unroll
-                    for (int p = 0; p < kMaxBits; ++p) wv |= ((rows[p] >> c) & 1u) << p;
-                    acc[r] = two_sum_add(acc[r], __fmul_rn((float)wv, __ldg(xf + (int64_t)J * K + c)));
-                }
+                for (int r = 0; r < K; ++r) acc[r] += (long long)__popc(tile_row<K>(wd, r) & xs) << p;
             }
         } else {
 #pragma unroll
@@ -378,17 +345,6 @@ __global__ void __launch_bounds__(kLongThreads) planes_long_kernel(const int32_t
             if (i < n) store_y<BITS>(y, i, v, row_kept(mask, comp, i));
         }
         __syncthreads();
-    }
-}
-
-template <class F>
-b2sr_status with_tile(int k, F&& f) {
-    switch (k) {
-        case 4: return f(std::integral_constant<int, 4>());
-        case 8: return f(std::integral_constant<int, 8>());
-        case 16: return f(std::integral_constant<int, 16>());
-        case 32: return f(std::integral_constant<int, 32>());
-        default: return fail(B2SR_ERR_UNSUPPORTED_TILE, "bad tile_dim");
     }
 }
 

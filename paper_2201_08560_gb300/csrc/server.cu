@@ -46,10 +46,6 @@ b2sr_status spmm4_dispatch(b2sr_matrix* h, const float* X, float* Y, const uint3
 
 using Clock = std::chrono::steady_clock;
 
-static int grid_for(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)sm_count() * 8));
-}
-
 // ---------------------------------------------------------------------------
 // device side
 // ---------------------------------------------------------------------------

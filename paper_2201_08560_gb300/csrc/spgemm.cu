@@ -195,28 +195,13 @@ __global__ void build_rowptr_from_rows(const int32_t* __restrict__ tilerow, int6
     }
 }
 
-static int grid_for(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)sm_count() * 16));
-}
-
-template <class F>
-static b2sr_status with_k(int k, F&& f) {
-    switch (k) {
-        case 4: return f(std::integral_constant<int, 4>());
-        case 8: return f(std::integral_constant<int, 8>());
-        case 16: return f(std::integral_constant<int, 16>());
-        case 32: return f(std::integral_constant<int, 32>());
-        default: return fail(B2SR_ERR_UNSUPPORTED_TILE, "bad tile_dim");
-    }
-}
-
 static MatView view(const b2sr_matrix* h) { return MatView{h->rowptr, h->colind, h->tiles, h->T, h->ntr}; }
 
 b2sr_status masked_count(const b2sr_matrix* A, const b2sr_matrix* B, const b2sr_matrix* M, int64_t* count,
                          cudaStream_t s) {
     B2SR_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int64_t), s));
     if (M->T == 0) return B2SR_OK;
-    return with_k(A->k, [&](auto kc) -> b2sr_status {
+    return with_tile(A->k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
         int64_t warps = M->T;
         int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(warps * 32, 256), (int64_t)sm_count() * 16));
@@ -225,12 +210,6 @@ b2sr_status masked_count(const b2sr_matrix* A, const b2sr_matrix* B, const b2sr_
         B2SR_LAUNCH_CHECK("masked_count_kernel");
         return B2SR_OK;
     });
-}
-
-static int bits_for(int64_t v) {
-    int b = 1;
-    while ((int64_t(1) << b) < v) ++b;
-    return b;
 }
 
 b2sr_status spgemm_bool(const b2sr_matrix* A, const b2sr_matrix* B, cudaStream_t s, b2sr_matrix** out) {
@@ -243,9 +222,9 @@ b2sr_status spgemm_bool(const b2sr_matrix* A, const b2sr_matrix* B, cudaStream_t
         B2SR_TRY(a_tilerow.alloc(A->T * sizeof(int32_t)));
         B2SR_TRY(cnt.alloc((A->T + 1) * sizeof(int32_t)));
         B2SR_TRY(off.alloc((A->T + 1) * sizeof(int64_t)));
-        row_of_tiles_kernel<<<grid_for(ntr), 256, 0, s>>>(A->rowptr, ntr, A->T, a_tilerow.as<int32_t>());
+        row_of_tiles_kernel<<<grid_wide(ntr), 256, 0, s>>>(A->rowptr, ntr, A->T, a_tilerow.as<int32_t>());
         B2SR_LAUNCH_CHECK("row_of_tiles_kernel");
-        product_counts_kernel<<<grid_for(A->T), 256, 0, s>>>(A->colind, A->T, B->rowptr, cnt.as<int32_t>());
+        product_counts_kernel<<<grid_wide(A->T), 256, 0, s>>>(A->colind, A->T, B->rowptr, cnt.as<int32_t>());
         B2SR_LAUNCH_CHECK("product_counts_kernel");
         B2SR_CUDA_TRY(cudaMemsetAsync(cnt.as<int32_t>() + A->T, 0, sizeof(int32_t), s));
         B2SR_TRY(exclusive_scan_i32_to_i64(cnt.as<int32_t>(), off.as<int64_t>(), A->T + 1, s));
@@ -263,9 +242,9 @@ b2sr_status spgemm_bool(const b2sr_matrix* A, const b2sr_matrix* B, cudaStream_t
         B2SR_TRY(idx.alloc(P * sizeof(uint32_t)));
         B2SR_TRY(itmp.alloc(P * sizeof(uint32_t)));
         B2SR_TRY(prod.alloc(P * k * sizeof(uint32_t)));
-        B2SR_TRY(with_k(k, [&](auto kc) -> b2sr_status {
+        B2SR_TRY(with_tile(k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
-            expand_kernel<K><<<grid_for(P), 256, 0, s>>>(a_tilerow.as<int32_t>(), A->colind, A->tiles, A->T,
+            expand_kernel<K><<<grid_wide(P), 256, 0, s>>>(a_tilerow.as<int32_t>(), A->colind, A->tiles, A->T,
                                                          off.as<int64_t>(), B->rowptr, B->colind, B->tiles, P,
                                                          sbits, keys.as<uint64_t>(), idx.as<uint32_t>(),
                                                          prod.as<uint32_t>());
@@ -276,7 +255,7 @@ b2sr_status spgemm_bool(const b2sr_matrix* A, const b2sr_matrix* B, cudaStream_t
                                       itmp.as<uint32_t>(), P, 0, 2 * sbits, s, &skeys, &sidx));
         B2SR_TRY(flag.alloc(P * sizeof(int32_t)));
         B2SR_TRY(tidx.alloc(P * sizeof(int64_t)));
-        spgemm_heads_kernel<<<grid_for(P), 256, 0, s>>>(skeys, P, flag.as<int32_t>());
+        spgemm_heads_kernel<<<grid_wide(P), 256, 0, s>>>(skeys, P, flag.as<int32_t>());
         B2SR_LAUNCH_CHECK("spgemm_heads_kernel");
         B2SR_TRY(exclusive_scan_i32_to_i64(flag.as<int32_t>(), tidx.as<int64_t>(), P, s));
         int64_t last = 0;
@@ -305,9 +284,9 @@ b2sr_status spgemm_bool(const b2sr_matrix* A, const b2sr_matrix* B, cudaStream_t
     st = ctilerow.alloc(std::max<int64_t>(TC, 1) * sizeof(int32_t));
     if (st != B2SR_OK) return release(st);
     if (P > 0) {
-        st = with_k(k, [&](auto kc) -> b2sr_status {
+        st = with_tile(k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
-            spgemm_merge_kernel<K><<<grid_for(P), 256, 0, s>>>(skeys, sidx, flag.as<int32_t>(), tidx.as<int64_t>(), P,
+            spgemm_merge_kernel<K><<<grid_wide(P), 256, 0, s>>>(skeys, sidx, flag.as<int32_t>(), tidx.as<int64_t>(), P,
                                                                prod.as<uint32_t>(), sbits, cci, ctilerow.as<int32_t>(),
                                                                reinterpret_cast<uint32_t*>(ct));
             B2SR_LAUNCH_CHECK("spgemm_merge_kernel");
@@ -315,7 +294,7 @@ b2sr_status spgemm_bool(const b2sr_matrix* A, const b2sr_matrix* B, cudaStream_t
         });
         if (st != B2SR_OK) return release(st);
     }
-    build_rowptr_from_rows<<<grid_for(TC + 1), 256, 0, s>>>(ctilerow.as<int32_t>(), TC, ntr, crp);
+    build_rowptr_from_rows<<<grid_wide(TC + 1), 256, 0, s>>>(ctilerow.as<int32_t>(), TC, ntr, crp);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return release(cuda_fail(e, "build_rowptr_from_rows"));

@@ -1383,24 +1383,13 @@ static b2sr_status run_spmv(const b2sr_matrix* h, const SEM& sem, uint32_t* bits
 }
 
 
-template <class F>
-static b2sr_status with_k(int k, F&& f) {
-    switch (k) {
-        case 4: return f(std::integral_constant<int, 4>());
-        case 8: return f(std::integral_constant<int, 8>());
-        case 16: return f(std::integral_constant<int, 16>());
-        case 32: return f(std::integral_constant<int, 32>());
-        default: return fail(B2SR_ERR_UNSUPPORTED_TILE, "bad tile_dim");
-    }
-}
-
 b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, const void* x, b2sr_vec out_kind,
                           void* y, const uint32_t* mask, int comp, const float* weights, cudaStream_t s,
                           const int32_t* gate) {
     comp = comp ? 1 : 0;
     if (sr == B2SR_BOOL_OR_AND && in_kind == B2SR_VEC_BITS && out_kind == B2SR_VEC_BITS) {
         if (weights) return fail(B2SR_ERR_INVALID_ARG, "weights apply to MIN_PLUS only");
-        return with_k(h->k, [&](auto kc) -> b2sr_status {
+        return with_tile(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
             SemBool<K> sem{static_cast<const uint32_t*>(x), static_cast<uint32_t*>(y), mask, comp, h->n};
             return run_spmv<K>(h, sem, static_cast<uint32_t*>(y), s, "spmv_bool", (mask ? 3.0 : 2.0) * h->n / 8.0, gate);
@@ -1408,7 +1397,7 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
     }
     if (sr == B2SR_PLUS_TIMES && in_kind == B2SR_VEC_BITS && out_kind == B2SR_VEC_I32) {
         if (weights) return fail(B2SR_ERR_INVALID_ARG, "weights apply to MIN_PLUS only");
-        return with_k(h->k, [&](auto kc) -> b2sr_status {
+        return with_tile(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
             SemCount<K> sem{static_cast<const uint32_t*>(x), static_cast<int32_t*>(y), mask, comp, h->n};
             return run_spmv<K>(h, sem, nullptr, s, "spmv_count", (mask ? 2.0 : 1.0) * h->n / 8.0 + 4.0 * h->n, gate);
@@ -1416,7 +1405,7 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
     }
     if (sr == B2SR_PLUS_TIMES && in_kind == B2SR_VEC_F32 && out_kind == B2SR_VEC_F32) {
         if (weights) return fail(B2SR_ERR_INVALID_ARG, "weights apply to MIN_PLUS only");
-        return with_k(h->k, [&](auto kc) -> b2sr_status {
+        return with_tile(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
             SemPlus<K> sem{static_cast<const float*>(x), static_cast<float*>(y), mask, comp, h->n};
             return run_spmv<K>(h, sem, nullptr, s, "spmv_plus", 8.0 * h->n + (mask ? h->n / 8.0 : 0.0), gate);
@@ -1424,7 +1413,7 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
     }
     if (sr == B2SR_MIN_PLUS && in_kind == B2SR_VEC_F32 && out_kind == B2SR_VEC_F32) {
         if (weights) B2SR_TRY(ensure_voff(h, s));
-        return with_k(h->k, [&](auto kc) -> b2sr_status {
+        return with_tile(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
             SemMinPlus<K> sem{static_cast<const float*>(x), static_cast<float*>(y), mask, comp, h->n, weights,
                               h->voff, weights != nullptr};
@@ -1435,7 +1424,7 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
     }
     if (sr == B2SR_MIN_PLUS && in_kind == B2SR_VEC_I32 && out_kind == B2SR_VEC_I32) {
         if (weights) return fail(B2SR_ERR_INVALID_ARG, "int32 MIN_PLUS takes no weights (all weights are 0)");
-        return with_k(h->k, [&](auto kc) -> b2sr_status {
+        return with_tile(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
             SemMinI32<K> sem{static_cast<const int32_t*>(x), static_cast<int32_t*>(y), mask, comp, h->n};
             return run_spmv<K>(h, sem, nullptr, s, "spmv_min_i32", 8.0 * h->n + (mask ? h->n / 8.0 : 0.0), gate);
@@ -1443,7 +1432,7 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
     }
     if (sr == B2SR_MAX_TIMES && in_kind == B2SR_VEC_F32 && out_kind == B2SR_VEC_F32) {
         if (weights) return fail(B2SR_ERR_INVALID_ARG, "weights apply to MIN_PLUS only");
-        return with_k(h->k, [&](auto kc) -> b2sr_status {
+        return with_tile(h->k, [&](auto kc) -> b2sr_status {
             constexpr int K = decltype(kc)::value;
             SemMaxF32<K> sem{static_cast<const float*>(x), static_cast<float*>(y), mask, comp, h->n};
             return run_spmv<K>(h, sem, nullptr, s, "spmv_max", 8.0 * h->n + (mask ? h->n / 8.0 : 0.0), gate);
@@ -1454,7 +1443,7 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
 
 b2sr_status spmm64_dispatch(b2sr_matrix* h, const uint64_t* X, uint64_t* Y, const uint64_t* M, int comp,
                             cudaStream_t s, const int32_t* gate) {
-    return with_k(h->k, [&](auto kc) -> b2sr_status {
+    return with_tile(h->k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
         SemOr64<K> sem{reinterpret_cast<const unsigned long long*>(X), reinterpret_cast<unsigned long long*>(Y),
                        reinterpret_cast<const unsigned long long*>(M), comp ? 1 : 0, h->n};
@@ -1464,7 +1453,7 @@ b2sr_status spmm64_dispatch(b2sr_matrix* h, const uint64_t* X, uint64_t* Y, cons
 
 b2sr_status spmv_maxkey_dispatch(b2sr_matrix* h, const uint64_t* x, uint64_t* y, const uint32_t* mask, int comp,
                                  cudaStream_t s, const int32_t* gate) {
-    return with_k(h->k, [&](auto kc) -> b2sr_status {
+    return with_tile(h->k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
         SemMaxKey<K> sem{reinterpret_cast<const unsigned long long*>(x), reinterpret_cast<unsigned long long*>(y), mask,
                          comp ? 1 : 0, h->n};
@@ -1474,7 +1463,7 @@ b2sr_status spmv_maxkey_dispatch(b2sr_matrix* h, const uint64_t* x, uint64_t* y,
 
 b2sr_status spmm4_dispatch(b2sr_matrix* h, const float* X, float* Y, const uint32_t* M, int comp, cudaStream_t s,
                            const int32_t* gate) {
-    return with_k(h->k, [&](auto kc) -> b2sr_status {
+    return with_tile(h->k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
         SemPlus4<K> sem{reinterpret_cast<const float4*>(X), reinterpret_cast<float4*>(Y), M, comp ? 1 : 0, h->n};
         return run_spmv<K>(h, sem, nullptr, s, "spmm_plus4", 32.0 * h->n + (M ? h->n / 8.0 : 0.0), gate);
@@ -1594,7 +1583,7 @@ extern "C" b2sr_status b2sr_spmv_bool_noalloc(b2sr_handle h, const uint32_t* x, 
     void* scratch = noalloc_scratch_ptr(dev, &st);
     if (!scratch) return st;
     const int comp = mask_complement ? 1 : 0;
-    return with_k(h->k, [&](auto kc) -> b2sr_status {
+    return with_tile(h->k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
         SemBool<K> sem{x, y, mask, comp, h->n};
         return run_spmv_bool_fixed<K>(h, sem, y, scratch, to_stream(stream));

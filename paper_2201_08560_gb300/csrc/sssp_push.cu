@@ -27,10 +27,6 @@
 
 namespace b2sr {
 
-static int grid_for(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)sm_count() * 8));
-}
-
 struct PushSide {
     uint32_t* act;   // vertices improved in the previous round (bitset)
     int32_t* list;   // their tile-rows, each once
@@ -158,17 +154,6 @@ __global__ void push_advance_kernel(int32_t* cur_count, const int32_t* next_coun
 __global__ void push_init_kernel(float* dist, int32_t n, int32_t src) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         dist[i] = (i == src) ? 0.0f : INFINITY;
-}
-
-template <class F>
-static b2sr_status with_tile(int k, F&& f) {
-    switch (k) {
-        case 4: return f(std::integral_constant<int, 4>());
-        case 8: return f(std::integral_constant<int, 8>());
-        case 16: return f(std::integral_constant<int, 16>());
-        case 32: return f(std::integral_constant<int, 32>());
-        default: return fail(B2SR_ERR_UNSUPPORTED_TILE, "bad tile_dim");
-    }
 }
 
 b2sr_status sssp_push(b2sr_matrix* hT, const float* w, int32_t src, float* dist, float delta, int max_iters,

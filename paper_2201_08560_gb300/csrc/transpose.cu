@@ -19,16 +19,6 @@ namespace b2sr {
 
 namespace {
 
-int grid_for(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)sm_count() * 8));
-}
-
-int bits_for(int64_t v) {  // bits to hold values in [0, v)
-    int b = 1;
-    while (b < 62 && ((int64_t)1 << b) < v) ++b;
-    return b;
-}
-
 // key = tile-col << rbits | tile-row, payload = the tile's index
 __global__ void tr_keys_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind, int32_t ntr,
                                int64_t T, int rbits, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
@@ -105,17 +95,6 @@ __global__ void tr_fill_kernel(const uint64_t* __restrict__ keys, const uint32_t
         uint32_t* dst = reinterpret_cast<uint32_t*>(tiles_t + p * TB);
 #pragma unroll
         for (int q = 0; q < TW; ++q) dst[q] = o[q];
-    }
-}
-
-template <class F>
-b2sr_status with_tile(int k, F&& f) {
-    switch (k) {
-        case 4: return f(std::integral_constant<int, 4>());
-        case 8: return f(std::integral_constant<int, 8>());
-        case 16: return f(std::integral_constant<int, 16>());
-        case 32: return f(std::integral_constant<int, 32>());
-        default: return fail(B2SR_ERR_UNSUPPORTED_TILE, "bad tile_dim");
     }
 }
 
