@@ -28,9 +28,33 @@ b2sr_status cuda_fail(cudaError_t e, const char* what) {
     return fail(B2SR_ERR_CUDA, m);
 }
 
+// The stream-ordered pool keeps freed memory for reuse (up to a quarter of the
+// device) instead of returning it to the driver at every synchronisation: the
+// conversion's sort buffers and every driver's temporaries are re-used from
+// call to call rather than mapped again.  A property of this process's pool
+// only, gone with the process.
+static void keep_pool_memory() {
+    static std::once_flag once[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return;
+    }
+    std::call_once(once[dev], [dev] {
+        cudaMemPool_t pool = nullptr;
+        size_t free_b = 0, total_b = 0;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            uint64_t keep = (uint64_t)total_b / 4;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    });
+}
+
 b2sr_status dmalloc(void** p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    keep_pool_memory();
     cudaError_t e = cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
