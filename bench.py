@@ -493,6 +493,22 @@ def traffic_for(family, tile, kname):
     return None, None
 
 
+def aggregate_replicas(ms_total, e2e_ms, edges_per_step, steps, world, device):
+    """Whole-job throughput of `world` independent replicas (the graph does not
+    shard: every query reads all of it): the slowest rank's times (all-reduce
+    MAX) over the edges all ranks processed.  Returns (ms_total, e2e_ms,
+    GTEPS, end-to-end GTEPS), the same on every rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_total, e2e_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_total, e2e_ms = float(t[0]), float(t[1])
+    value = world * edges_per_step * steps / (ms_total / 1e3) / 1e9
+    e2e_value = world * edges_per_step * steps / (e2e_ms / 1e3) / 1e9
+    return ms_total, e2e_ms, value, e2e_value
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -614,14 +630,9 @@ def main():
     e2e_ms = e0.elapsed_time(e1)
 
     # ---- max over ranks ----
-    t = torch.tensor([ms_total, e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_total, e2e_ms = float(t[0]), float(t[1])
     edges = QUERIES_PER_STEP * g.nnz
+    ms_total, e2e_ms, value, e2e_value = aggregate_replicas(ms_total, e2e_ms, edges, args.steps, world, dev)
     ms_step = ms_total / args.steps
-    value = world * edges * args.steps / (ms_total / 1e3) / 1e9
-    e2e_value = world * edges * args.steps / (e2e_ms / 1e3) / 1e9
 
     if rank != 0:
         if world > 1:
