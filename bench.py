@@ -84,7 +84,7 @@ def oracle_step_estimate(g, srcs, xbits, bfs_sources=2, pr_iters=2):
     t0 = time.perf_counter(); oracle.pagerank(g, DAMP, pr_iters); t["pr_per_iter"] = (time.perf_counter() - t0) / pr_iters
     t0 = time.perf_counter(); oracle.cc(g); t["cc"] = time.perf_counter() - t0
     step = t["convert"] + t["spmv"] + NSRC * t["bfs_per_source"] + PR_ITERS * t["pr_per_iter"] + t["cc"]
-    sample = (f"oracle (plain C, 1 thread) on the same graph: CSR->B2SR k=8, Boolean SpMV and CC once, BFS from "
+    sample = (f"oracle (plain C, 1 thread) on the same graph: CSR->B2SR k={TILE}, Boolean SpMV and CC once, BFS from "
               f"{bfs_sources} of the {NSRC} sources, PageRank {pr_iters} iterations; step time extrapolated to "
               f"{NSRC} sources and {PR_ITERS} iterations")
     return step, t, sample
@@ -118,7 +118,7 @@ def run_reference(args):
     wall = time.perf_counter() - t_all
     step = statistics.median(times)
     value = edges / step / 1e9
-    sample = (f"oracle (plain C, 1 thread) on the same graph: CSR->B2SR k=8 timed once ({t_conv:.2f} s); each step "
+    sample = (f"oracle (plain C, 1 thread) on the same graph: CSR->B2SR k={TILE} timed once ({t_conv:.2f} s); each step "
               f"times the Boolean SpMV, BFS from one of the {NSRC} sources, one PageRank iteration and CC, and "
               f"extrapolates to {NSRC} sources and {PR_ITERS} iterations")
     line = {
