@@ -560,13 +560,13 @@ def main():
     labels = torch.empty(g.n, dtype=torch.int32, device=dev)
     srcs_l = [int(s) for s in srcs]
 
-    def step(rp_, ci_, x_):
+    def step(rp_, ci_, x_, y_=y, levels_=levels, pr_=pr, labels_=labels):
         m = B.b2sr_from_csr(g.n, rp_, ci_, TILE)
         B.b2sr_set_schedule(m, SCHEDULE)
-        B.b2sr_spmv(m, B.BOOL_OR_AND, B.VEC_BITS, x_, B.VEC_BITS, y)
-        B.b2sr_bfs_multi(m, srcs_l, levels)
-        B.b2sr_pagerank(m, DAMP, PR_ITERS, None, pr)
-        B.b2sr_cc(m, labels)
+        B.b2sr_spmv(m, B.BOOL_OR_AND, B.VEC_BITS, x_, B.VEC_BITS, y_)
+        B.b2sr_bfs_multi(m, srcs_l, levels_)
+        B.b2sr_pagerank(m, DAMP, PR_ITERS, None, pr_)
+        B.b2sr_cc(m, labels_)
         m.close()
 
     for _ in range(args.warmup):
@@ -602,30 +602,54 @@ def main():
     B.b2sr_timing_reset()
 
     # ---- end to end through the C ABI with host buffers ----
-    lv_h = torch.empty((NSRC, g.n), dtype=torch.int32).pin_memory()
-    pr_hh = torch.empty(g.n, dtype=torch.float32).pin_memory()
-    lab_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
-    y_h = torch.empty(words, dtype=torch.int32).pin_memory()
-    h2d = rp_h.numel() * 4 + ci_h.numel() * 4 + x_h.numel() * 4
-    d2h = lv_h.numel() * 4 + pr_hh.numel() * 4 + lab_h.numel() * 4 + y_h.numel() * 4
-    rp_d = torch.empty_like(rp)
-    ci_d = torch.empty_like(ci)
-    x_d = torch.empty_like(x)
+    # Every step copies its CSR and input vector in from pinned host memory and
+    # its results (levels, PageRank, labels, SpMV output) back out.  The copies
+    # run on two copy streams with double buffers, so step i+1's input copy and
+    # step i's result copy overlap step i's kernels; events order each buffer's
+    # reuse.  The library runs on the default stream.
+    comp = torch.cuda.current_stream()
+    cin, cout = torch.cuda.Stream(), torch.cuda.Stream()
+    ins_d = [tuple(torch.empty_like(t) for t in (rp, ci, x)) for _ in range(2)]
+    outs_d = [(y, levels, pr, labels), tuple(torch.empty_like(t) for t in (y, levels, pr, labels))]
+    outs_h = [tuple(torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs_d[0]) for _ in range(2)]
+    h2d = sum(t.numel() * t.element_size() for t in (rp_h, ci_h, x_h))
+    d2h = sum(t.numel() * t.element_size() for t in outs_h[0])
+    in_ready = [torch.cuda.Event() for _ in range(2)]
+    in_free = [torch.cuda.Event() for _ in range(2)]
+    done = [torch.cuda.Event() for _ in range(2)]
+    out_free = [torch.cuda.Event() for _ in range(2)]
+
+    def copy_in(i):
+        b = i % 2
+        cin.wait_event(in_free[b])        # step i-2 is done reading this buffer
+        with torch.cuda.stream(cin):
+            for dst, src in zip(ins_d[b], (rp_h, ci_h, x_h)):
+                dst.copy_(src, non_blocking=True)
+        in_ready[b].record(cin)
+
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        rp_d.copy_(rp_h, non_blocking=True)
-        ci_d.copy_(ci_h, non_blocking=True)
-        x_d.copy_(x_h, non_blocking=True)
-        step(rp_d, ci_d, x_d)
-        lv_h.copy_(levels, non_blocking=True)
-        pr_hh.copy_(pr, non_blocking=True)
-        lab_h.copy_(labels, non_blocking=True)
-        y_h.copy_(y, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-    e1.record()
+    e0.record(comp)
+    copy_in(0)
+    for i in range(args.steps):
+        b = i % 2
+        if i + 1 < args.steps:
+            copy_in(i + 1)
+        comp.wait_event(in_ready[b])
+        comp.wait_event(out_free[b])      # step i-2's results have left this buffer
+        step(*ins_d[b], *outs_d[b])
+        in_free[b].record(comp)
+        done[b].record(comp)
+        cout.wait_event(done[b])
+        with torch.cuda.stream(cout):
+            for dst, src in zip(outs_h[b], outs_d[b]):
+                dst.copy_(src, non_blocking=True)
+        out_free[b].record(cout)
+    for b in range(2):
+        comp.wait_event(out_free[b])
+    e1.record(comp)
+    e1.synchronize()
     barrier()
     e2e_ms = e0.elapsed_time(e1)
 
