@@ -647,8 +647,10 @@ struct GatherLayout<K, SEM, true> {
 // ---------------------------------------------------------------------------
 // pieces shared by the chunk kernels
 // ---------------------------------------------------------------------------
+// Tile indices fit in int32 (T < 2^31: TileColInd and TileRowPtr are int32),
+// which keeps the walk's compares and shuffles single-word.
 struct LaneSpan {
-    int64_t cs, ce, tl;
+    int32_t cs, ce, tl;
     int cnt;
 };
 
@@ -657,39 +659,39 @@ struct LaneSpan {
 // one coalesced load, and the search is a shuffle binary search.
 struct RowCursor {
     int32_t row;
-    int64_t row_start, next;
+    int32_t row_start, next;
     bool head_cs;
 };
 
-__device__ __forceinline__ RowCursor locate_row(const SpmvGeom& g, int64_t c, const LaneSpan& ls, int lane) {
+__device__ __forceinline__ RowCursor locate_row(const SpmvGeom& g, int32_t c, const LaneSpan& ls, int lane) {
     constexpr unsigned FULL = 0xffffffffu;
     const int32_t r0 = __ldg(g.chunk_row + c);
     const int32_t r1 = __ldg(g.chunk_row + c + 1);
     const int32_t span = r1 - r0;
-    const int64_t win = lane <= span + 1 ? (int64_t)__ldg(g.rowptr + r0 + lane) : INT64_MAX;
+    const int32_t win = lane <= span + 1 ? __ldg(g.rowptr + r0 + lane) : INT32_MAX;
     RowCursor rc;
     rc.head_cs = __shfl_sync(FULL, win, 0) == ls.cs;
     int32_t row = r0;
     if (span > 0) {
         // first window: the row starts are lanes 1..31 (lane 0 is rowptr[r0])
-        const int64_t b = lane == 0 ? INT64_MIN : win;
+        const int32_t b = lane == 0 ? INT32_MIN : win;
         int pos = 0;
 #pragma unroll
         for (int step = 16; step >= 1; step >>= 1) {
-            const int64_t v = __shfl_sync(FULL, b, pos + step - 1);
+            const int32_t v = __shfl_sync(FULL, b, pos + step - 1);
             if (v <= ls.tl) pos += step;
         }
         pos += (__shfl_sync(FULL, b, pos) <= ls.tl) ? 1 : 0;
         int32_t add = pos - 1;  // lane 0 is always counted
-        int64_t last = __shfl_sync(FULL, win, 31);
+        int32_t last = __shfl_sync(FULL, win, 31);
         for (int32_t base = 32; base <= span && last < ls.ce; base += 32) {
             // further windows (rare: many tile-rows in one chunk)
             const int32_t j = base + lane;
-            const int64_t bb = j <= span ? (int64_t)__ldg(g.rowptr + r0 + j) : INT64_MAX;
+            const int32_t bb = j <= span ? __ldg(g.rowptr + r0 + j) : INT32_MAX;
             int p2 = 0;
 #pragma unroll
             for (int step = 16; step >= 1; step >>= 1) {
-                const int64_t v = __shfl_sync(FULL, bb, p2 + step - 1);
+                const int32_t v = __shfl_sync(FULL, bb, p2 + step - 1);
                 if (v <= ls.tl) p2 += step;
             }
             p2 += (__shfl_sync(FULL, bb, p2) <= ls.tl) ? 1 : 0;
@@ -699,11 +701,11 @@ __device__ __forceinline__ RowCursor locate_row(const SpmvGeom& g, int64_t c, co
         row = r0 + add;
     }
     const int d = row - r0;
-    const int64_t a0 = __shfl_sync(FULL, win, d < 32 ? d : 0);
-    const int64_t a1 = __shfl_sync(FULL, win, d + 1 < 32 ? d + 1 : 0);
+    const int32_t a0 = __shfl_sync(FULL, win, d < 32 ? d : 0);
+    const int32_t a1 = __shfl_sync(FULL, win, d + 1 < 32 ? d + 1 : 0);
     rc.row = row;
-    rc.row_start = d < 32 ? a0 : (int64_t)__ldg(g.rowptr + row);
-    rc.next = d + 1 < 32 ? a1 : (int64_t)__ldg(g.rowptr + row + 1);
+    rc.row_start = d < 32 ? a0 : __ldg(g.rowptr + row);
+    rc.next = d + 1 < 32 ? a1 : __ldg(g.rowptr + row + 1);
     return rc;
 }
 
@@ -712,11 +714,11 @@ __device__ __forceinline__ RowCursor locate_row(const SpmvGeom& g, int64_t c, co
 template <class SEM, class Acc>
 struct Walk {
     int32_t row;
-    int64_t next;
+    int32_t next;
     bool has_end = false;
     bool open = false;
     // called after tile t (the lane's i-th of cnt) has been accumulated
-    __device__ __forceinline__ void end_tile(const SpmvGeom& g, const SEM& sem, Acc& acc, Acc& F, int64_t t, int i,
+    __device__ __forceinline__ void end_tile(const SpmvGeom& g, const SEM& sem, Acc& acc, Acc& F, int32_t t, int i,
                                              int cnt, const RegAcc<typename SEM::V, SEM::NV>& idv) {
         open = true;
         if (t + 1 == next) {  // tile-row `row` ends with tile t
@@ -732,7 +734,7 @@ struct Walk {
             open = false;
             if (i + 1 < cnt) {
                 int32_t R = row + 1;
-                while ((int64_t)__ldg(g.rowptr + R + 1) == next) { sem.store(R, idv); ++R; }
+                while (__ldg(g.rowptr + R + 1) == next) { sem.store(R, idv); ++R; }
                 row = R;
                 next = __ldg(g.rowptr + row + 1);
             }
@@ -787,11 +789,11 @@ __device__ __forceinline__ void close_chunk(const SEM& sem, Partials<typename SE
 }
 
 template <int K>
-__device__ __forceinline__ void load_lane_tiles(const SpmvGeom& g, int64_t tl, uint4 (&tv)[ChunkShape<K>::TILE_V4],
+__device__ __forceinline__ void load_lane_tiles(const SpmvGeom& g, int32_t tl, uint4 (&tv)[ChunkShape<K>::TILE_V4],
                                                 int32_t (&col)[ChunkShape<K>::P]) {
     using S = ChunkShape<K>;
     constexpr int P = S::P;
-    const uint4* src = reinterpret_cast<const uint4*>(g.tiles + tl * S::TB);
+    const uint4* src = reinterpret_cast<const uint4*>(g.tiles + (int64_t)tl * S::TB);
 #pragma unroll
     for (int q = 0; q < S::TILE_V4; ++q) tv[q] = __ldg(src + q);
     if constexpr (P % 4 == 0) {
@@ -824,14 +826,14 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
     constexpr int P = S::P;
     const int warp = threadIdx.x >> 5;
     const int lane = (int)lane_id();
-    const int64_t c = (int64_t)blockIdx.x * kSpmvWarps + warp;
+    const int32_t c = (int32_t)blockIdx.x * kSpmvWarps + warp;
     if (c >= g.nchunks || gated_off(g.gate)) return;  // whole warps leave together
 
     LaneSpan ls;
     ls.cs = c * S::CT;
-    ls.ce = min(ls.cs + (int64_t)S::CT, g.T);
-    ls.tl = ls.cs + (int64_t)lane * P;
-    ls.cnt = (int)max((int64_t)0, min((int64_t)P, ls.ce - ls.tl));
+    ls.ce = min(ls.cs + S::CT, (int32_t)g.T);
+    ls.tl = ls.cs + lane * P;
+    ls.cnt = max(0, min(P, ls.ce - ls.tl));
 
     uint4 tv[S::TILE_V4];
     int32_t col[P];
@@ -867,11 +869,11 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
     if (ls.cnt > 0) {
         // empty tile-rows just before a row that starts at this lane's first tile
         if (ls.tl > 0 && rc.row_start == ls.tl)
-            for (int32_t R = rc.row - 1; R >= 0 && (int64_t)__ldg(g.rowptr + R) == ls.tl; --R) sem.store(R, idv);
+            for (int32_t R = rc.row - 1; R >= 0 && __ldg(g.rowptr + R) == ls.tl; --R) sem.store(R, idv);
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             if (i < ls.cnt) {
-                const int64_t t = ls.tl + i;
+                const int32_t t = ls.tl + i;
                 if constexpr (!SEM::kGather) {
                     sem.tile(acc, words + i * S::TW, xs[i]);
                 } else {
@@ -943,7 +945,7 @@ __global__ void __launch_bounds__(kSpmvThreads, (gather_min_blocks<K, SEM>())) s
     extern __shared__ __align__(16) uint8_t smem[];
     const int warp = threadIdx.x >> 5;
     const int lane = (int)lane_id();
-    const int64_t c = (int64_t)blockIdx.x * kSpmvWarps + warp;
+    const int32_t c = (int32_t)blockIdx.x * kSpmvWarps + warp;
     if (c >= g.nchunks || gated_off(g.gate)) return;  // whole warps leave together
 
     uint8_t* wsm = smem + warp * L::bytes;
@@ -956,9 +958,9 @@ __global__ void __launch_bounds__(kSpmvThreads, (gather_min_blocks<K, SEM>())) s
 
     LaneSpan ls;
     ls.cs = c * S::CT;
-    ls.ce = min(ls.cs + (int64_t)S::CT, g.T);
-    ls.tl = ls.cs + (int64_t)lane * P;
-    ls.cnt = (int)max((int64_t)0, min((int64_t)P, ls.ce - ls.tl));
+    ls.ce = min(ls.cs + S::CT, (int32_t)g.T);
+    ls.tl = ls.cs + lane * P;
+    ls.cnt = max(0, min(P, ls.ce - ls.tl));
 
     uint4 tv[S::TILE_V4];
     int32_t col[P];
@@ -1050,26 +1052,26 @@ __global__ void __launch_bounds__(kSpmvThreads, (gather_min_blocks<K, SEM>())) s
         const int32_t r0 = __ldg(g.chunk_row + c);
         const int32_t span = __ldg(g.chunk_row + c + 1) - r0;
         if (staged && span <= 3) {
-            const int64_t win = lane <= span + 1 ? (int64_t)__ldg(g.rowptr + r0 + lane) : INT64_MAX;
+            const int32_t win = lane <= span + 1 ? __ldg(g.rowptr + r0 + lane) : INT32_MAX;
             cp_async_wait_all();
             __syncwarp();  // values, tags and slot starts of every lane are visible
             const int32_t* pre = reinterpret_cast<const int32_t*>(wsm + L::pre_off);
-            auto slot_of = [&](int64_t t) -> int {  // first slot of chunk tile t (nbits at the chunk end)
+            auto slot_of = [&](int32_t t) -> int {  // first slot of chunk tile t (nbits at the chunk end)
                 if (t >= ls.ce) return nbits;
-                const int64_t o = t - ls.cs;
-                return pre[(int)(o % P) * 32 + (int)(o / P)];
+                const int32_t o = t - ls.cs;
+                return pre[(o % P) * 32 + (o / P)];
             };
-            const int64_t a0 = __shfl_sync(FULL, win, 0);
+            const int32_t a0 = __shfl_sync(FULL, win, 0);
             if (lane == 0 && a0 == ls.cs && ls.cs > 0)  // empty rows just before the chunk's first tile-row
-                for (int32_t R = r0 - 1; R >= 0 && (int64_t)__ldg(g.rowptr + R) == ls.cs; --R) sem.store(R, idv);
+                for (int32_t R = r0 - 1; R >= 0 && __ldg(g.rowptr + R) == ls.cs; --R) sem.store(R, idv);
             for (int j = 0; j <= span; ++j) {
                 const int32_t R = r0 + j;
-                const int64_t a = __shfl_sync(FULL, win, j), b = __shfl_sync(FULL, win, j + 1);
+                const int32_t a = __shfl_sync(FULL, win, j), b = __shfl_sync(FULL, win, j + 1);
                 if (a == b) {  // empty tile-row inside the chunk's range
                     if (lane == 0 && a >= ls.cs && a < ls.ce && a > 0) sem.store(R, idv);
                     continue;
                 }
-                const int64_t ts = max(a, ls.cs), te = min(b, ls.ce);
+                const int32_t ts = max(a, ls.cs), te = min(b, ls.ce);
                 if (ts >= te) continue;  // its tiles lie outside this chunk
                 const int s0 = slot_of(ts), s1 = slot_of(te);
                 RegAcc<V, NV> acc;
@@ -1115,7 +1117,7 @@ __global__ void __launch_bounds__(kSpmvThreads, (gather_min_blocks<K, SEM>())) s
     if (ls.cnt > 0) {
         // empty tile-rows just before a row that starts at this lane's first tile
         if (ls.tl > 0 && rc.row_start == ls.tl)
-            for (int32_t R = rc.row - 1; R >= 0 && (int64_t)__ldg(g.rowptr + R) == ls.tl; --R) sem.store(R, idv);
+            for (int32_t R = rc.row - 1; R >= 0 && __ldg(g.rowptr + R) == ls.tl; --R) sem.store(R, idv);
         if (staged) {
             int i = 0;
             for (int j = 0; j < nb; ++j) {
@@ -1138,7 +1140,7 @@ __global__ void __launch_bounds__(kSpmvThreads, (gather_min_blocks<K, SEM>())) s
 #pragma unroll
             for (int i = 0; i < P; ++i) {
                 if (i < ls.cnt) {
-                    const int64_t t = ls.tl + i;
+                    const int32_t t = ls.tl + i;
                     const G* xt = sem.src() + (int64_t)col[i] * K;
                     const float* wt = sem.weighted ? sem.wts() + __ldg(sem.voffs() + t) : nullptr;
                     int qb = 0;
