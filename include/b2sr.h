@@ -336,7 +336,9 @@ b2sr_status b2sr_spgemm_masked_count(b2sr_handle A, b2sr_handle B, b2sr_handle M
 
 /* Boolean SpGEMM C = A (x) B over OR-AND, output in B2SR with the same
  * tile_dim (not in the paper's Table 3; built from the same tile products):
- * C_IJ[r] = OR_K OR_{m: bit m of A_IK[r]} B_KJ[m].  Synchronises `stream`. */
+ * C_IJ[r] = OR_K OR_{m: bit m of A_IK[r]} B_KJ[m].  Synchronises `stream`.
+ * B2SR_ERR_OOM for more than 2^32 tile products or 2^31 - 1 result tiles
+ * (every handle indexes its tiles with int32). */
 b2sr_status b2sr_spgemm_bool(b2sr_handle A, b2sr_handle B, void* stream, b2sr_handle* C);
 
 /* ---------------------------------------------------------------------- */

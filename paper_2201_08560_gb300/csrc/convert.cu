@@ -225,6 +225,8 @@ b2sr_status new_handle_from_tiles(int32_t n, int k, int64_t T, int32_t* rowptr, 
         b2sr_destroy(h);
         return st;
     };
+    // the SpMV and driver kernels index tiles with int32
+    if (T >= (int64_t(1) << 31)) return cleanup(fail(B2SR_ERR_OOM, "more than 2^31 - 1 tiles"));
     DevBuf cnt(s);
     b2sr_status st = cnt.alloc(sizeof(int64_t));
     if (st != B2SR_OK) return cleanup(st);
