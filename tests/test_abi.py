@@ -69,3 +69,13 @@ def test_host_side_errors_without_gpu(lib):
     assert lib.b2sr_spmv(None, 0, 0, None, 0, None, None, 0, None, None) == 1
     lib.b2sr_version.restype = ctypes.c_char_p
     assert lib.b2sr_version().decode().count(".") == 2
+    # the max-times, transpose and bit-plane entry points check their handle first
+    for name, args in (("b2sr_mis", (None, None, None, 0, None)),
+                       ("b2sr_color", (None, None, None, 0, 0, None)),
+                       ("b2sr_transpose", (None, None, ctypes.byref(out))),
+                       ("b2sr_planes_from_csr", (None, None, None, None, 8, None, None)),
+                       ("b2sr_spmv_planes", (None, None, 8, 0, None, 4, None, None, 0, None))):
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int
+        assert f(*args) == 1, name  # INVALID_ARG: not a handle
+    assert lib.b2sr_transpose(None, None, None) == 1  # out is NULL
