@@ -69,65 +69,67 @@ def make_graph():
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_step_estimate(g, srcs, xbits, bfs_sources=2, pr_iters=2):
-    """Times the oracle on a bounded sample of one step and extrapolates the
-    full step: conversion, SpMV and CC once, BFS on `bfs_sources` of the 16
-    sources, PageRank for `pr_iters` iterations."""
+def oracle_step(g, srcs, xbits, threads):
+    """One whole step of the workload on the CPU oracle with `threads` host
+    threads: CSR -> B2SR (one thread), the Boolean SpMV (row loop on all
+    threads), BFS from the 16 sources (one source per thread), PageRank for
+    50 iterations (row loops on all threads) and CC (one thread, union-find).
+    Returns (seconds, per-part seconds)."""
+    from concurrent.futures import ThreadPoolExecutor
     import oracle
+    oracle.set_threads(threads)
     t = {}
-    t0 = time.perf_counter(); oracle.b2sr(g, TILE); t["convert"] = time.perf_counter() - t0
-    t0 = time.perf_counter(); oracle.spmv_bool(g, xbits); t["spmv"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    for s in srcs[:bfs_sources]:
-        oracle.bfs(g, int(s))
-    t["bfs_per_source"] = (time.perf_counter() - t0) / bfs_sources
-    t0 = time.perf_counter(); oracle.pagerank(g, DAMP, pr_iters); t["pr_per_iter"] = (time.perf_counter() - t0) / pr_iters
-    t0 = time.perf_counter(); oracle.cc(g); t["cc"] = time.perf_counter() - t0
-    step = t["convert"] + t["spmv"] + NSRC * t["bfs_per_source"] + PR_ITERS * t["pr_per_iter"] + t["cc"]
-    sample = (f"oracle (plain C, 1 thread) on the same graph: CSR->B2SR k={TILE}, Boolean SpMV and CC once, BFS from "
-              f"{bfs_sources} of the {NSRC} sources, PageRank {pr_iters} iterations; step time extrapolated to "
-              f"{NSRC} sources and {PR_ITERS} iterations")
-    return step, t, sample
+    a = time.perf_counter(); oracle.b2sr(g, TILE); t["convert"] = time.perf_counter() - a
+    a = time.perf_counter(); oracle.spmv_bool(g, xbits); t["spmv"] = time.perf_counter() - a
+    a = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda s: oracle.bfs(g, int(s)), srcs))
+    t["bfs_16_sources"] = time.perf_counter() - a
+    a = time.perf_counter(); oracle.pagerank(g, DAMP, PR_ITERS); t["pagerank_50"] = time.perf_counter() - a
+    a = time.perf_counter(); oracle.cc(g); t["cc"] = time.perf_counter() - a
+    return sum(t.values()), t
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def run_reference(args):
-    """The CPU oracle on the same step: conversion timed once, then per step a
-    bounded sample (SpMV, one BFS source, one PageRank iteration, CC) from
-    which the full step time is extrapolated."""
+    """The CPU oracle on the same workload and metric: whole steps (no
+    extrapolation) on all of the host's cores, W untimed then K timed."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     g, srcs, xbits = make_graph()
     import oracle
     oracle.build()
+    cores = host_cores()
     edges = QUERIES_PER_STEP * g.nnz
-    t0 = time.perf_counter()
-    oracle.b2sr(g, TILE)
-    t_conv = time.perf_counter() - t0
     for _ in range(args.warmup):
-        oracle.spmv_bool(g, xbits)
-    times = []
+        oracle_step(g, srcs, xbits, cores)
+    times, parts = [], []
     t_all = time.perf_counter()
-    for i in range(args.steps):
-        p = {}
-        a = time.perf_counter(); oracle.spmv_bool(g, xbits); p["spmv"] = time.perf_counter() - a
-        a = time.perf_counter(); oracle.bfs(g, int(srcs[i % NSRC])); p["bfs"] = time.perf_counter() - a
-        a = time.perf_counter(); oracle.pagerank(g, DAMP, 1); p["pr"] = time.perf_counter() - a
-        a = time.perf_counter(); oracle.cc(g); p["cc"] = time.perf_counter() - a
-        times.append(t_conv + p["spmv"] + NSRC * p["bfs"] + PR_ITERS * p["pr"] + p["cc"])
+    for _ in range(args.steps):
+        st, p = oracle_step(g, srcs, xbits, cores)
+        times.append(st)
+        parts.append(p)
     wall = time.perf_counter() - t_all
-    step = statistics.median(times)
-    value = edges / step / 1e9
-    sample = (f"oracle (plain C, 1 thread) on the same graph: CSR->B2SR k={TILE} timed once ({t_conv:.2f} s); each step "
-              f"times the Boolean SpMV, BFS from one of the {NSRC} sources, one PageRank iteration and CC, and "
-              f"extrapolates to {NSRC} sources and {PR_ITERS} iterations")
+    total = sum(times)
+    value = args.steps * edges / total / 1e9
+    sample = (f"whole steps of the workload on the oracle (plain C): CSR->B2SR k={TILE} and CC on one thread, "
+              f"the Boolean SpMV and PageRank's row loops on {cores} OpenMP threads, the {NSRC} BFS sources "
+              f"{cores} at a time; {args.steps} timed steps after {args.warmup} untimed")
     line = {
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": int(args.gpus), "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8/f64", "data": "synthetic", "impl": "reference",
-        "config": workload_desc(g.n, g.nnz),
-        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample,
-                         "wall_s": wall},
+        "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8/f64", "data": "synthetic", "impl": "reference",
+        "config": dict(workload_desc(g.n, g.nnz), parallelism=f"replicas x{args.gpus}"),
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": cores, "kind": "oracle", "sample": sample,
+                         "nproc": os.cpu_count(), "timed_wall_s": wall,
+                         "parts_s_median": {k: statistics.median(p[k] for p in parts) for k in parts[0]}},
         "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -151,7 +153,7 @@ def _serve_graph(scale, seed):
     return g.n, g.rowptr, g.colind, np.flatnonzero(deg > 0).astype(np.int32)
 
 
-def serving_extra(B, dev, pool=None):
+def serving_extra(B, dev, gs, t_gen):
     """32 resident graphs (scales 14..20, k = 8); 10,000 queries, half BFS from
     a random non-isolated source and half personalised PageRank (20 iterations,
     all teleport mass on a random non-isolated source), arriving as a Poisson
@@ -159,17 +161,8 @@ def serving_extra(B, dev, pool=None):
     throughput for that stream, its throughput when all queries are queued at
     once, and the throughput of one query per driver call on a sample of the
     same mix."""
-    import multiprocessing as mp
     import torch
     lo, hi = SERVE_SCALES
-    specs = [(lo + i % (hi - lo + 1), 1000 + i) for i in range(SERVE_GRAPHS)]
-    t_gen = time.perf_counter()
-    if pool is None:
-        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as own:
-            gs = own.starmap(_serve_graph, specs)
-    else:
-        gs = pool.starmap(_serve_graph, specs)
-    t_gen = time.perf_counter() - t_gen
     mats = []
     for n, rp, ci, _ in gs:
         mats.append(B.b2sr_from_csr(n, torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), SERVE_TILE))
@@ -287,7 +280,7 @@ def serving_extra(B, dev, pool=None):
                      f"seeds 1000+i, k={SERVE_TILE} direct schedule, {resident / 2**30:.2f} GiB resident; {SERVE_QUERIES} queries, 50% BFS "
                      f"(random non-isolated source) / 50% personalised PageRank ({SERVE_PR_ITERS} iters, d={DAMP}), "
                      f"Poisson arrivals at {SERVE_RATE:.0f}/s; budget {SERVE_BUDGET >> 30} GiB, 64 BFS lanes and 2 "
-                     f"four-column PageRank blocks per graph; graph generation {t_gen:.1f} s on the host (untimed)")
+                     f"four-column PageRank blocks per graph; graphs generated on the host before any timing ({t_gen:.1f} s)")
     for m in mats:
         m.close()
     return res
@@ -300,6 +293,7 @@ GRID_SIDE, GRID_WSEED, SSSP_DELTA = 4096, 5, 400.0
 TC_SCALE, TC_EF = 18, 32
 MS_SCALE, MS_SOURCES = 22, 64
 ARENA_GRAPHS, ARENA_SCALES = 256, (8, 16)
+PERM_SEED = 2
 
 
 def _grid_weighted():
@@ -328,12 +322,12 @@ def _timed(fn, reps=1):
     return a.elapsed_time(b) / reps
 
 
-def grid_tc_extra(B, dev, grid_res, tc_res):
+def grid_tc_extra(B, dev, grid, tc):
     """SSSP from the corner of a 4096 x 4096 4-neighbour grid with fp32 weights
     on the 1/16 lattice in [1, 100); triangle count of R-MAT scale 18 ef32."""
     import torch
     out = {}
-    n, rp, ci, w = grid_res.get()
+    n, rp, ci, w = grid
     rp_d, ci_d = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
     with B.b2sr_from_csr(n, rp_d, ci_d, EXTRA_TILE) as m:
         wb = B.b2sr_weights_from_csr(m, rp_d, ci_d, torch.from_numpy(w).to(dev))
@@ -345,7 +339,7 @@ def grid_tc_extra(B, dev, grid_res, tc_res):
         out["sssp_grid4096"] = {"driver": "b2sr_sssp_push", "delta": SSSP_DELTA, "ms": ms, "nnz": int(ci.size),
                                 "gteps": ci.size / (ms / 1e3) / 1e9, "dist_far_corner": far, "n": int(n)}
     del rp_d, ci_d
-    n, rp, ci = tc_res.get()
+    n, rp, ci = tc
     rp_d, ci_d = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
     with B.b2sr_from_csr(n, rp_d, ci_d, EXTRA_TILE) as m:
         cnt = {}
@@ -357,7 +351,7 @@ def grid_tc_extra(B, dev, grid_res, tc_res):
     return out
 
 
-def batching_extra(B, dev, big_res, arena_res, arena_scales):
+def batching_extra(B, dev, big, arena_gs, arena_scales):
     """64-source BFS on R-MAT scale 22 (tile_dim and schedule from the
     autotuner) against 64 single-source BFS calls; 256 R-MAT graphs (scales
     8..16) in one block-diagonal arena, one BFS each in one captured level loop,
@@ -365,7 +359,7 @@ def batching_extra(B, dev, big_res, arena_res, arena_scales):
     import torch
     from paper_2201_08560_gb300 import graphs
     out = {}
-    n, rp, ci = big_res.get()
+    n, rp, ci = big
     rp_d, ci_d = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
     rng = np.random.default_rng(17)
     deg = np.diff(rp)
@@ -392,7 +386,7 @@ def batching_extra(B, dev, big_res, arena_res, arena_scales):
                                "speedup": t_plain / t_multi, "nnz": int(ci.size),
                                "batched_gteps": MS_SOURCES * ci.size / (t_multi / 1e3) / 1e9}
     del rp_d, ci_d
-    gs = arena_res.get()
+    gs = arena_gs
     csrs = [(gn, torch.from_numpy(grp).to(dev), torch.from_numpy(gci).to(dev)) for gn, grp, gci in gs]
     arena, bases = B.b2sr_from_csr_batch(csrs, EXTRA_TILE)
     srcs_a = [int(bases[i]) for i in range(len(gs))]  # vertex 0 of every graph (its hub)
@@ -509,6 +503,157 @@ def aggregate_replicas(ms_total, e2e_ms, edges_per_step, steps, world, device):
     return ms_total, e2e_ms, value, e2e_value
 
 
+def generate_extra_graphs():
+    """Every graph the extras use, generated on the host by a spawn-started
+    process pool before any timed region starts (so no timing overlaps host
+    generation work).  Returns a dict of plain arrays and the wall time."""
+    import multiprocessing as mp
+    t0 = time.perf_counter()
+    lo, hi = SERVE_SCALES
+    serve_specs = [(lo + i % (hi - lo + 1), 1000 + i) for i in range(SERVE_GRAPHS)]
+    rng = np.random.default_rng(23)
+    a_scales = [int(v) for v in rng.integers(ARENA_SCALES[0], ARENA_SCALES[1] + 1, ARENA_GRAPHS)]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        serve = pool.starmap_async(_serve_graph, serve_specs)
+        grid = pool.apply_async(_grid_weighted)
+        tc = pool.apply_async(_rmat_plain, (TC_SCALE, TC_EF, 2))
+        big = pool.apply_async(_rmat_plain, (MS_SCALE, EDGE_FACTOR, 3))
+        perm = pool.apply_async(_rmat_perm, (SCALE, EDGE_FACTOR, SEED, PERM_SEED))
+        arena = pool.starmap_async(_rmat_plain, [(sc, EDGE_FACTOR, 5000 + i) for i, sc in enumerate(a_scales)])
+        out = {"serve": serve.get(), "grid": grid.get(), "tc": tc.get(), "big": big.get(), "perm": perm.get(),
+               "arena": arena.get()}
+    return out, time.perf_counter() - t0
+
+
+def _rmat_perm(scale, ef, seed, perm_seed):
+    from paper_2201_08560_gb300 import graphs
+    g = graphs.permute(graphs.rmat(scale, ef, seed=seed), perm_seed)
+    return g.n, g.rowptr, g.colind
+
+
+def timed_steps(B, step, args, barrier, uuid=None):
+    """W untimed then K timed steps (CUDA events on the launching stream, a
+    synchronising barrier on both sides), with the library's per-family SpMV
+    launch timing on and, if `uuid` is given, clocks sampled meanwhile.
+    Returns (ms over the K steps, per-family timing, launches, clocks)."""
+    import torch
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    B.b2sr_timing_reset()
+    B.b2sr_timing_enable(True)
+    launches0 = B.b2sr_launch_count()
+    clk = ClockSampler(uuid) if uuid is not None else None
+    if clk is not None:
+        clk.__enter__()
+    try:
+        barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            step()
+        ev1.record()
+        barrier()
+    finally:
+        if clk is not None:
+            clk.__exit__()
+    launches = B.b2sr_launch_count() - launches0
+    B.b2sr_timing_enable(False)
+    fam = {}
+    for f in FAMILIES:
+        t, n, by = B.b2sr_timing_read(f)
+        if n:
+            fam[f] = {"ms": t, "launches": n, "bytes": by}
+    B.b2sr_timing_reset()
+    return ev0.elapsed_time(ev1), fam, launches, (clk.summary() if clk is not None else None)
+
+
+def roofline_of(fam, ms_total, peak, peak_src, tile, schedule):
+    """Roofline entry of the family with the most device time in a timed
+    region: algorithmic bytes per launch over its average CUDA-event launch
+    time, against the measured copy bandwidth."""
+    if not fam:
+        return None
+    dom = max(fam, key=lambda f: fam[f]["ms"])
+    d = fam[dom]
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    kname = spmv_kernel_name(dom, tile, schedule)
+    traffic, _ = traffic_for(dom, tile, kname)
+    return {"bound": "hbm", "kernel": f"{kname} ({dom}, k={tile})", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+            "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+            "avg_launch_us": d["ms"] / d["launches"] * 1e3, "launches": d["launches"],
+            "share_of_step": d["ms"] / ms_total, "traffic": traffic}
+
+
+def spmv_kernel_name(family, tile, schedule):
+    """The SpMV kernel a family runs at this tile_dim and schedule (the
+    library's dispatch: the tile_dim-4 kernel for the bit-vector
+    schemes and for the value schemes under the direct schedule)."""
+    bits = family in ("spmv_bool", "spmv_count")
+    if tile == 4 and (bits or schedule == 2):
+        return "spmv_k4_kernel"
+    if not bits and tile <= 16 and schedule != 2:
+        return "spmv_gather_kernel"
+    return "spmv_chunks_kernel"
+
+
+def measured_peak():
+    peak, src = 6800.0, "fallback 6.8 TB/s"
+    try:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak, src = float(pk["hbm_gbs"]), "measured hbm_gbs (MEASURED_PEAKS.json)"
+    except Exception:
+        pass
+    return peak, src
+
+
+def tile_sweep(B, dev, graphs_by_name, x_bits, peak):
+    """Boolean and plus-times SpMV kernel time at tile_dim 4/8/16/32 (both
+    schedules of the value scheme where it has two) on each graph: kernel us,
+    algorithmic GB/s and the fraction of the measured copy bandwidth."""
+    import torch
+    out = {}
+    for name, (n, rp, ci) in graphs_by_name.items():
+        rows = {}
+        rp_d, ci_d = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
+        x = torch.from_numpy(x_bits.view(np.int32)).to(dev)
+        y = torch.empty(B.bitset_words(n), dtype=torch.int32, device=dev)
+        xf = torch.from_numpy(np.random.default_rng(5).random(n).astype(np.float32)).to(dev)
+        yf = torch.empty(n, dtype=torch.float32, device=dev)
+        for k in (4, 8, 16, 32):
+            ent = {}
+            with B.b2sr_from_csr(n, rp_d, ci_d, k) as m:
+                ent["tiles"] = m.n_tiles
+                for label, sched, call, fam in (
+                        ("bool", 2, lambda: B.b2sr_spmv(m, B.BOOL_OR_AND, B.VEC_BITS, x, B.VEC_BITS, y), "spmv_bool"),
+                        ("plus_staged", 1, lambda: B.b2sr_spmv(m, B.PLUS_TIMES, B.VEC_F32, xf, B.VEC_F32, yf), "spmv_plus"),
+                        ("plus_direct", 2, lambda: B.b2sr_spmv(m, B.PLUS_TIMES, B.VEC_F32, xf, B.VEC_F32, yf), "spmv_plus")):
+                    if k == 32 and label == "plus_staged":
+                        continue  # one schedule at tile_dim 32
+                    B.b2sr_set_schedule(m, sched)
+                    for _ in range(3):
+                        call()
+                    torch.cuda.synchronize()
+                    B.b2sr_timing_reset()
+                    B.b2sr_timing_enable(True)
+                    for _ in range(10):
+                        call()
+                    torch.cuda.synchronize()
+                    t, nl, by = B.b2sr_timing_read(fam)
+                    B.b2sr_timing_enable(False)
+                    B.b2sr_timing_reset()
+                    us = t / nl * 1e3
+                    gbs = by / nl / (us / 1e6) / 1e9
+                    ent[label] = {"kernel": spmv_kernel_name(fam, k, sched), "us": us, "gbs": gbs,
+                                  "frac": gbs / peak, "gteps": int(ci.size) / (us / 1e6) / 1e9}
+            rows[f"k{k}"] = ent
+        out[name] = rows
+        del rp_d, ci_d
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -528,12 +673,17 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
 
-    import torch
-    import torch.distributed as dist
-
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the extras' graphs are generated before any GPU timing (rank 0 only)
+    pre, t_gen = (None, 0.0)
+    if rank == 0 and not args.no_extras:
+        pre, t_gen = generate_extra_graphs()
+
+    import torch
+    import torch.distributed as dist
+
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -560,18 +710,14 @@ def main():
     labels = torch.empty(g.n, dtype=torch.int32, device=dev)
     srcs_l = [int(s) for s in srcs]
 
-    def step(rp_, ci_, x_, y_=y, levels_=levels, pr_=pr, labels_=labels):
-        m = B.b2sr_from_csr(g.n, rp_, ci_, TILE)
+    def step(rp_=rp, ci_=ci, x_=x, y_=y, levels_=levels, pr_=pr, labels_=labels, n=g.n, srcs_=srcs_l):
+        m = B.b2sr_from_csr(n, rp_, ci_, TILE)
         B.b2sr_set_schedule(m, SCHEDULE)
         B.b2sr_spmv(m, B.BOOL_OR_AND, B.VEC_BITS, x_, B.VEC_BITS, y_)
-        B.b2sr_bfs_multi(m, srcs_l, levels_)
+        B.b2sr_bfs_multi(m, srcs_, levels_)
         B.b2sr_pagerank(m, DAMP, PR_ITERS, None, pr_)
         B.b2sr_cc(m, labels_)
         m.close()
-
-    for _ in range(args.warmup):
-        step(rp, ci, x)
-    barrier()
 
     # ---- device-resident timed region ----
     try:
@@ -579,27 +725,7 @@ def main():
         uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
     except Exception:
         uuid = str(local)
-    B.b2sr_timing_reset()
-    B.b2sr_timing_enable(True)
-    launches0 = B.b2sr_launch_count()
-    with ClockSampler(uuid) as clk:
-        barrier()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        for _ in range(args.steps):
-            step(rp, ci, x)
-        ev1.record()
-        barrier()
-    launches = B.b2sr_launch_count() - launches0
-    B.b2sr_timing_enable(False)
-    ms_total = ev0.elapsed_time(ev1)
-    fam = {}
-    for f in FAMILIES:
-        t, n, by = B.b2sr_timing_read(f)
-        if n:
-            fam[f] = {"ms": t, "launches": n, "bytes": by}
-    B.b2sr_timing_reset()
+    ms_total, fam, launches, clocks = timed_steps(B, step, args, barrier, uuid)
 
     # ---- end to end through the C ABI with host buffers ----
     # Every step copies its CSR and input vector in from pinned host memory and
@@ -657,14 +783,18 @@ def main():
     edges = QUERIES_PER_STEP * g.nnz
     ms_total, e2e_ms, value, e2e_value = aggregate_replicas(ms_total, e2e_ms, edges, args.steps, world, dev)
     ms_step = ms_total / args.steps
+    del ins_d, outs_d, outs_h
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
 
-    # ---- extras: batched vs plain BFS, Boolean SpMV alone ----
+    peak, peak_src = measured_peak()
+    roofline = roofline_of(fam, ms_total, peak, peak_src, TILE, SCHEDULE)
     extra = {}
+
+    # ---- extras: batched vs plain BFS, Boolean SpMV alone ----
     with B.b2sr_from_csr(g.n, rp, ci, TILE) as m:
         B.b2sr_set_schedule(m, SCHEDULE)
         for _ in range(2):
@@ -707,7 +837,7 @@ def main():
         B.b2sr_timing_enable(False)
         B.b2sr_timing_reset()
         extra["spmv_bool"] = {"tile_dim": TILE, "kernel_us": tb / nb * 1e3, "gteps": g.nnz / (tb / nb / 1e3) / 1e9,
-                              "gbs": byb / nb / (tb / nb / 1e3) / 1e9}
+                              "gbs": byb / nb / (tb / nb / 1e3) / 1e9, "frac": byb / nb / (tb / nb / 1e3) / 1e9 / peak}
         # max-times (Table 4): the SpMV alone, then MIS and colouring by rounds of local maxima
         xf = torch.from_numpy(np.random.default_rng(37).normal(size=g.n).astype(np.float32)).to(dev)
         yf = torch.empty(g.n, dtype=torch.float32, device=dev)
@@ -750,8 +880,33 @@ def main():
             "priority": "random permutation of 1..n (seed 31)", "mis_ms": t_mis, "mis_size": int(ins.sum().item()),
             "colouring_push_ms": t_col, "colouring_max_times_rounds_ms": t_col_mt,
             "colours": int(cols.max().item()) + 1}
+    del levels
 
-    if not args.no_extras:
+    if pre is not None:
+        # config 2's permuted ids: the same step on the permuted graph
+        pn, prp, pci = pre["perm"]
+        prp_d, pci_d = torch.from_numpy(prp).to(dev), torch.from_numpy(pci).to(dev)
+        psrcs = [int(v) for v in graphs_sources(pn, prp, NSRC, 7)]
+        plev = torch.empty((NSRC, pn), dtype=torch.int32, device=dev)
+
+        def pstep():
+            step(prp_d, pci_d, x, y, plev, pr, labels, pn, psrcs)
+        pms, pfam, _, _ = timed_steps(B, pstep, args, barrier)
+        extra["step_rmat20_permuted"] = {
+            "workload": f"R-MAT scale {SCALE} ef{EDGE_FACTOR} seed {SEED}, ids permuted (seed {PERM_SEED}); "
+                        f"the same step, tile_dim {TILE}", "nnz": int(pci.size),
+            "gteps": QUERIES_PER_STEP * int(pci.size) * args.steps / (pms / 1e3) / 1e9,
+            "ms_per_step": pms / args.steps, "roofline": roofline_of(pfam, pms, peak, peak_src, TILE, SCHEDULE),
+            "kernel_breakdown_ms_per_step": {f: pfam[f]["ms"] / args.steps for f in pfam}}
+        del plev
+        # config 2's tile_dim sweep of the Boolean and plus-times SpMVs, unpermuted and permuted
+        try:
+            extra["tile_sweep"] = tile_sweep(B, dev, {"rmat20": (g.n, g.rowptr, g.colind), "rmat20_perm": (pn, prp, pci)},
+                                             xbits, peak)
+        except Exception as e:
+            extra["tile_sweep"] = {"failed": repr(e)}
+        del prp_d, pci_d
+        torch.cuda.empty_cache()
         try:
             smp = np.random.default_rng(29).integers(0, g.n, 8192).astype(np.int32)
             mt, rep = B.b2sr_autotune(g.n, rp, ci, smp, B.PLUS_TIMES, B.VEC_F32, keep_ratio=0.0, trials=5)
@@ -761,57 +916,35 @@ def main():
                                       "est_ratio": rep["est_ratio"], "used": {"tile_dim": TILE, "schedule": SCHEDULE}}
         except Exception as e:
             extra["autotune_main"] = {"failed": repr(e)}
-        import multiprocessing as mp
-        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-            rng = np.random.default_rng(23)
-            a_scales = [int(v) for v in rng.integers(ARENA_SCALES[0], ARENA_SCALES[1] + 1, ARENA_GRAPHS)]
-            grid_res = pool.apply_async(_grid_weighted)
-            tc_res = pool.apply_async(_rmat_plain, (TC_SCALE, TC_EF, 2))
-            big_res = pool.apply_async(_rmat_plain, (MS_SCALE, EDGE_FACTOR, 3))
-            arena_res = pool.starmap_async(_rmat_plain, [(sc, EDGE_FACTOR, 5000 + i) for i, sc in enumerate(a_scales)])
-            for name, fn in (("serving", lambda: serving_extra(B, dev, pool)),
-                             ("grid_sssp_and_tc", lambda: grid_tc_extra(B, dev, grid_res, tc_res)),
-                             ("batching", lambda: batching_extra(B, dev, big_res, arena_res,
-                                                                 f"{ARENA_SCALES[0]}..{ARENA_SCALES[1]} uniform, seed 23"))):
-                try:
-                    extra[name] = fn()
-                except Exception as e:  # reported, never fatal to the main line
-                    extra[name] = {"failed": repr(e)}
-
-    # ---- roofline of the dominant kernel ----
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    peak, peak_src = 6800.0, "fallback 6.8 TB/s"
-    try:
-        pk = json.load(open(peaks_path))
-        peak, peak_src = float(pk["hbm_gbs"]), "measured hbm_gbs (MEASURED_PEAKS.json)"
-    except Exception:
-        pass
-    roofline = None
-    if fam:
-        dom = max(fam, key=lambda f: fam[f]["ms"])
-        d = fam[dom]
-        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        traffic = None
-        staged_kernel = dom not in ("spmv_bool", "spmv_count") and TILE <= 16 and SCHEDULE != 2
-        kname = "spmv_gather_kernel" if staged_kernel else "spmv_chunks_kernel"
-        traffic, _ = traffic_for(dom, TILE, kname)
-        roofline = {"bound": "hbm", "kernel": f"{kname} ({dom}, k={TILE})", "achieved": achieved,
-                    "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
-                    "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
-                    "avg_launch_us": d["ms"] / d["launches"] * 1e3, "launches": d["launches"],
-                    "share_of_step": d["ms"] / ms_total,
-                    "traffic": traffic}
+        for name, fn in (("serving", lambda: serving_extra(B, dev, pre["serve"], t_gen)),
+                         ("grid_sssp_and_tc", lambda: grid_tc_extra(B, dev, pre["grid"], pre["tc"])),
+                         ("batching", lambda: batching_extra(B, dev, pre["big"], pre["arena"],
+                                                             f"{ARENA_SCALES[0]}..{ARENA_SCALES[1]} uniform, seed 23"))):
+            try:
+                extra[name] = fn()
+            except Exception as e:  # reported, never fatal to the main line
+                extra[name] = {"failed": repr(e)}
+            torch.cuda.empty_cache()
+        extra["graph_generation_s"] = t_gen
 
     cpu = None
     if not args.no_cpu_baseline:
         try:
             import oracle
             oracle.build()
-            cstep, parts, sample = oracle_step_estimate(g, srcs, xbits)
-            cpu = {"value": edges / cstep / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample,
-                   "step_s_extrapolated": cstep, "parts_s": parts}
+            cores = host_cores()
+            s_all, p_all = oracle_step(g, srcs, xbits, cores)
+            s_one, p_one = oracle_step(g, srcs, xbits, 1)
+            cpu = {"value": edges / s_all / 1e9, "unit": "GTEPS", "cores": cores, "kind": "oracle",
+                   "nproc": os.cpu_count(),
+                   "sample": (f"one whole step of the workload on the oracle (plain C) with {cores} host threads "
+                              f"(CSR->B2SR and CC on one thread, SpMV and PageRank row loops on all, the BFS "
+                              f"sources {cores} at a time), then the same step on one thread"),
+                   "step_s": s_all, "parts_s": p_all,
+                   "single_thread": {"value": edges / s_one / 1e9, "unit": "GTEPS", "cores": 1, "step_s": s_one,
+                                     "parts_s": p_one}}
         except Exception as e:  # the baseline is reported, never required
-            cpu = {"value": None, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+            cpu = {"value": None, "unit": "GTEPS", "cores": None, "kind": "oracle", "sample": f"failed: {e}"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
@@ -821,7 +954,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": e2e_ms / args.steps},
         "gpu_launches": int(launches),
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "kernel_breakdown_ms_per_step": {f: fam[f]["ms"] / args.steps for f in fam},
@@ -831,6 +964,11 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def graphs_sources(n, rowptr, count, seed):
+    from paper_2201_08560_gb300 import graphs
+    return graphs.sources(graphs.CSR(n, rowptr, np.zeros(0, np.int32)), count, seed)
 
 
 if __name__ == "__main__":

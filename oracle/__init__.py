@@ -31,7 +31,7 @@ def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so with gcc (portable flags only)."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-fopenmp", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -70,6 +70,7 @@ def _load():
                 "orc_pagerank": (ctypes.c_int, [i32, p, p, d, ctypes.c_int, p, p]),
                 "orc_cc": (ctypes.c_int, [i32, p, p, p]),
                 "orc_sample_profile": (ctypes.c_int, [i32, p, p, p, i64, p, p]),
+                "orc_set_threads": (ctypes.c_int, [ctypes.c_int]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -77,6 +78,11 @@ def _load():
                 f.argtypes = args
             _lib = lib
     return _lib
+
+
+def set_threads(threads: int = 0) -> int:
+    """Host threads for the oracle's row loops (0 keeps the current count); returns the count in force."""
+    return int(_load().orc_set_threads(int(threads)))
 
 
 def _ptr(a: Optional[np.ndarray]):

@@ -29,6 +29,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_EINVAL (-1)
@@ -49,6 +52,23 @@ static int bit_get(const uint32_t* bits, int64_t v) {
 
 static void bit_set(uint32_t* bits, int64_t v) {
     bits[v >> 5] |= (1u << (v & 31));
+}
+
+/* Host threads for the row loops below (the CPU baseline is timed on one
+ * thread and on all of them).  Each row's value is computed by one thread in
+ * the same order either way, so the results do not depend on the count;
+ * rows are dealt in blocks of ROW_BLOCK (a multiple of 32, so a bitset word
+ * is written by one thread).  Without OpenMP everything runs on one thread. */
+#define ROW_BLOCK 1024
+
+int orc_set_threads(int threads) {
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+    return omp_get_max_threads();
+#else
+    (void)threads;
+    return 1;
+#endif
 }
 
 /* mask_mode: 0 = no mask, 1 = keep where mask bit set, 2 = keep where clear */
@@ -219,6 +239,7 @@ int64_t orc_b2sr_to_csr(int32_t n, int k, const int32_t* tile_rowptr, const int3
 void orc_spmv_bool(int32_t n, const int32_t* rowptr, const int32_t* colind, const uint32_t* x,
                    uint32_t* y, const uint32_t* mask, int mask_mode) {
     memset(y, 0, (size_t)((n + 31) / 32) * sizeof(uint32_t));
+#pragma omp parallel for schedule(dynamic, ROW_BLOCK)
     for (int64_t i = 0; i < n; ++i) {
         int hit = 0;
         for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) hit |= bit_get(x, colind[e]);
@@ -230,6 +251,7 @@ void orc_spmv_bool(int32_t n, const int32_t* rowptr, const int32_t* colind, cons
  * Table 2 and the popc formula of Sec. IV): y_i = |{j in row i : x_j = 1}|. */
 void orc_spmv_count(int32_t n, const int32_t* rowptr, const int32_t* colind, const uint32_t* x,
                     int32_t* y, const uint32_t* mask, int mask_mode) {
+#pragma omp parallel for schedule(dynamic, ROW_BLOCK)
     for (int64_t i = 0; i < n; ++i) {
         int32_t c = 0;
         for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) c += bit_get(x, colind[e]);
@@ -241,6 +263,7 @@ void orc_spmv_count(int32_t n, const int32_t* rowptr, const int32_t* colind, con
  * y_i = sum_{j in row i} x_j, summed in fp64 in CSR order. */
 void orc_spmv_plus(int32_t n, const int32_t* rowptr, const int32_t* colind, const double* x,
                    double* y, const uint32_t* mask, int mask_mode) {
+#pragma omp parallel for schedule(dynamic, ROW_BLOCK)
     for (int64_t i = 0; i < n; ++i) {
         double s = 0.0;
         for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) s += x[colind[e]];
@@ -254,6 +277,7 @@ void orc_spmv_plus(int32_t n, const int32_t* rowptr, const int32_t* colind, cons
  * w == NULL means every edge weight is 1; otherwise w is in CSR order. */
 void orc_spmv_minplus(int32_t n, const int32_t* rowptr, const int32_t* colind, const double* x,
                       const float* w, double* y, const uint32_t* mask, int mask_mode) {
+#pragma omp parallel for schedule(dynamic, ROW_BLOCK)
     for (int64_t i = 0; i < n; ++i) {
         double m = x[i];
         for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
@@ -268,6 +292,7 @@ void orc_spmv_minplus(int32_t n, const int32_t* rowptr, const int32_t* colind, c
  * y_i = min(x_i, min_{j in row i} x_j). */
 void orc_spmv_min_i32(int32_t n, const int32_t* rowptr, const int32_t* colind, const int32_t* x,
                       int32_t* y, const uint32_t* mask, int mask_mode) {
+#pragma omp parallel for schedule(dynamic, ROW_BLOCK)
     for (int64_t i = 0; i < n; ++i) {
         int32_t m = x[i];
         for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
@@ -281,6 +306,7 @@ void orc_spmv_min_i32(int32_t n, const int32_t* rowptr, const int32_t* colind, c
  * or a masked-out output. */
 void orc_spmv_max(int32_t n, const int32_t* rowptr, const int32_t* colind, const double* x, double* y,
                   const uint32_t* mask, int mask_mode) {
+#pragma omp parallel for schedule(dynamic, ROW_BLOCK)
     for (int64_t i = 0; i < n; ++i) {
         double m = -INFINITY;
         for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
@@ -293,6 +319,7 @@ void orc_spmv_max(int32_t n, const int32_t* rowptr, const int32_t* colind, const
  * Y_i = OR_{j in row i} X_j, then AND with M_i (mode 1) or ~M_i (mode 2). */
 void orc_spmm_or64(int32_t n, const int32_t* rowptr, const int32_t* colind, const uint64_t* X,
                    uint64_t* Y, const uint64_t* M, int mask_mode) {
+#pragma omp parallel for schedule(dynamic, ROW_BLOCK)
     for (int64_t i = 0; i < n; ++i) {
         uint64_t acc = 0;
         for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) acc |= X[colind[e]];
@@ -588,7 +615,9 @@ int orc_pagerank(int32_t n, const int32_t* rowptr, const int32_t* colind, double
     for (int64_t e = 0; e < rowptr[n]; ++e) outdeg[colind[e]] += 1;
     for (int64_t v = 0; v < n; ++v) x[v] = 1.0 / (double)n;
     for (int t = 0; t < iters; ++t) {
+#pragma omp parallel for schedule(static)
         for (int64_t j = 0; j < n; ++j) c[j] = outdeg[j] > 0 ? x[j] / (double)outdeg[j] : 0.0;
+#pragma omp parallel for schedule(dynamic, ROW_BLOCK)
         for (int64_t i = 0; i < n; ++i) {
             double s = 0.0;
             for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) s += c[colind[e]];

@@ -663,12 +663,15 @@ struct RowCursor {
     bool head_cs;
 };
 
-__device__ __forceinline__ RowCursor locate_row(const SpmvGeom& g, int32_t c, const LaneSpan& ls, int lane) {
+// Row pointers of a chunk's tile-rows r0 .. r0+span+1 that fit one warp
+// (lane j holds rowptr[r0 + j]); the search loads any further windows itself.
+__device__ __forceinline__ int32_t row_window(const SpmvGeom& g, int32_t r0, int32_t span, int lane) {
+    return lane <= span + 1 ? __ldg(g.rowptr + r0 + lane) : INT32_MAX;
+}
+
+__device__ __forceinline__ RowCursor locate_row_win(const SpmvGeom& g, int32_t r0, int32_t span, int32_t win,
+                                                    const LaneSpan& ls, int lane) {
     constexpr unsigned FULL = 0xffffffffu;
-    const int32_t r0 = __ldg(g.chunk_row + c);
-    const int32_t r1 = __ldg(g.chunk_row + c + 1);
-    const int32_t span = r1 - r0;
-    const int32_t win = lane <= span + 1 ? __ldg(g.rowptr + r0 + lane) : INT32_MAX;
     RowCursor rc;
     rc.head_cs = __shfl_sync(FULL, win, 0) == ls.cs;
     int32_t row = r0;
@@ -707,6 +710,12 @@ __device__ __forceinline__ RowCursor locate_row(const SpmvGeom& g, int32_t c, co
     rc.row_start = d < 32 ? a0 : __ldg(g.rowptr + row);
     rc.next = d + 1 < 32 ? a1 : __ldg(g.rowptr + row + 1);
     return rc;
+}
+
+__device__ __forceinline__ RowCursor locate_row(const SpmvGeom& g, int32_t c, const LaneSpan& ls, int lane) {
+    const int32_t r0 = __ldg(g.chunk_row + c);
+    const int32_t span = __ldg(g.chunk_row + c + 1) - r0;
+    return locate_row_win(g, r0, span, row_window(g, r0, span, lane), ls, lane);
 }
 
 // Per-lane walk state: the tile-row being accumulated, where it ends, the
@@ -905,6 +914,244 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
                     }
                 }
                 wk.end_tile(g, sem, acc, F, t, i, ls.cnt, idv);
+            }
+        }
+    }
+    close_chunk(sem, part, c, ls, lane, rc.head_cs, rc.row, wk.has_end, wk.open, acc, F, P);
+}
+
+// ---------------------------------------------------------------------------
+// tile_dim-4 chunk kernel.  At k = 4 a tile is 4 bytes and holds 1.15 set
+// bits on average on R-MAT graphs (90% of the tiles hold exactly one), so the
+// kernel is shaped by the per-tile costs:
+//   * each lane reads its 8 tile words and 8 tile columns with one 32-byte
+//     load each, marked not to be kept in L1: the tile stream passes through
+//     once, and L1 stays for the input vector, whose random gathers are what
+//     bounds the value schemes (they hit L2 when they miss L1);
+//   * value schemes gather the input under every tile's first (highest) set
+//     bit before the walk, eight independent loads per lane, so a lane waits
+//     for one round trip, not one per bit;
+//   * a chunk that lies inside one tile-row (most chunks of a power-law
+//     graph) needs no row search, walk or segmented scan: its lanes add to
+//     the same k rows, joined by one fixed-order butterfly;
+//   * otherwise a tile's further bits are added in the walk by lanes where a
+//     tile-row ends; in every other lane all eight tiles belong to one
+//     tile-row, so their further bits are added in one flat loop after the
+//     walk (the tile's word and column picked from registers by a select
+//     tree).  Rows, empty rows and cross-lane and cross-chunk joins are the
+//     chunk kernel's.
+// The order of every sum is fixed by the data.
+// ---------------------------------------------------------------------------
+// the input a lane holds per tile: a value scheme's gathered value, or the
+// bit-vector schemes' k-bit segment
+template <class SEM, bool = SEM::kGather>
+struct GatherOf {
+    using type = uint32_t;
+};
+template <class SEM>
+struct GatherOf<SEM, true> {
+    using type = typename SEM::G;
+};
+
+template <class SEM>
+struct K4Shape {
+    // resident blocks of 256 threads the registers are budgeted for: the
+    // value schemes keep eight gathered values and the tile words and columns
+    // live through the walk
+    static constexpr int MIN_BLOCKS =
+        !SEM::kGather ? 5 : (sizeof(typename SEM::V) <= 4 ? 4 : (sizeof(typename SEM::V) <= 8 ? 3 : 2));
+};
+
+// 32 bytes from global memory in one load, not allocated in L1
+__device__ __forceinline__ void ld32_stream(const void* p, uint32_t (&v)[8]) {
+    asm volatile("ld.global.nc.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "l"(p));
+}
+
+// v[i] for a runtime i in [0, 8): a select tree on the bits of i, so the
+// array stays in registers
+template <class T>
+__device__ __forceinline__ T pick8(const T (&v)[8], int i) {
+    const bool b0 = i & 1, b1 = i & 2, b2 = i & 4;
+    const T a0 = b0 ? v[1] : v[0], a1 = b0 ? v[3] : v[2], a2 = b0 ? v[5] : v[4], a3 = b0 ? v[7] : v[6];
+    const T c0 = b1 ? a1 : a0, c1 = b1 ? a3 : a2;
+    return b2 ? c1 : c0;
+}
+
+// acc[r] <- acc[r] (+) v as a select on every row (no branch, so lanes with
+// different rows stay converged, and the register indices stay constant)
+template <class SEM, class A, class G>
+__device__ __forceinline__ void add_row(const SEM& sem, A& acc, int r, G v) {
+#pragma unroll
+    for (int u = 0; u < SEM::NV; ++u) {
+        const auto cur = acc.get(u);
+        const auto upd = sem.apply(cur, v, 1.0f);
+        acc.set(u, u == r ? upd : cur);
+    }
+}
+
+// highest set bit of a non-zero tile word: row p >> 3, column p & 3
+__device__ __forceinline__ int top_bit(uint32_t w) { return 31 - __clz(w); }
+
+// The bits after the first of the lane's tiles flagged in `more`, in tile
+// order and from the highest bit down, added to the rows of one tile-row in
+// a flat loop (lanes with fewer bits finish early).
+template <class SEM, class A>
+__device__ __forceinline__ void add_further_bits(const SEM& sem, A& acc, uint32_t more, const uint32_t (&w)[8],
+                                                 const uint32_t (&cu)[8]) {
+    using G = typename SEM::G;
+    uint32_t m = more, b = 0u;
+    const G* xt = sem.src();
+    while (m != 0u || b != 0u) {
+        if (b == 0u) {
+            const int i = __ffs(m) - 1;
+            m &= m - 1u;
+            const uint32_t wi = pick8(w, i);
+            b = wi ^ (1u << top_bit(wi));
+            xt = sem.src() + (int64_t)(int32_t)pick8(cu, i) * 4;
+        }
+        const int p = top_bit(b);
+        b ^= 1u << p;
+        add_row(sem, acc, p >> 3, __ldg(xt + (p & 3)));
+    }
+}
+
+template <class SEM>
+__global__ void __launch_bounds__(kSpmvThreads, K4Shape<SEM>::MIN_BLOCKS)
+    spmv_k4_kernel(SpmvGeom g, SEM sem, Partials<typename SEM::V> part) {
+    using S = ChunkShape<4>;
+    using V = typename SEM::V;
+    constexpr int NV = SEM::NV;
+    constexpr int P = S::P;
+    static_assert(P == 8 && S::TW == 1, "eight one-word tiles a lane");
+    const int warp = threadIdx.x >> 5;
+    const int lane = (int)lane_id();
+    const int32_t c = (int32_t)blockIdx.x * kSpmvWarps + warp;
+    if (c >= g.nchunks || gated_off(g.gate)) return;  // whole warps leave together
+
+    LaneSpan ls;
+    ls.cs = c * S::CT;
+    ls.ce = min(ls.cs + S::CT, (int32_t)g.T);
+    ls.tl = ls.cs + lane * P;
+    ls.cnt = max(0, min(P, ls.ce - ls.tl));
+
+    // a chunk whose every output row is masked out reads no tiles (zero words:
+    // the walk still stores its rows and partials, all the identity)
+    const int32_t ra = __ldg(g.chunk_row + c), rb = __ldg(g.chunk_row + c + 1);
+    const bool sat = sem.saturated((int64_t)ra * 4, ((int64_t)rb + 1) * 4);
+    uint32_t w[P], cu[P];
+    if (!sat) {
+        // the arrays are padded to whole chunks, so every lane's 32 bytes exist
+        ld32_stream(reinterpret_cast<const uint32_t*>(g.tiles) + ls.tl, w);
+        ld32_stream(g.colind + ls.tl, cu);
+    } else {
+#pragma unroll
+        for (int i = 0; i < P; ++i) { w[i] = 0u; cu[i] = 0u; }
+    }
+    // the inputs under the tiles (first set bits, or the bit segments): loads
+    // issued before the row search so their latency overlaps it
+    using G = typename GatherOf<SEM>::type;
+    G xv[P];
+    uint32_t rsel = 0, has = 0, more = 0;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        const bool ok = i < ls.cnt && w[i] != 0u;
+        if constexpr (SEM::kGather) {
+            const int p = ok ? top_bit(w[i]) : 0;
+            xv[i] = ok ? __ldg(sem.src() + (int64_t)(int32_t)cu[i] * 4 + (p & 3)) : G{};
+            rsel |= (uint32_t)(p >> 3) << (2 * i);
+            has |= (ok ? 1u : 0u) << i;
+            more |= (ok && (w[i] & (w[i] - 1u)) != 0u ? 1u : 0u) << i;
+        } else {
+            xv[i] = ok ? sem.xseg((int32_t)cu[i]) : 0u;
+        }
+    }
+    RegAcc<V, NV> acc, F, idv;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { acc.set(v, sem.ident()); F.set(v, sem.ident()); idv.set(v, sem.ident()); }
+
+    if (ra == rb) {
+        // The whole chunk lies in tile-row ra (warp-uniform): every lane's
+        // tiles add to the same k rows, so no row search, walk or segmented
+        // scan is needed -- one fixed-order butterfly joins the lanes.
+        const int32_t row_start = __ldg(g.rowptr + ra);
+        if (ls.cnt > 0) {
+            if constexpr (SEM::kGather) {
+#pragma unroll
+                for (int i = 0; i < P; ++i)
+                    if ((has >> i) & 1u) add_row(sem, acc, (int)((rsel >> (2 * i)) & 3u), xv[i]);
+                add_further_bits(sem, acc, more, w, cu);
+            } else {
+#pragma unroll
+                for (int i = 0; i < P; ++i)
+                    if (i < ls.cnt) sem.tile(acc, w + i, xv[i]);
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const V other = shfl_xor(acc.get(v), o);
+                acc.set(v, (lane & o) ? sem.comb(other, acc.get(v)) : sem.comb(acc.get(v), other));
+            }
+        }
+        if (lane == 0) {
+            const bool head = row_start == ls.cs;  // the row begins with this chunk
+            if (head && ls.cs > 0)                 // empty tile-rows just before it
+                for (int32_t R = ra - 1; R >= 0 && __ldg(g.rowptr + R) == ls.cs; --R) sem.store(R, idv);
+            if (head && c + 1 == g.nchunks) {
+                sem.store(ra, acc);  // begins and ends in this chunk (the matrix's last)
+            } else {
+                // continued by later chunks (head) or begun in earlier ones
+                typename SEM::V* dst = (head ? part.val_last : part.val_first) + (int64_t)c * NV;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) dst[v] = acc.get(v);
+            }
+        }
+        return;
+    }
+    const RowCursor rc = locate_row_win(g, ra, rb - ra, row_window(g, ra, rb - ra, lane), ls, lane);
+    Walk<SEM, RegAcc<V, NV>> wk;
+    wk.row = rc.row;
+    wk.next = rc.next;
+    if constexpr (SEM::kGather) {
+        // a tile-row ends inside this lane: its tiles' further bits are added in tile order
+        const bool lane_end = ls.cnt > 0 && rc.next <= ls.tl + ls.cnt;
+        if (ls.cnt > 0) {
+            // empty tile-rows just before a row that starts at this lane's first tile
+            if (ls.tl > 0 && rc.row_start == ls.tl)
+                for (int32_t R = rc.row - 1; R >= 0 && __ldg(g.rowptr + R) == ls.tl; --R) sem.store(R, idv);
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                if (i < ls.cnt) {
+                    if ((has >> i) & 1u) add_row(sem, acc, (int)((rsel >> (2 * i)) & 3u), xv[i]);
+                    if (lane_end && ((more >> i) & 1u)) {
+                        const G* xt = sem.src() + (int64_t)(int32_t)cu[i] * 4;
+                        uint32_t b = w[i] ^ (1u << top_bit(w[i]));
+                        while (b) {
+                            const int p = top_bit(b);
+                            b ^= 1u << p;
+                            add_row(sem, acc, p >> 3, __ldg(xt + (p & 3)));
+                        }
+                    }
+                    wk.end_tile(g, sem, acc, F, ls.tl + i, i, ls.cnt, idv);
+                }
+            }
+            // every tile of such a lane is in one tile-row: the further bits of all its
+            // tiles in one flat loop
+            if (!lane_end) add_further_bits(sem, acc, more, w, cu);
+        }
+    } else {
+        if (ls.cnt > 0) {
+            if (ls.tl > 0 && rc.row_start == ls.tl)
+                for (int32_t R = rc.row - 1; R >= 0 && __ldg(g.rowptr + R) == ls.tl; --R) sem.store(R, idv);
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                if (i < ls.cnt) {
+                    sem.tile(acc, w + i, xv[i]);
+                    wk.end_tile(g, sem, acc, F, ls.tl + i, i, ls.cnt, idv);
+                }
             }
         }
     }
@@ -1340,6 +1587,40 @@ static double spmv_bytes(const b2sr_matrix* h, double vec_bytes) {
     return 4.0 * ((double)h->ntr + 1.0) + (double)h->T * (4.0 + tile_bytes(h->k)) + vec_bytes;
 }
 
+// The tile_dim-4 kernel serves k = 4: the bit-vector schemes always, the
+// value schemes under the direct schedule (the staged schedule keeps its own
+// kernel, so each schedule sums in one fixed order) when no weight side array
+// is given.
+template <int K, class SEM>
+static bool use_k4(const b2sr_matrix* h, const SEM& sem) {
+    if constexpr (K != 4) {
+        return false;
+    } else {
+        if constexpr (SEM::kGather) {
+            if (sem.weighted || h->schedule != B2SR_SCHED_DIRECT) return false;
+        }
+        return true;
+    }
+}
+
+// The direct chunk kernel: the tile_dim-4 one where it serves, else the
+// general one.
+template <int K, class SEM>
+static b2sr_status launch_direct(const b2sr_matrix* h, const SEM& sem, Partials<typename SEM::V> part,
+                                 cudaStream_t s, const SpmvGeom& g) {
+    const unsigned blocks = (unsigned)ceil_div(h->nchunks, kSpmvWarps);
+    if constexpr (K == 4) {
+        if (use_k4<K>(h, sem)) {
+            spmv_k4_kernel<SEM><<<blocks, kSpmvThreads, 0, s>>>(g, sem, part);
+            B2SR_LAUNCH_CHECK("spmv_k4_kernel");
+            return B2SR_OK;
+        }
+    }
+    spmv_chunks_kernel<K, SEM><<<blocks, kSpmvThreads, 0, s>>>(g, sem, part);
+    B2SR_LAUNCH_CHECK("spmv_chunks_kernel");
+    return B2SR_OK;
+}
+
 // the chunk kernel (staged or direct) and the cross-chunk join
 template <int K, class SEM>
 static b2sr_status run_chunks(const b2sr_matrix* h, const SEM& sem, cudaStream_t s, const char* family,
@@ -1362,9 +1643,9 @@ static b2sr_status run_chunks(const b2sr_matrix* h, const SEM& sem, cudaStream_t
     }
     if (!staged) {
         void* tok = timing_begin(s);
-        spmv_chunks_kernel<K, SEM><<<blocks, kSpmvThreads, 0, s>>>(g, sem, part);
+        const b2sr_status st = launch_direct<K, SEM>(h, sem, part, s, g);
         timing_end(tok, family, spmv_bytes(h, vec_bytes), s);
-        B2SR_LAUNCH_CHECK("spmv_chunks_kernel");
+        B2SR_TRY(st);
     }
     return launch_fixup<K, SEM>(h, sem, part, s, gate);
 }
@@ -1566,8 +1847,7 @@ static b2sr_status run_spmv_bool_fixed(const b2sr_matrix* h, const SemBool<K>& s
     Partials<uint32_t> part;
     part.val_first = static_cast<uint32_t*>(scratch);
     part.val_last = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(scratch) + half);
-    spmv_chunks_kernel<K, SEM><<<(unsigned)ceil_div(h->nchunks, kSpmvWarps), kSpmvThreads, 0, s>>>(g, sem, part);
-    B2SR_LAUNCH_CHECK("spmv_chunks_kernel");
+    B2SR_TRY((launch_direct<K, SEM>(h, sem, part, s, g)));
     return launch_fixup<K, SEM>(h, sem, part, s, nullptr);
 }
 

@@ -79,3 +79,4 @@ def test_host_side_errors_without_gpu(lib):
         f.restype = ctypes.c_int
         assert f(*args) == 1, name  # INVALID_ARG: not a handle
     assert lib.b2sr_transpose(None, None, None) == 1  # out is NULL
+

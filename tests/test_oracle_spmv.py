@@ -98,3 +98,25 @@ def test_or64(n, density, seed, mode):
     if M is not None:
         expect = expect & (~M if mode else M)
     np.testing.assert_array_equal(oracle.spmm_or64(g, X, M, bool(mode)), expect)
+
+
+def test_row_loops_do_not_depend_on_thread_count():
+    """The oracle's row loops run on any number of host threads (the CPU
+    baseline is timed on one and on all); every row is still computed by one
+    thread in CSR order, so each result is identical, bit for bit."""
+    from paper_2201_08560_gb300 import graphs
+    g = graphs.rmat(13, 16, seed=4)
+    xb = graphs.random_bits(g.n, 0.1, seed=1)
+    xf = np.random.default_rng(2).random(g.n)
+    mask = graphs.random_bits(g.n, 0.5, seed=3)
+    prev = oracle.set_threads(0)
+    try:
+        out = []
+        for t in (1, max(2, prev)):
+            oracle.set_threads(t)
+            out.append([oracle.spmv_bool(g, xb, mask, True), oracle.spmv_count(g, xb), oracle.spmv_plus(g, xf),
+                        oracle.spmv_minplus(g, xf), oracle.spmv_max(g, xf), oracle.pagerank(g, 0.85, 5)])
+        for a, b in zip(*out):
+            np.testing.assert_array_equal(a, b)
+    finally:
+        oracle.set_threads(prev)
