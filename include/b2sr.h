@@ -305,11 +305,18 @@ b2sr_status b2sr_spmm_f32x4(b2sr_handle h, const float* X, float* Y, const uint3
  * Computes exactly what b2sr_spmv computes for BOOL_OR_AND, BITS -> BITS
  * (same x, y, mask and mask_complement meaning), but keeps its scratch (the
  * partial rows of tile-rows that cross chunks) in a fixed 4 MiB array compiled
- * into the library, which every device that loads the library holds until the
- * process exits.  It calls no cudaMalloc, cudaFree or allocating routine.
- *  - The first call on each device looks up that device's copy of the array
- *    (cudaGetSymbolAddress) with the device current; make that first call
- *    before any stream capture.
+ * into the library.  It calls no cudaMalloc, cudaFree or allocating routine.
+ *  - A device gets its copy of the array when the CUDA runtime loads the
+ *    library's SpMV code on it: with lazy module loading (the default since
+ *    CUDA 12.2) that is the first SpMV launch or the first call of this
+ *    function on that device, and the copy stays until the process exits or
+ *    the device is reset.  Make the first call on each device (or any earlier
+ *    b2sr_spmv on it) before the caller reserves the device's free memory and
+ *    before any stream capture.  That call also looks the copy's address up
+ *    (cudaGetSymbolAddress) with the device current; the address is kept for
+ *    the process, so do not call this function after cudaDeviceReset.
+ *  - h must belong to the current device (else B2SR_ERR_INVALID_ARG): each
+ *    device's call uses that device's copy.
  *  - Matrices needing more scratch than the array holds (more than 262,144
  *    chunks at k=8, or 524,288 at k=4/16/32; a chunk is 256 tiles at k=4/8,
  *    128 at k=16, 64 at k=32) are rejected

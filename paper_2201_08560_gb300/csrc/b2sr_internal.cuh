@@ -164,6 +164,10 @@ b2sr_status check_handle(const b2sr_matrix* h);
 b2sr_status ensure_voff(b2sr_matrix* h, cudaStream_t s);
 b2sr_status ensure_outdeg(b2sr_matrix* h, cudaStream_t s);
 b2sr_status build_schedule(b2sr_matrix* h, cudaStream_t s);
+// Sets *bad (device memory) non-zero if rowptr[0] != 0, rowptr[n] != nnz, a
+// row pointer decreases or a column lies outside [0, n); stream-ordered.
+b2sr_status validate_csr_async(int32_t n, const int32_t* rowptr, const int32_t* colind, int64_t nnz, int* bad,
+                               cudaStream_t s);
 b2sr_status new_handle_from_tiles(int32_t n, int k, int64_t T, int32_t* rowptr, int32_t* colind,
                                   uint8_t* tiles, int64_t cap, cudaStream_t s, b2sr_matrix** out);
 

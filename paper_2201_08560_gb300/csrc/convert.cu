@@ -34,6 +34,14 @@ __global__ void validate_csr_kernel(int32_t n, const int32_t* __restrict__ rowpt
     }
 }
 
+// Sets *bad (device) non-zero if the CSR is malformed; stream-ordered, no sync.
+b2sr_status validate_csr_async(int32_t n, const int32_t* rowptr, const int32_t* colind, int64_t nnz, int* bad,
+                               cudaStream_t s) {
+    validate_csr_kernel<<<grid_wide(std::max<int64_t>(n, nnz)), 256, 0, s>>>(n, rowptr, colind, nnz, bad);
+    B2SR_LAUNCH_CHECK("validate_csr_kernel");
+    return B2SR_OK;
+}
+
 // ---------------------------------------------------------------------------
 // keys
 // ---------------------------------------------------------------------------
@@ -512,8 +520,7 @@ extern "C" b2sr_status b2sr_from_csr(int32_t n, const int32_t* rowptr, const int
         DevBuf bad(s);
         B2SR_TRY(bad.alloc(sizeof(int)));
         B2SR_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
-        validate_csr_kernel<<<grid_wide(std::max<int64_t>(n, nnz)), 256, 0, s>>>(n, rowptr, colind, nnz, bad.as<int>());
-        B2SR_LAUNCH_CHECK("validate_csr_kernel");
+        B2SR_TRY(validate_csr_async(n, rowptr, colind, nnz, bad.as<int>(), s));
         int hbad = 0;
         B2SR_CUDA_TRY(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         B2SR_CUDA_TRY(cudaStreamSynchronize(s));

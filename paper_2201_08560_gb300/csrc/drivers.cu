@@ -477,6 +477,20 @@ extern "C" b2sr_status b2sr_from_csr_batch(int ngraphs, const int32_t* n_host, c
     }
     base_host[ngraphs] = N;
     if (N >= (int64_t(1) << 31) || NNZ >= (int64_t(1) << 31)) return fail(B2SR_ERR_INVALID_ARG, "arena too large");
+    // every graph's own CSR is checked before it is shifted into the arena: a
+    // column outside [0, n_g) would otherwise land in a neighbouring graph
+    {
+        DevBuf bad(s);
+        B2SR_TRY(bad.alloc((size_t)ngraphs * sizeof(int)));
+        B2SR_CUDA_TRY(cudaMemsetAsync(bad.p, 0, (size_t)ngraphs * sizeof(int), s));
+        for (int g = 0; g < ngraphs; ++g)
+            B2SR_TRY(validate_csr_async(n_host[g], rowptrs[g], colinds[g], nnz_host[g], bad.as<int>() + g, s));
+        std::vector<int> hbad((size_t)ngraphs);
+        B2SR_CUDA_TRY(cudaMemcpyAsync(hbad.data(), bad.p, (size_t)ngraphs * sizeof(int), cudaMemcpyDeviceToHost, s));
+        B2SR_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int g = 0; g < ngraphs; ++g)
+            if (hbad[g]) return fail(B2SR_ERR_INVALID_ARG, "malformed CSR in graph " + std::to_string(g));
+    }
     DevBuf rp(s), ci(s);
     B2SR_TRY(rp.alloc((N + 1) * sizeof(int32_t)));
     B2SR_TRY(ci.alloc(std::max<int64_t>(NNZ, 1) * sizeof(int32_t)));

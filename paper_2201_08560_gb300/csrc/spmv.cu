@@ -921,46 +921,21 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
 }
 
 // ---------------------------------------------------------------------------
-// tile_dim-4 chunk kernel.  At k = 4 a tile is 4 bytes and holds 1.15 set
-// bits on average on R-MAT graphs (90% of the tiles hold exactly one), so the
-// kernel is shaped by the per-tile costs:
-//   * each lane reads its 8 tile words and 8 tile columns with one 32-byte
-//     load each, marked not to be kept in L1: the tile stream passes through
-//     once, and L1 stays for the input vector, whose random gathers are what
-//     bounds the value schemes (they hit L2 when they miss L1);
-//   * value schemes gather the input under every tile's first (highest) set
-//     bit before the walk, eight independent loads per lane, so a lane waits
-//     for one round trip, not one per bit;
-//   * a chunk that lies inside one tile-row (most chunks of a power-law
-//     graph) needs no row search, walk or segmented scan: its lanes add to
-//     the same k rows, joined by one fixed-order butterfly;
-//   * otherwise a tile's further bits are added in the walk by lanes where a
-//     tile-row ends; in every other lane all eight tiles belong to one
-//     tile-row, so their further bits are added in one flat loop after the
-//     walk (the tile's word and column picked from registers by a select
-//     tree).  Rows, empty rows and cross-lane and cross-chunk joins are the
-//     chunk kernel's.
-// The order of every sum is fixed by the data.
+// tile_dim-4 chunk kernel for the bit-vector schemes (Boolean and count
+// SpMVs).  At k = 4 a tile is 4 bytes, so the tile stream is tiny per tile and
+// the kernel is shaped by per-tile latency:
+//   * persistent warps: warp gw takes chunks gw, gw + W, ... and loads the
+//     next chunk's tile stream (8 tile words and 8 tile columns a lane, one
+//     32-byte load each, marked not to be kept in L1, plus the chunk's row
+//     pointers) into registers before it works on the current one, so every
+//     warp keeps a chunk in flight;
+//   * a chunk inside one tile-row (most chunks of a power-law graph) needs no
+//     row search, walk or segmented scan: one fixed-order butterfly joins the
+//     lanes; other chunks take the chunk kernel's walk and joins.
 // ---------------------------------------------------------------------------
-// the input a lane holds per tile: a value scheme's gathered value, or the
-// bit-vector schemes' k-bit segment
-template <class SEM, bool = SEM::kGather>
-struct GatherOf {
-    using type = uint32_t;
-};
-template <class SEM>
-struct GatherOf<SEM, true> {
-    using type = typename SEM::G;
-};
-
-template <class SEM>
-struct K4Shape {
-    // resident blocks of 256 threads the registers are budgeted for: the
-    // value schemes keep eight gathered values and the tile words and columns
-    // live through the walk
-    static constexpr int MIN_BLOCKS =
-        !SEM::kGather ? 5 : (sizeof(typename SEM::V) <= 4 ? 4 : (sizeof(typename SEM::V) <= 8 ? 3 : 2));
-};
+// resident 256-thread blocks the registers are budgeted for (every lane holds
+// two chunks' tile words and columns)
+constexpr int kK4MinBlocks = 4;
 
 // 32 bytes from global memory in one load, not allocated in L1
 __device__ __forceinline__ void ld32_stream(const void* p, uint32_t (&v)[8]) {
@@ -969,103 +944,56 @@ __device__ __forceinline__ void ld32_stream(const void* p, uint32_t (&v)[8]) {
                  : "l"(p));
 }
 
-// v[i] for a runtime i in [0, 8): a select tree on the bits of i, so the
-// array stays in registers
-template <class T>
-__device__ __forceinline__ T pick8(const T (&v)[8], int i) {
-    const bool b0 = i & 1, b1 = i & 2, b2 = i & 4;
-    const T a0 = b0 ? v[1] : v[0], a1 = b0 ? v[3] : v[2], a2 = b0 ? v[5] : v[4], a3 = b0 ? v[7] : v[6];
-    const T c0 = b1 ? a1 : a0, c1 = b1 ? a3 : a2;
-    return b2 ? c1 : c0;
-}
-
-// acc[r] <- acc[r] (+) v as a select on every row (no branch, so lanes with
-// different rows stay converged, and the register indices stay constant)
-template <class SEM, class A, class G>
-__device__ __forceinline__ void add_row(const SEM& sem, A& acc, int r, G v) {
-#pragma unroll
-    for (int u = 0; u < SEM::NV; ++u) {
-        const auto cur = acc.get(u);
-        const auto upd = sem.apply(cur, v, 1.0f);
-        acc.set(u, u == r ? upd : cur);
-    }
-}
-
-// highest set bit of a non-zero tile word: row p >> 3, column p & 3
-__device__ __forceinline__ int top_bit(uint32_t w) { return 31 - __clz(w); }
-
-// The bits after the first of the lane's tiles flagged in `more`, in tile
-// order and from the highest bit down, added to the rows of one tile-row in
-// a flat loop (lanes with fewer bits finish early).
-template <class SEM, class A>
-__device__ __forceinline__ void add_further_bits(const SEM& sem, A& acc, uint32_t more, const uint32_t (&w)[8],
-                                                 const uint32_t (&cu)[8]) {
-    using G = typename SEM::G;
-    uint32_t m = more, b = 0u;
-    const G* xt = sem.src();
-    while (m != 0u || b != 0u) {
-        if (b == 0u) {
-            const int i = __ffs(m) - 1;
-            m &= m - 1u;
-            const uint32_t wi = pick8(w, i);
-            b = wi ^ (1u << top_bit(wi));
-            xt = sem.src() + (int64_t)(int32_t)pick8(cu, i) * 4;
-        }
-        const int p = top_bit(b);
-        b ^= 1u << p;
-        add_row(sem, acc, p >> 3, __ldg(xt + (p & 3)));
-    }
-}
+// The tile stream of one chunk as a lane holds it: the chunk's first and last
+// tile-rows and their row pointers (lane j: rowptr[ra + j]), whether every
+// output row of it is masked out (then no tiles are read and the words are
+// zero: the walk still stores its rows and partials, all the identity), and
+// the lane's 8 tile words and columns.
+struct K4Tiles {
+    int32_t ra, rb;
+    int32_t win;
+    bool sat;
+    uint32_t w[8], cu[8];
+};
 
 template <class SEM>
-__global__ void __launch_bounds__(kSpmvThreads, K4Shape<SEM>::MIN_BLOCKS)
-    spmv_k4_kernel(SpmvGeom g, SEM sem, Partials<typename SEM::V> part) {
+__device__ __forceinline__ void k4_load(const SpmvGeom& g, const SEM& sem, int32_t c, int lane, K4Tiles& t) {
+    t.ra = __ldg(g.chunk_row + c);
+    t.rb = __ldg(g.chunk_row + c + 1);
+    t.win = row_window(g, t.ra, t.rb - t.ra, lane);
+    t.sat = sem.saturated((int64_t)t.ra * 4, ((int64_t)t.rb + 1) * 4);
+    if (!t.sat) {
+        // the arrays are padded to whole chunks, so every lane's 32 bytes exist
+        const int64_t tl = (int64_t)c * chunk_tiles(4) + lane * 8;
+        ld32_stream(reinterpret_cast<const uint32_t*>(g.tiles) + tl, t.w);
+        ld32_stream(g.colind + tl, t.cu);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { t.w[i] = 0u; t.cu[i] = 0u; }
+    }
+}
+
+// One chunk from its loaded tile stream.
+template <class SEM>
+__device__ __forceinline__ void k4_chunk(const SpmvGeom& g, const SEM& sem, Partials<typename SEM::V> part, int32_t c,
+                                         int lane, const K4Tiles& t) {
     using S = ChunkShape<4>;
     using V = typename SEM::V;
     constexpr int NV = SEM::NV;
     constexpr int P = S::P;
-    static_assert(P == 8 && S::TW == 1, "eight one-word tiles a lane");
-    const int warp = threadIdx.x >> 5;
-    const int lane = (int)lane_id();
-    const int32_t c = (int32_t)blockIdx.x * kSpmvWarps + warp;
-    if (c >= g.nchunks || gated_off(g.gate)) return;  // whole warps leave together
-
+    static_assert(P == 8 && S::TW == 1 && !SEM::kGather, "eight one-word tiles a lane, bit-vector schemes");
     LaneSpan ls;
     ls.cs = c * S::CT;
     ls.ce = min(ls.cs + S::CT, (int32_t)g.T);
     ls.tl = ls.cs + lane * P;
     ls.cnt = max(0, min(P, ls.ce - ls.tl));
-
-    // a chunk whose every output row is masked out reads no tiles (zero words:
-    // the walk still stores its rows and partials, all the identity)
-    const int32_t ra = __ldg(g.chunk_row + c), rb = __ldg(g.chunk_row + c + 1);
-    const bool sat = sem.saturated((int64_t)ra * 4, ((int64_t)rb + 1) * 4);
-    uint32_t w[P], cu[P];
-    if (!sat) {
-        // the arrays are padded to whole chunks, so every lane's 32 bytes exist
-        ld32_stream(reinterpret_cast<const uint32_t*>(g.tiles) + ls.tl, w);
-        ld32_stream(g.colind + ls.tl, cu);
-    } else {
-#pragma unroll
-        for (int i = 0; i < P; ++i) { w[i] = 0u; cu[i] = 0u; }
-    }
-    // the inputs under the tiles (first set bits, or the bit segments): loads
-    // issued before the row search so their latency overlaps it
-    using G = typename GatherOf<SEM>::type;
-    G xv[P];
-    uint32_t rsel = 0, has = 0, more = 0;
+    const int32_t ra = t.ra, rb = t.rb;
+    // the 4-bit input segment under each tile
+    uint32_t xs[P];
 #pragma unroll
     for (int i = 0; i < P; ++i) {
-        const bool ok = i < ls.cnt && w[i] != 0u;
-        if constexpr (SEM::kGather) {
-            const int p = ok ? top_bit(w[i]) : 0;
-            xv[i] = ok ? __ldg(sem.src() + (int64_t)(int32_t)cu[i] * 4 + (p & 3)) : G{};
-            rsel |= (uint32_t)(p >> 3) << (2 * i);
-            has |= (ok ? 1u : 0u) << i;
-            more |= (ok && (w[i] & (w[i] - 1u)) != 0u ? 1u : 0u) << i;
-        } else {
-            xv[i] = ok ? sem.xseg((int32_t)cu[i]) : 0u;
-        }
+        const bool ok = i < ls.cnt && t.w[i] != 0u;
+        xs[i] = ok ? sem.xseg((int32_t)t.cu[i]) : 0u;
     }
     RegAcc<V, NV> acc, F, idv;
 #pragma unroll
@@ -1075,19 +1003,10 @@ __global__ void __launch_bounds__(kSpmvThreads, K4Shape<SEM>::MIN_BLOCKS)
         // The whole chunk lies in tile-row ra (warp-uniform): every lane's
         // tiles add to the same k rows, so no row search, walk or segmented
         // scan is needed -- one fixed-order butterfly joins the lanes.
-        const int32_t row_start = __ldg(g.rowptr + ra);
-        if (ls.cnt > 0) {
-            if constexpr (SEM::kGather) {
+        const int32_t row_start = __shfl_sync(0xffffffffu, t.win, 0);
 #pragma unroll
-                for (int i = 0; i < P; ++i)
-                    if ((has >> i) & 1u) add_row(sem, acc, (int)((rsel >> (2 * i)) & 3u), xv[i]);
-                add_further_bits(sem, acc, more, w, cu);
-            } else {
-#pragma unroll
-                for (int i = 0; i < P; ++i)
-                    if (i < ls.cnt) sem.tile(acc, w + i, xv[i]);
-            }
-        }
+        for (int i = 0; i < P; ++i)
+            if (i < ls.cnt) sem.tile(acc, t.w + i, xs[i]);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
 #pragma unroll
@@ -1104,58 +1023,50 @@ __global__ void __launch_bounds__(kSpmvThreads, K4Shape<SEM>::MIN_BLOCKS)
                 sem.store(ra, acc);  // begins and ends in this chunk (the matrix's last)
             } else {
                 // continued by later chunks (head) or begun in earlier ones
-                typename SEM::V* dst = (head ? part.val_last : part.val_first) + (int64_t)c * NV;
+                V* dst = (head ? part.val_last : part.val_first) + (int64_t)c * NV;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) dst[v] = acc.get(v);
             }
         }
         return;
     }
-    const RowCursor rc = locate_row_win(g, ra, rb - ra, row_window(g, ra, rb - ra, lane), ls, lane);
+    const RowCursor rc = locate_row_win(g, ra, rb - ra, t.win, ls, lane);
     Walk<SEM, RegAcc<V, NV>> wk;
     wk.row = rc.row;
     wk.next = rc.next;
-    if constexpr (SEM::kGather) {
-        // a tile-row ends inside this lane: its tiles' further bits are added in tile order
-        const bool lane_end = ls.cnt > 0 && rc.next <= ls.tl + ls.cnt;
-        if (ls.cnt > 0) {
-            // empty tile-rows just before a row that starts at this lane's first tile
-            if (ls.tl > 0 && rc.row_start == ls.tl)
-                for (int32_t R = rc.row - 1; R >= 0 && __ldg(g.rowptr + R) == ls.tl; --R) sem.store(R, idv);
+    if (ls.cnt > 0) {
+        // empty tile-rows just before a row that starts at this lane's first tile
+        if (ls.tl > 0 && rc.row_start == ls.tl)
+            for (int32_t R = rc.row - 1; R >= 0 && __ldg(g.rowptr + R) == ls.tl; --R) sem.store(R, idv);
 #pragma unroll
-            for (int i = 0; i < P; ++i) {
-                if (i < ls.cnt) {
-                    if ((has >> i) & 1u) add_row(sem, acc, (int)((rsel >> (2 * i)) & 3u), xv[i]);
-                    if (lane_end && ((more >> i) & 1u)) {
-                        const G* xt = sem.src() + (int64_t)(int32_t)cu[i] * 4;
-                        uint32_t b = w[i] ^ (1u << top_bit(w[i]));
-                        while (b) {
-                            const int p = top_bit(b);
-                            b ^= 1u << p;
-                            add_row(sem, acc, p >> 3, __ldg(xt + (p & 3)));
-                        }
-                    }
-                    wk.end_tile(g, sem, acc, F, ls.tl + i, i, ls.cnt, idv);
-                }
-            }
-            // every tile of such a lane is in one tile-row: the further bits of all its
-            // tiles in one flat loop
-            if (!lane_end) add_further_bits(sem, acc, more, w, cu);
-        }
-    } else {
-        if (ls.cnt > 0) {
-            if (ls.tl > 0 && rc.row_start == ls.tl)
-                for (int32_t R = rc.row - 1; R >= 0 && __ldg(g.rowptr + R) == ls.tl; --R) sem.store(R, idv);
-#pragma unroll
-            for (int i = 0; i < P; ++i) {
-                if (i < ls.cnt) {
-                    sem.tile(acc, w + i, xv[i]);
-                    wk.end_tile(g, sem, acc, F, ls.tl + i, i, ls.cnt, idv);
-                }
+        for (int i = 0; i < P; ++i) {
+            if (i < ls.cnt) {
+                sem.tile(acc, t.w + i, xs[i]);
+                wk.end_tile(g, sem, acc, F, ls.tl + i, i, ls.cnt, idv);
             }
         }
     }
     close_chunk(sem, part, c, ls, lane, rc.head_cs, rc.row, wk.has_end, wk.open, acc, F, P);
+}
+
+template <class SEM>
+__global__ void __launch_bounds__(kSpmvThreads, kK4MinBlocks)
+    spmv_k4_kernel(SpmvGeom g, SEM sem, Partials<typename SEM::V> part) {
+    const int lane = (int)lane_id();
+    const int32_t W = (int32_t)gridDim.x * kSpmvWarps;
+    int32_t c = (int32_t)blockIdx.x * kSpmvWarps + (threadIdx.x >> 5);
+    if (c >= g.nchunks || gated_off(g.gate)) return;  // whole warps leave together
+    K4Tiles cur, nxt;
+    k4_load(g, sem, c, lane, cur);
+    for (;;) {
+        const int32_t cn = c + W;
+        const bool more = cn < g.nchunks;
+        if (more) k4_load(g, sem, cn, lane, nxt);
+        k4_chunk(g, sem, part, c, lane, cur);
+        if (!more) break;
+        c = cn;
+        cur = nxt;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1587,21 +1498,9 @@ static double spmv_bytes(const b2sr_matrix* h, double vec_bytes) {
     return 4.0 * ((double)h->ntr + 1.0) + (double)h->T * (4.0 + tile_bytes(h->k)) + vec_bytes;
 }
 
-// The tile_dim-4 kernel serves k = 4: the bit-vector schemes always, the
-// value schemes under the direct schedule (the staged schedule keeps its own
-// kernel, so each schedule sums in one fixed order) when no weight side array
-// is given.
+// The tile_dim-4 kernel serves the bit-vector schemes at k = 4.
 template <int K, class SEM>
-static bool use_k4(const b2sr_matrix* h, const SEM& sem) {
-    if constexpr (K != 4) {
-        return false;
-    } else {
-        if constexpr (SEM::kGather) {
-            if (sem.weighted || h->schedule != B2SR_SCHED_DIRECT) return false;
-        }
-        return true;
-    }
-}
+constexpr bool use_k4() { return K == 4 && !SEM::kGather; }
 
 // The direct chunk kernel: the tile_dim-4 one where it serves, else the
 // general one.
@@ -1609,15 +1508,15 @@ template <int K, class SEM>
 static b2sr_status launch_direct(const b2sr_matrix* h, const SEM& sem, Partials<typename SEM::V> part,
                                  cudaStream_t s, const SpmvGeom& g) {
     const unsigned blocks = (unsigned)ceil_div(h->nchunks, kSpmvWarps);
-    if constexpr (K == 4) {
-        if (use_k4<K>(h, sem)) {
-            spmv_k4_kernel<SEM><<<blocks, kSpmvThreads, 0, s>>>(g, sem, part);
-            B2SR_LAUNCH_CHECK("spmv_k4_kernel");
-            return B2SR_OK;
-        }
+    if constexpr (use_k4<K, SEM>()) {
+        // persistent: the resident blocks, each warp looping over chunks
+        const unsigned grid = (unsigned)std::min<int64_t>(blocks, (int64_t)sm_count() * kK4MinBlocks);
+        spmv_k4_kernel<SEM><<<grid, kSpmvThreads, 0, s>>>(g, sem, part);
+        B2SR_LAUNCH_CHECK("spmv_k4_kernel");
+    } else {
+        spmv_chunks_kernel<K, SEM><<<blocks, kSpmvThreads, 0, s>>>(g, sem, part);
+        B2SR_LAUNCH_CHECK("spmv_chunks_kernel");
     }
-    spmv_chunks_kernel<K, SEM><<<blocks, kSpmvThreads, 0, s>>>(g, sem, part);
-    B2SR_LAUNCH_CHECK("spmv_chunks_kernel");
     return B2SR_OK;
 }
 
@@ -1796,8 +1695,10 @@ extern "C" b2sr_status b2sr_spmm_bits64(b2sr_handle h, const uint64_t* X, uint64
 // or a deployment that must not allocate once it is running (fixed-memory or
 // real-time services).  For them b2sr_spmv_bool_noalloc keeps the only scratch
 // the Boolean SpMV needs -- the per-chunk partial rows joined by the fixup
-// kernel -- in a fixed array compiled into the library.  That array exists on
-// every device that loads the library, for the life of the process.
+// kernel -- in a fixed array compiled into this file.  A device holds its copy
+// from the moment the runtime loads this file's device code on it (the first
+// SpMV launch or symbol lookup there, under lazy module loading) until the
+// process exits or the device is reset.
 // ---------------------------------------------------------------------------
 namespace b2sr {
 
@@ -1861,6 +1762,9 @@ extern "C" b2sr_status b2sr_spmv_bool_noalloc(b2sr_handle h, const uint32_t* x, 
     if (x == y) return fail(B2SR_ERR_INVALID_ARG, "y must not alias x");
     int dev = 0;
     B2SR_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != h->device)
+        return fail(B2SR_ERR_INVALID_ARG, "the handle belongs to device " + std::to_string(h->device) +
+                                              ", the current device is " + std::to_string(dev));
     b2sr_status st = B2SR_OK;
     void* scratch = noalloc_scratch_ptr(dev, &st);
     if (!scratch) return st;

@@ -167,3 +167,46 @@ def test_launches_counted_per_replay(B):
         B.b2sr_bfs(m2, 0)
         long = B.b2sr_launch_count() - l0
     assert long > 5 * short > 0
+
+
+def test_arena_rejects_a_malformed_graph(B):
+    """Each graph's own CSR is validated before it is shifted into the arena,
+    so a column outside [0, n_g) is refused instead of becoming an edge into
+    the next graph: a column equal to n_1 in graph 1, a negative column in
+    graph 2, a last row pointer that disagrees with nnz, and a column in a
+    graph with no vertices.  The error names the graph."""
+    good = [graphs.path(40), graphs.cycle(33), graphs.star(50)]
+
+    def build(mutate):
+        csrs = []
+        for i, g in enumerate(good):
+            rp, ci = g.rowptr.copy(), g.colind.copy()
+            rp, ci, n = mutate(i, rp, ci, g.n)
+            csrs.append((n, torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda()))
+        return B.b2sr_from_csr_batch(csrs, 8)
+
+    def col_eq_n(i, rp, ci, n):
+        if i == 1:
+            ci[0] = n
+        return rp, ci, n
+
+    def negative(i, rp, ci, n):
+        if i == 2:
+            ci[-1] = -1
+        return rp, ci, n
+
+    def short_rowptr(i, rp, ci, n):
+        if i == 1:
+            rp[-1] -= 1
+        return rp, ci, n
+
+    def empty_with_col(i, rp, ci, n):
+        if i == 0:
+            return np.zeros(1, np.int32), np.array([0], np.int32), 0
+        return rp, ci, n
+
+    for mutate, gi in ((col_eq_n, 1), (negative, 2), (short_rowptr, 1), (empty_with_col, 0)):
+        with pytest.raises(B.B2SRError, match=f"graph {gi}"):
+            build(mutate)
+    m, bases = build(lambda i, rp, ci, n: (rp, ci, n))   # the unmodified graphs still pack
+    m.close()

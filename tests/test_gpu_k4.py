@@ -1,17 +1,16 @@
-"""GPU parity of the tile_dim-4 SpMV kernel: every scheme it serves, against
-the oracle, on graphs with the tile patterns the kernel treats apart.
+"""GPU parity at tile_dim 4, where the Boolean and count SpMVs run on their
+own persistent kernel (each warp prefetches its next chunk's tiles; a chunk
+inside one tile-row is joined by a butterfly instead of the row walk) and the
+value schemes on the general chunk kernel.
 
-The kernel gathers the input under each tile's first set bit before its
-walk and adds the other bits either in the walk (lanes where a tile-row
-ends) or in one flat loop afterwards (lanes whose tiles all lie in one
-tile-row).  The graphs exercise each case: dense tiles (all sixteen bits set,
-so most bits are further bits), short tile-rows of multi-bit tiles (further
-bits added inside the walk), one row spanning many chunks (the cross-chunk
-join), empty rows, a ragged n, and a masked level loop's all-masked chunks.
-Bit-exact for Boolean, integer, min, max and OR results; plus-times within
-1e-5 relative error of the fp64 oracle (the bound derived in
-test_gpu_spmv.py), and bitwise reproducible from call to call.  The four-column
-PageRank block sums each column exactly like the single-column SpMV."""
+Every scheme is compared with the oracle on graphs with the tile patterns the
+kernels treat apart: dense tiles (all sixteen bits set), short tile-rows of
+multi-bit tiles, one row spanning many chunks (the cross-chunk join), empty
+rows, a ragged n, and a masked level loop's all-masked chunks.  Bit-exact for
+Boolean, integer, min, max and OR results; plus-times within 1e-5 relative
+error of the fp64 oracle (the bound derived in test_gpu_spmv.py), and bitwise
+reproducible from call to call.  The four-column PageRank block sums each
+column exactly like the single-column SpMV."""
 import numpy as np
 import pytest
 import torch
@@ -48,8 +47,8 @@ def B():
 
 
 def _run_all(B, g, m):
-    """Every scheme the tile_dim-4 kernel serves."""
-    B.b2sr_set_schedule(m, 2)  # DIRECT: the value schemes take the tile_dim-4 kernel
+    """Every SpMV scheme at tile_dim 4."""
+    B.b2sr_set_schedule(m, 2)  # DIRECT
     n = g.n
     words = B.bitset_words(n)
     xb = graphs.random_bits(n, 0.1, seed=3)
@@ -94,7 +93,7 @@ def _run_all(B, g, m):
 
 
 @pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=IDS)
-def test_k4_kernel_against_oracle(B, gi):
+def test_k4_schemes_against_oracle(B, gi):
     name, g = GRAPHS[gi]
     rp, ci = csr_dev(g)
     cg = oracle.canonicalize(g)
