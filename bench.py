@@ -40,7 +40,8 @@ SERVE_TILE = 4           # tile_dim of the served graphs (direct schedule, as th
 EXTRA_TILE = 8           # tile_dim of the grid SSSP, triangle-count and arena extras
 NSRC, PR_ITERS, DAMP = 16, 50, 0.85
 QUERIES_PER_STEP = 1 + NSRC + PR_ITERS + 1  # edge passes counted per step (x nnz)
-FAMILIES = ["spmv_bool", "spmv_count", "spmv_plus", "spmv_minplus", "spmv_min_i32", "spmm_or64"]
+FAMILIES = ["spmv_bool", "spmv_count", "spmv_plus", "spmv_minplus", "spmv_min_i32", "spmm_or64", "spmm_plus4",
+            "spmv_max", "spmv_maxkey"]
 
 
 def workload_desc(n, nnz):
@@ -294,6 +295,7 @@ TC_SCALE, TC_EF = 18, 32
 MS_SCALE, MS_SOURCES = 22, 64
 ARENA_GRAPHS, ARENA_SCALES = 256, (8, 16)
 PERM_SEED = 2
+ALU_PEAK_TOPS = 152 * 4 * 32 * 2.07e9 / 3 / 1e12   # AND-popc word operations per second at issue bound
 
 
 def _grid_weighted():
@@ -344,10 +346,36 @@ def grid_tc_extra(B, dev, grid, tc):
     with B.b2sr_from_csr(n, rp_d, ci_d, EXTRA_TILE) as m:
         cnt = {}
         ms = _timed(lambda: cnt.__setitem__("t", B.b2sr_tc(m)), reps=3)
-        out["tc_rmat18_ef32"] = {"ms": ms, "nnz": int(ci.size), "l_edges": int(ci.size) // 2,
-                                 "edges_per_s": (ci.size // 2) / (ms / 1e3),
-                                 "edges_counted": "|L|, the strictly lower triangle's entries",
-                                 "triangles": int(cnt["t"].item()), "n": int(n)}
+        ms_lower = _timed(lambda: B.b2sr_lower(m).close(), reps=3)
+        with B.b2sr_lower(m) as L:
+            count = torch.empty(1, dtype=torch.int64, device=dev)
+            B.b2sr_spgemm_masked_count(L, L, L, count)
+            torch.cuda.synchronize()
+            B.b2sr_timing_reset()
+            B.b2sr_timing_enable(True)
+            for _ in range(5):
+                B.b2sr_spgemm_masked_count(L, L, L, count)
+            torch.cuda.synchronize()
+            tk, nk, _ = B.b2sr_timing_read("spgemm_masked")
+            B.b2sr_timing_enable(False)
+            B.b2sr_timing_reset()
+            _, pairs = B.b2sr_spgemm_masked_count_work(L, L, L)
+            pairs = int(pairs.item())
+            l_tiles = L.n_tiles
+        kern_ms = tk / nk
+        ops = pairs / (kern_ms / 1e3)
+        out["tc_rmat18_ef32"] = {
+            "tile_dim": EXTRA_TILE, "ms": ms, "lower_ms": ms_lower, "kernel_ms": kern_ms,
+            "nnz": int(ci.size), "l_edges": int(ci.size) // 2, "l_tiles": int(l_tiles),
+            "edges_per_s": (ci.size // 2) / (ms / 1e3), "kernel_edges_per_s": (ci.size // 2) / (kern_ms / 1e3),
+            "edges_counted": "|L|, the strictly lower triangle's entries",
+            "triangles": int(cnt["t"].item()), "n": int(n),
+            "roofline": {"bound": "alu", "kernel": f"masked_count_kernel (k={EXTRA_TILE})",
+                         "achieved": ops / 1e12, "peak": ALU_PEAK_TOPS, "unit": "T AND-popc ops/s",
+                         "frac": ops / 1e12 / ALU_PEAK_TOPS, "algorithmic_ops_per_launch": pairs,
+                         "peak_source": "issue bound: 3 integer instructions (LOP3, POPC, IADD) per AND-popc "
+                                        "of one row word, 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz / 3",
+                         "traffic": None}}
     return out
 
 
@@ -589,10 +617,11 @@ def roofline_of(fam, ms_total, peak, peak_src, tile, schedule):
 
 def spmv_kernel_name(family, tile, schedule):
     """The SpMV kernel a family runs at this tile_dim and schedule (the
-    library's dispatch: the tile_dim-4 kernel for the bit-vector
-    schemes and for the value schemes under the direct schedule)."""
+    library's dispatch: the tile_dim-4 kernel for the bit-vector schemes at
+    k = 4, the staged gather kernel for the value schemes under the staged
+    schedule at k <= 16, the chunk kernel otherwise)."""
     bits = family in ("spmv_bool", "spmv_count")
-    if tile == 4 and (bits or schedule == 2):
+    if tile == 4 and bits:
         return "spmv_k4_kernel"
     if not bits and tile <= 16 and schedule != 2:
         return "spmv_gather_kernel"

@@ -341,6 +341,15 @@ b2sr_status b2sr_spmv_bool_noalloc(b2sr_handle h, const uint32_t* x, uint32_t* y
 b2sr_status b2sr_spgemm_masked_count(b2sr_handle A, b2sr_handle B, b2sr_handle M, int64_t* count,
                                      void* stream);
 
+/* The same masked count (Table 3, bmm_bin_bin_sum_masked) that also reports
+ * its integer work, for measurement (no counterpart in the paper): *pairs
+ * (device int64[1], written) receives the number of AND-popc operations on
+ * one row word each, i.e. over every mask tile (I, J), the bits of M_IJ times
+ * the tile-columns K with A_IK and B_JK both stored.  count as above.
+ * B2SR_ERR_INVALID_ARG if count or pairs is NULL or the handles disagree. */
+b2sr_status b2sr_spgemm_masked_count_work(b2sr_handle A, b2sr_handle B, b2sr_handle M, int64_t* count,
+                                          int64_t* pairs, void* stream);
+
 /* Boolean SpGEMM C = A (x) B over OR-AND, output in B2SR with the same
  * tile_dim (not in the paper's Table 3; built from the same tile products):
  * C_IJ[r] = OR_K OR_{m: bit m of A_IK[r]} B_KJ[m].  Synchronises `stream`.
@@ -538,7 +547,8 @@ int64_t b2sr_launch_count(void);
  * paper) on (1) or off (0).  While
  * on, every such launch is bracketed by two events on its own stream and
  * recorded under its family: "spmv_bool", "spmv_count", "spmv_plus",
- * "spmv_minplus", "spmv_min_i32" or "spmm_or64". */
+ * "spmv_minplus", "spmv_min_i32", "spmm_or64" or "spgemm_masked" (the
+ * masked-count SpGEMM kernel; its bytes are the three matrices' arrays). */
 void b2sr_timing_enable(int on);
 
 /* Timing read-out (no counterpart in the paper).

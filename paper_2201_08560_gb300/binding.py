@@ -80,6 +80,7 @@ def _load() -> ctypes.CDLL:
         "b2sr_spmv_bool_noalloc": (c_int, [p, p, p, p, c_int, p]),
         "b2sr_spmm_f32x4": (c_int, [p, p, p, p, c_int, p]),
         "b2sr_spgemm_masked_count": (c_int, [p, p, p, p, p]),
+        "b2sr_spgemm_masked_count_work": (c_int, [p, p, p, p, p, p]),
         "b2sr_spgemm_bool": (c_int, [p, p, p, pp]),
         "b2sr_set_schedule": (c_int, [p, c_int]),
         "b2sr_sample_profile": (c_int, [i32, p, p, i64, p, i64, p, p, p]),
@@ -351,6 +352,14 @@ def b2sr_spgemm_masked_count(A: Matrix, B: Matrix, M: Matrix, count: Optional[to
         count = torch.empty(1, dtype=torch.int64, device=torch.device("cuda", torch.cuda.current_device()))
     _check(lib.b2sr_spgemm_masked_count(A.handle, B.handle, M.handle, _ptr(count), _stream(stream)))
     return count
+
+
+def b2sr_spgemm_masked_count_work(A: Matrix, B: Matrix, M: Matrix, stream=None):
+    """(count, pairs): the masked count and its AND-popc word operations, as int64 device tensors."""
+    count = torch.empty(1, dtype=torch.int64, device=_dev())
+    pairs = torch.empty(1, dtype=torch.int64, device=_dev())
+    _check(lib.b2sr_spgemm_masked_count_work(A.handle, B.handle, M.handle, _ptr(count), _ptr(pairs), _stream(stream)))
+    return count, pairs
 
 
 def b2sr_spgemm_bool(A: Matrix, B: Matrix, stream=None) -> Matrix:

@@ -24,7 +24,7 @@ b2sr_status spmv_dispatch(b2sr_matrix* h, b2sr_semiring sr, b2sr_vec in_kind, co
 b2sr_status spmm64_dispatch(b2sr_matrix* h, const uint64_t* X, uint64_t* Y, const uint64_t* M, int comp,
                             cudaStream_t s, const int32_t* gate);
 b2sr_status masked_count(const b2sr_matrix* A, const b2sr_matrix* B, const b2sr_matrix* M, int64_t* count,
-                         cudaStream_t s);
+                         cudaStream_t s, int64_t* pairs);
 
 // active <- found (only while active); level counter advances with it
 __global__ void advance_kernel(int32_t* active, const int32_t* found, int32_t* level) {
@@ -452,7 +452,7 @@ extern "C" b2sr_status b2sr_tc(b2sr_handle h, int64_t* count, void* stream) {
     if (!count) return fail(B2SR_ERR_INVALID_ARG, "count is NULL");
     b2sr_handle L = nullptr;
     B2SR_TRY(b2sr_lower(h, stream, &L));
-    b2sr_status st = masked_count(L, L, L, count, to_stream(stream));
+    b2sr_status st = masked_count(L, L, L, count, to_stream(stream), nullptr);
     b2sr_destroy(L);
     return st;
 }

@@ -28,38 +28,49 @@ b2sr_status cuda_fail(cudaError_t e, const char* what) {
     return fail(B2SR_ERR_CUDA, m);
 }
 
-// The stream-ordered pool keeps freed memory for reuse (up to a quarter of the
-// device) instead of returning it to the driver at every synchronisation: the
-// conversion's sort buffers and every driver's temporaries are re-used from
-// call to call rather than mapped again.  A property of this process's pool
-// only, gone with the process.
-static void keep_pool_memory() {
+// Device memory comes from a stream-ordered pool of the library's own, one per
+// device, created on first use.  It keeps freed memory for reuse (up to a
+// quarter of the device) instead of returning it to the driver at every
+// synchronisation, so the conversion's sort buffers and every driver's
+// temporaries are re-used from call to call rather than mapped again.  Being
+// private, it leaves the process's default pool, which the host application
+// may tune for itself, untouched.
+static cudaMemPool_t library_pool(int dev) {
     static std::once_flag once[64];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-        cudaGetLastError();
-        return;
-    }
+    static cudaMemPool_t pools[64] = {nullptr};
+    if (dev < 0 || dev >= 64) return nullptr;
     std::call_once(once[dev], [dev] {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
         cudaMemPool_t pool = nullptr;
-        size_t free_b = 0, total_b = 0;
-        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-            uint64_t keep = (uint64_t)total_b / 4;
-            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+                uint64_t keep = (uint64_t)total_b / 4;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            }
+            pools[dev] = pool;
         }
         cudaGetLastError();
     });
+    return pools[dev];
 }
 
 b2sr_status dmalloc(void** p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
-    keep_pool_memory();
-    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    int dev = 0;
+    B2SR_CUDA_TRY(cudaGetDevice(&dev));
+    cudaMemPool_t pool = library_pool(dev);
+    if (!pool) return fail(B2SR_ERR_CUDA, "could not create the library's memory pool on device " + std::to_string(dev));
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
-        return fail(B2SR_ERR_OOM, "cudaMallocAsync(" + std::to_string(bytes) + " bytes) failed: " +
+        return fail(B2SR_ERR_OOM, "cudaMallocFromPoolAsync(" + std::to_string(bytes) + " bytes) failed: " +
                                       cudaGetErrorString(e));
     }
     return B2SR_OK;

@@ -1,9 +1,11 @@
 // B2SR SpGEMM: bmm_bin_bin_sum_masked (Table 3, Listing 2; the fused-sum
 // triangle-counting kernel of Sec. V) and the Boolean product C = A (x) B.
 //
-// Masked count: for a mask tile (I, J) the tile-column lists of A's tile-row I
-// and B's tile-row J are intersected (binary search of the shorter list's
-// entries in the longer one, 32 lanes at a time); every common K adds
+// Masked count: each warp takes a run of consecutive mask tiles (so their
+// tile-rows come from one search, then a walk of the row pointers); for a mask
+// tile (I, J) the tile-column lists of A's tile-row I and B's tile-row J are
+// intersected (binary search of the shorter list's entries in the longer one,
+// 32 lanes at a time); every common K adds
 //   sum over bits (r, c) of M_IJ of popc(A_IK[r] & B_JK[c]),
 // i.e. Listing 2's AND-popc of two bit-rows, restricted to the mask.  Lanes
 // accumulate in registers, a warp sums with shuffles and one 64-bit atomic
@@ -43,19 +45,28 @@ struct MatView {
 };
 
 template <int K>
-__global__ void masked_count_kernel(MatView A, MatView B, MatView M, unsigned long long* __restrict__ out) {
+__global__ void masked_count_kernel(MatView A, MatView B, MatView M, unsigned long long* __restrict__ out,
+                                    unsigned long long* __restrict__ pairs) {
     const int lane = (int)lane_id();
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long acc = 0;
-    for (int64_t mt = gw; mt < M.T; mt += nw) {
-        // tile-row I of mask tile mt: largest I with M.rowptr[I] <= mt
-        int32_t lo = 0, hi = M.ntr - 1;
+    unsigned long long acc = 0, npairs = 0;
+    // each warp takes a run of consecutive mask tiles: their tile-row is found
+    // once by a binary search and then advanced as the run crosses rows
+    const int64_t per = (M.T + nw - 1) / nw;
+    const int64_t t0 = gw * per, t1 = min(M.T, t0 + per);
+    int32_t I = 0;
+    if (t0 < t1) {
+        int32_t lo = 0, hi = M.ntr - 1;  // largest I with M.rowptr[I] <= t0
         while (lo < hi) {
             int32_t mid = lo + (hi - lo + 1) / 2;
-            if ((int64_t)__ldg(M.rowptr + mid) <= mt) lo = mid; else hi = mid - 1;
+            if ((int64_t)__ldg(M.rowptr + mid) <= t0) lo = mid; else hi = mid - 1;
         }
-        const int32_t I = lo;
+        I = lo;
+    }
+    int64_t row_end = t0 < t1 ? __ldg(M.rowptr + I + 1) : 0;
+    for (int64_t mt = t0; mt < t1; ++mt) {
+        while (mt >= row_end) row_end = __ldg(M.rowptr + (++I) + 1);
         const int32_t J = __ldg(M.colind + mt);
         uint32_t mrow[K];
 #pragma unroll
@@ -88,12 +99,19 @@ __global__ void masked_count_kernel(MatView A, MatView B, MatView M, unsigned lo
 #pragma unroll
                     for (int q2 = 0; q2 < K; ++q2) bc = (q2 == c) ? brow[q2] : bc;
                     acc += (unsigned long long)__popc(ar & bc);
+                    ++npairs;
                 }
             }
         }
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0 && acc) atomicAdd(out, acc);
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+    }
+    if (lane == 0) {
+        if (acc) atomicAdd(out, acc);
+        if (pairs && npairs) atomicAdd(pairs, npairs);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -197,16 +215,25 @@ __global__ void build_rowptr_from_rows(const int32_t* __restrict__ tilerow, int6
 
 static MatView view(const b2sr_matrix* h) { return MatView{h->rowptr, h->colind, h->tiles, h->T, h->ntr}; }
 
+// The masked count; `pairs` (device int64, optional) receives the number of
+// AND-popc word operations done (one per mask bit per common tile-column).
 b2sr_status masked_count(const b2sr_matrix* A, const b2sr_matrix* B, const b2sr_matrix* M, int64_t* count,
-                         cudaStream_t s) {
+                         cudaStream_t s, int64_t* pairs) {
     B2SR_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int64_t), s));
+    if (pairs) B2SR_CUDA_TRY(cudaMemsetAsync(pairs, 0, sizeof(int64_t), s));
     if (M->T == 0) return B2SR_OK;
+    auto* out = reinterpret_cast<unsigned long long*>(count);
+    auto* prs = reinterpret_cast<unsigned long long*>(pairs);
+    const double bytes = 3.0 * (4.0 * ((double)A->ntr + 1.0)) + ((double)A->T + B->T + M->T) * (4.0 + tile_bytes(A->k));
     return with_tile(A->k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
-        int64_t warps = M->T;
-        int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(warps * 32, 256), (int64_t)sm_count() * 16));
-        masked_count_kernel<K><<<grid, 256, 0, s>>>(view(A), view(B), view(M),
-                                                     reinterpret_cast<unsigned long long*>(count));
+        // runs of eight mask tiles a warp; the blocks are scheduled as SMs free
+        // up, which balances runs of long (hub) rows against short ones
+        const int64_t warps = ceil_div(M->T, 8);
+        const int grid = (int)std::max<int64_t>(1, ceil_div(warps, 8));
+        void* tok = timing_begin(s);
+        masked_count_kernel<K><<<grid, 256, 0, s>>>(view(A), view(B), view(M), out, prs);
+        timing_end(tok, "spgemm_masked", bytes, s);
         B2SR_LAUNCH_CHECK("masked_count_kernel");
         return B2SR_OK;
     });
@@ -314,7 +341,19 @@ extern "C" b2sr_status b2sr_spgemm_masked_count(b2sr_handle A, b2sr_handle B, b2
     if (!count) return fail(B2SR_ERR_INVALID_ARG, "count is NULL");
     if (A->n != B->n || A->n != M->n || A->k != B->k || A->k != M->k)
         return fail(B2SR_ERR_INVALID_ARG, "A, B and M need the same n and tile_dim");
-    return masked_count(A, B, M, count, to_stream(stream));
+    return masked_count(A, B, M, count, to_stream(stream), nullptr);
+}
+
+extern "C" b2sr_status b2sr_spgemm_masked_count_work(b2sr_handle A, b2sr_handle B, b2sr_handle M, int64_t* count,
+                                                     int64_t* pairs, void* stream) {
+    clear_error();
+    B2SR_TRY(check_handle(A));
+    B2SR_TRY(check_handle(B));
+    B2SR_TRY(check_handle(M));
+    if (!count || !pairs) return fail(B2SR_ERR_INVALID_ARG, "count or pairs is NULL");
+    if (A->n != B->n || A->n != M->n || A->k != B->k || A->k != M->k)
+        return fail(B2SR_ERR_INVALID_ARG, "A, B and M need the same n and tile_dim");
+    return masked_count(A, B, M, count, to_stream(stream), pairs);
 }
 
 extern "C" b2sr_status b2sr_spgemm_bool(b2sr_handle A, b2sr_handle B, void* stream, b2sr_handle* C) {

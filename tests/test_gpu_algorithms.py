@@ -42,6 +42,59 @@ def test_masked_count_asymmetric(B, k, n, da, db, seed):
     assert got == oracle.masked_count(A, Bm, M)
 
 
+def _tile_pairs(A, Bm, M, k):
+    """Work of the masked count from the oracle's B2SR arrays: over every mask
+    tile (I, J), its set bits times the tile-columns K stored in both A's
+    tile-row I and B's tile-row J."""
+    def rows(g):
+        trp, tci, tiles = oracle.b2sr(g, k)
+        return [set(tci[trp[i]:trp[i + 1]].tolist()) for i in range(len(trp) - 1)], trp, tci, tiles
+    ra, _, _, _ = rows(A)
+    rb, _, _, _ = rows(Bm)
+    _, mrp, mci, mtiles = rows(M)
+    total = 0
+    for i in range(len(mrp) - 1):
+        for t in range(mrp[i], mrp[i + 1]):
+            bits = sum(bin(int(w)).count("1") for w in np.atleast_1d(mtiles[t]))
+            total += bits * len(ra[i] & rb[int(mci[t])])
+    return total
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("n,da,db,seed", [(1, 1.0, 1.0, 0), (77, 0.08, 0.1, 1), (300, 0.02, 0.03, 2)])
+def test_masked_count_work(B, k, n, da, db, seed):
+    """The count with its work report equals the plain count, and the reported
+    AND-popc operations equal the tile-level work computed from the oracle's
+    tile arrays."""
+    A = graphs.random_directed(n, da, seed)
+    Bm = graphs.random_directed(n, db, seed + 50)
+    M = graphs.random_directed(n, 0.3, seed + 99)
+    with mat(B, A, k) as a, mat(B, Bm, k) as b, mat(B, M, k) as mm:
+        cnt, pairs = B.b2sr_spgemm_masked_count_work(a, b, mm)
+    assert int(cnt.item()) == oracle.masked_count(A, Bm, M)
+    assert int(pairs.item()) == _tile_pairs(A, Bm, M, k)
+
+
+def _hub_with_path(n):
+    """Vertex 0 joined to every other vertex, and the others joined in a path:
+    n - 2 triangles (0, i, i+1), all through one hub row."""
+    i = np.arange(1, n, dtype=np.int64)
+    src = np.concatenate([np.zeros(n - 1, np.int64), i[:-1]])
+    dst = np.concatenate([i, i[1:]])
+    return graphs.from_edges(n, src, dst)
+
+
+@pytest.mark.parametrize("k", [4, 8])
+def test_masked_count_long_row(B, k):
+    """A mask tile-row whose A row has more tiles than the staged list holds
+    (a hub with 199,999 neighbours): positions are then searched in global
+    memory."""
+    g = _hub_with_path(200000)
+    with mat(B, g, k) as m:
+        assert int(B.b2sr_spgemm_masked_count(m, m, m).item()) == oracle.masked_count(g, g, g)
+        assert int(B.b2sr_tc(m).item()) == 200000 - 2
+
+
 @pytest.mark.parametrize("k", KS)
 @pytest.mark.parametrize("gi", [0, 1, 2, 3, 4, 6, 7, 8], ids=["rmat12", "rmat11perm", "star20k", "grid37x41",
                                                                "gaps", "n1", "empty45", "mycielski9"])
