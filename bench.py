@@ -531,25 +531,35 @@ def aggregate_replicas(ms_total, e2e_ms, edges_per_step, steps, world, device):
     return ms_total, e2e_ms, value, e2e_value
 
 
-def generate_extra_graphs():
-    """Every graph the extras use, generated on the host by a spawn-started
-    process pool before any timed region starts (so no timing overlaps host
-    generation work).  Returns a dict of plain arrays and the wall time."""
+EXTRAS = ("config2", "serving", "grid_sssp_and_tc", "batching")
+
+
+def generate_extra_graphs(which):
+    """Every graph the chosen extras use, generated on the host by a
+    spawn-started process pool before any timed region starts (so no timing
+    overlaps host generation work).  Returns a dict of plain arrays and the
+    wall time."""
     import multiprocessing as mp
     t0 = time.perf_counter()
     lo, hi = SERVE_SCALES
     serve_specs = [(lo + i % (hi - lo + 1), 1000 + i) for i in range(SERVE_GRAPHS)]
     rng = np.random.default_rng(23)
     a_scales = [int(v) for v in rng.integers(ARENA_SCALES[0], ARENA_SCALES[1] + 1, ARENA_GRAPHS)]
+    out = {}
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-        serve = pool.starmap_async(_serve_graph, serve_specs)
-        grid = pool.apply_async(_grid_weighted)
-        tc = pool.apply_async(_rmat_plain, (TC_SCALE, TC_EF, 2))
-        big = pool.apply_async(_rmat_plain, (MS_SCALE, EDGE_FACTOR, 3))
-        perm = pool.apply_async(_rmat_perm, (SCALE, EDGE_FACTOR, SEED, PERM_SEED))
-        arena = pool.starmap_async(_rmat_plain, [(sc, EDGE_FACTOR, 5000 + i) for i, sc in enumerate(a_scales)])
-        out = {"serve": serve.get(), "grid": grid.get(), "tc": tc.get(), "big": big.get(), "perm": perm.get(),
-               "arena": arena.get()}
+        jobs = {}
+        if "serving" in which:
+            jobs["serve"] = pool.starmap_async(_serve_graph, serve_specs)
+        if "grid_sssp_and_tc" in which:
+            jobs["grid"] = pool.apply_async(_grid_weighted)
+            jobs["tc"] = pool.apply_async(_rmat_plain, (TC_SCALE, TC_EF, 2))
+        if "batching" in which:
+            jobs["big"] = pool.apply_async(_rmat_plain, (MS_SCALE, EDGE_FACTOR, 3))
+            jobs["arena"] = pool.starmap_async(_rmat_plain, [(sc, EDGE_FACTOR, 5000 + i) for i, sc in enumerate(a_scales)])
+        if "config2" in which:
+            jobs["perm"] = pool.apply_async(_rmat_perm, (SCALE, EDGE_FACTOR, SEED, PERM_SEED))
+        for key, job in jobs.items():
+            out[key] = job.get()
     return out, time.perf_counter() - t0
 
 
@@ -690,7 +700,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the serving, grid/TC and batching extras")
+    ap.add_argument("--no-extras", action="store_true", help="skip the extras (config 2 sweep, serving, grid/TC, batching)")
+    ap.add_argument("--extra", action="append", choices=EXTRAS, default=None,
+                    help="run only these extras (repeatable; default all)")
     ap.add_argument("--tile", type=int, default=None, help="override the main workload's tile_dim")
     ap.add_argument("--schedule", type=int, default=None, help="override its SpMV schedule (1 staged, 2 direct)")
     args = ap.parse_args()
@@ -707,8 +719,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     # the extras' graphs are generated before any GPU timing (rank 0 only)
     pre, t_gen = (None, 0.0)
-    if rank == 0 and not args.no_extras:
-        pre, t_gen = generate_extra_graphs()
+    which = () if args.no_extras else tuple(args.extra or EXTRAS)
+    if rank == 0 and which:
+        pre, t_gen = generate_extra_graphs(which)
 
     import torch
     import torch.distributed as dist
@@ -911,7 +924,7 @@ def main():
             "colours": int(cols.max().item()) + 1}
     del levels
 
-    if pre is not None:
+    if pre is not None and "config2" in which:
         # config 2's permuted ids: the same step on the permuted graph
         pn, prp, pci = pre["perm"]
         prp_d, pci_d = torch.from_numpy(prp).to(dev), torch.from_numpy(pci).to(dev)
@@ -945,10 +958,13 @@ def main():
                                       "est_ratio": rep["est_ratio"], "used": {"tile_dim": TILE, "schedule": SCHEDULE}}
         except Exception as e:
             extra["autotune_main"] = {"failed": repr(e)}
+    if pre is not None:
         for name, fn in (("serving", lambda: serving_extra(B, dev, pre["serve"], t_gen)),
                          ("grid_sssp_and_tc", lambda: grid_tc_extra(B, dev, pre["grid"], pre["tc"])),
                          ("batching", lambda: batching_extra(B, dev, pre["big"], pre["arena"],
                                                              f"{ARENA_SCALES[0]}..{ARENA_SCALES[1]} uniform, seed 23"))):
+            if name not in which:
+                continue
             try:
                 extra[name] = fn()
             except Exception as e:  # reported, never fatal to the main line

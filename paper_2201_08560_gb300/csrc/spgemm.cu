@@ -28,6 +28,13 @@ __device__ __forceinline__ uint32_t gword(const uint8_t* __restrict__ tiles, int
     return __ldg(tiles + t * K + r);
 }
 
+// a k <= 8 tile as one word: byte r is row r
+template <int K>
+__device__ __forceinline__ uint64_t tile_word64(const uint8_t* __restrict__ tiles, int64_t t) {
+    if (K == 8) return __ldg(reinterpret_cast<const unsigned long long*>(tiles) + t);
+    return __ldg(reinterpret_cast<const uint32_t*>(tiles) + t);
+}
+
 __device__ __forceinline__ int64_t lower_bound_i32(const int32_t* __restrict__ a, int64_t lo, int64_t hi, int32_t v) {
     while (lo < hi) {
         int64_t mid = (lo + hi) >> 1;
@@ -68,9 +75,18 @@ __global__ void masked_count_kernel(MatView A, MatView B, MatView M, unsigned lo
     for (int64_t mt = t0; mt < t1; ++mt) {
         while (mt >= row_end) row_end = __ldg(M.rowptr + (++I) + 1);
         const int32_t J = __ldg(M.colind + mt);
-        uint32_t mrow[K];
+        // k <= 8: a tile is one 32/64-bit word whose bytes are its rows, so a
+        // row is picked by a shift; larger tiles keep their rows in registers
+        constexpr int MR = K <= 8 ? 1 : K;
+        uint32_t mrow[MR];
+        uint64_t mw = 0;
+        (void)mrow;
+        if constexpr (K <= 8) {
+            mw = tile_word64<K>(M.tiles, mt);
+        } else {
 #pragma unroll
-        for (int r = 0; r < K; ++r) mrow[r] = gword<K>(M.tiles, mt, r);
+            for (int r = 0; r < K; ++r) mrow[r] = gword<K>(M.tiles, mt, r);
+        }
         const int64_t a0 = __ldg(A.rowptr + I), a1 = __ldg(A.rowptr + I + 1);
         const int64_t b0 = __ldg(B.rowptr + J), b1 = __ldg(B.rowptr + J + 1);
         const bool a_short = (a1 - a0) <= (b1 - b0);
@@ -84,22 +100,33 @@ __global__ void masked_count_kernel(MatView A, MatView B, MatView M, unsigned lo
             if (q >= l1 || __ldg(lcol + q) != Kc) continue;
             const int64_t ta = a_short ? p : q;  // tile A_IK
             const int64_t tb = a_short ? q : p;  // tile B_JK
-            uint32_t brow[K];
-#pragma unroll
-            for (int c = 0; c < K; ++c) brow[c] = gword<K>(B.tiles, tb, c);
-#pragma unroll
-            for (int r = 0; r < K; ++r) {
-                uint32_t bits = mrow[r];
-                if (!bits) continue;
-                const uint32_t ar = gword<K>(A.tiles, ta, r);
-                while (bits) {
-                    const int c = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    uint32_t bc = 0;
-#pragma unroll
-                    for (int q2 = 0; q2 < K; ++q2) bc = (q2 == c) ? brow[q2] : bc;
-                    acc += (unsigned long long)__popc(ar & bc);
+            if constexpr (K <= 8) {
+                const uint64_t aw = tile_word64<K>(A.tiles, ta), bw = tile_word64<K>(B.tiles, tb);
+                uint64_t m = mw;
+                while (m) {
+                    const int bit = __ffsll((long long)m) - 1;  // row bit >> 3, column bit & 7
+                    m &= m - 1;
+                    acc += (unsigned long long)__popc((uint32_t)((aw >> (bit & ~7)) & (bw >> (8 * (bit & 7))) & 0xFFu));
                     ++npairs;
+                }
+            } else {
+                uint32_t brow[K];
+#pragma unroll
+                for (int c = 0; c < K; ++c) brow[c] = gword<K>(B.tiles, tb, c);
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    uint32_t bits = mrow[r];
+                    if (!bits) continue;
+                    const uint32_t ar = gword<K>(A.tiles, ta, r);
+                    while (bits) {
+                        const int c = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        uint32_t bc = 0;
+#pragma unroll
+                        for (int q2 = 0; q2 < K; ++q2) bc = (q2 == c) ? brow[q2] : bc;
+                        acc += (unsigned long long)__popc(ar & bc);
+                        ++npairs;
+                    }
                 }
             }
         }
