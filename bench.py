@@ -40,14 +40,19 @@ SERVE_TILE = 4           # tile_dim of the served graphs (direct schedule, as th
 EXTRA_TILE = 8           # tile_dim of the grid SSSP, triangle-count and arena extras
 NSRC, PR_ITERS, DAMP = 16, 50, 0.85
 QUERIES_PER_STEP = 1 + NSRC + PR_ITERS + 1  # edge passes counted per step (x nnz)
+PERMUTE = None           # seed of a vertex relabelling of the main workload (None: R-MAT's own ids)
 FAMILIES = ["spmv_bool", "spmv_count", "spmv_plus", "spmv_minplus", "spmv_min_i32", "spmm_or64", "spmm_plus4",
             "spmv_max", "spmv_maxkey"]
+
+
+def ids_desc():
+    return "unpermuted ids" if PERMUTE is None else f"ids permuted (seed {PERMUTE})"
 
 
 def workload_desc(n, nnz):
     return {
         "workload": f"R-MAT scale {SCALE} ef{EDGE_FACTOR} a/b/c/d=0.57/0.19/0.19/0.05 seed {SEED}, symmetrised, "
-                    f"no self-loops/duplicates, unpermuted ids; B2SR tile {TILE}x{TILE}; step = CSR->B2SR + Boolean SpMV + "
+                    f"no self-loops/duplicates, {ids_desc()}; B2SR tile {TILE}x{TILE}; step = CSR->B2SR + Boolean SpMV + "
                     f"BFS from {NSRC} seeded sources (batched) + fp32 PageRank {PR_ITERS} iters + CC",
         "n": int(n), "nnz": int(nnz), "tile_dim": TILE, "schedule": "direct" if SCHEDULE == 2 else "staged",
         "tile_choice": "tile_dim sweep 4/8/16/32 by b2sr_autotune for the step's dominant scheme (plus-times, "
@@ -61,6 +66,8 @@ def workload_desc(n, nnz):
 def make_graph():
     from paper_2201_08560_gb300 import graphs
     g = graphs.rmat(SCALE, EDGE_FACTOR, seed=SEED)
+    if PERMUTE is not None:
+        g = graphs.permute(g, PERMUTE)
     srcs = graphs.sources(g, NSRC, seed=7)
     xbits = graphs.random_bits(g.n, 0.05, seed=3)
     return g, srcs, xbits
@@ -291,6 +298,7 @@ def serving_extra(B, dev, gs, t_gen):
 # the other workloads: weighted grid SSSP and triangle counting; batching
 # ---------------------------------------------------------------------------
 GRID_SIDE, GRID_WSEED, SSSP_DELTA = 4096, 5, 400.0
+SSSP_DELTA_SWEEP = (50.0, 100.0, 200.0, 400.0, 800.0, 1600.0)  # bucket widths timed beside the default
 TC_SCALE, TC_EF = 18, 32
 MS_SCALE, MS_SOURCES = 22, 64
 ARENA_GRAPHS, ARENA_SCALES = 256, (8, 16)
@@ -324,23 +332,11 @@ def _timed(fn, reps=1):
     return a.elapsed_time(b) / reps
 
 
-def grid_tc_extra(B, dev, grid, tc):
-    """SSSP from the corner of a 4096 x 4096 4-neighbour grid with fp32 weights
-    on the 1/16 lattice in [1, 100); triangle count of R-MAT scale 18 ef32."""
+def tc_extra(B, dev, tc):
+    """Triangle count of R-MAT scale 18 ef32 (tile_dim 8): the whole driver,
+    the lower-triangle extraction and the masked-count kernel alone."""
     import torch
     out = {}
-    n, rp, ci, w = grid
-    rp_d, ci_d = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
-    with B.b2sr_from_csr(n, rp_d, ci_d, EXTRA_TILE) as m:
-        wb = B.b2sr_weights_from_csr(m, rp_d, ci_d, torch.from_numpy(w).to(dev))
-        dist = torch.empty(n, dtype=torch.float32, device=dev)
-        # push rounds over the frontier (the grid is symmetric: the handle is its own transpose),
-        # delta-stepping buckets of 4x the largest weight
-        ms = _timed(lambda: B.b2sr_sssp_push(m, 0, wb, dist, delta=SSSP_DELTA), reps=3)
-        far = float(dist[-1].item())
-        out["sssp_grid4096"] = {"driver": "b2sr_sssp_push", "delta": SSSP_DELTA, "ms": ms, "nnz": int(ci.size),
-                                "gteps": ci.size / (ms / 1e3) / 1e9, "dist_far_corner": far, "n": int(n)}
-    del rp_d, ci_d
     n, rp, ci = tc
     rp_d, ci_d = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
     with B.b2sr_from_csr(n, rp_d, ci_d, EXTRA_TILE) as m:
@@ -364,7 +360,7 @@ def grid_tc_extra(B, dev, grid, tc):
             l_tiles = L.n_tiles
         kern_ms = tk / nk
         ops = pairs / (kern_ms / 1e3)
-        out["tc_rmat18_ef32"] = {
+        out = {
             "tile_dim": EXTRA_TILE, "ms": ms, "lower_ms": ms_lower, "kernel_ms": kern_ms,
             "nnz": int(ci.size), "l_edges": int(ci.size) // 2, "l_tiles": int(l_tiles),
             "edges_per_s": (ci.size // 2) / (ms / 1e3), "kernel_edges_per_s": (ci.size // 2) / (kern_ms / 1e3),
@@ -376,6 +372,33 @@ def grid_tc_extra(B, dev, grid, tc):
                          "peak_source": "issue bound: 3 integer instructions (LOP3, POPC, IADD) per AND-popc "
                                         "of one row word, 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz / 3",
                          "traffic": None}}
+    return out
+
+
+def grid_sssp_extra(B, dev, grid):
+    """SSSP from the corner of a 4096 x 4096 4-neighbour grid with fp32
+    weights on the 1/16 lattice in [1, 100) (tile_dim 8): the push driver at
+    the default bucket width, its rounds, and a sweep of bucket widths."""
+    import torch
+    n, rp, ci, w = grid
+    rp_d, ci_d = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
+    with B.b2sr_from_csr(n, rp_d, ci_d, EXTRA_TILE) as m:
+        wb = B.b2sr_weights_from_csr(m, rp_d, ci_d, torch.from_numpy(w).to(dev))
+        dist = torch.empty(n, dtype=torch.float32, device=dev)
+        # push rounds over the frontier (the grid is symmetric: the handle is its own transpose),
+        # delta-stepping buckets of 4x the largest weight
+        ms = _timed(lambda: B.b2sr_sssp_push(m, 0, wb, dist, delta=SSSP_DELTA), reps=3)
+        rounds = B.b2sr_sssp_push_rounds()
+        far = float(dist[-1].item())
+        sweep = {}
+        for delta in SSSP_DELTA_SWEEP:
+            t = _timed(lambda: B.b2sr_sssp_push(m, 0, wb, dist, delta=delta), reps=1)
+            r = B.b2sr_sssp_push_rounds()
+            sweep[str(delta)] = {"ms": t, "rounds": r, "us_per_round": t * 1e3 / r}
+        out = {"driver": "b2sr_sssp_push", "delta": SSSP_DELTA, "ms": ms, "nnz": int(ci.size),
+               "gteps": ci.size / (ms / 1e3) / 1e9, "rounds": rounds,
+               "us_per_round": ms * 1e3 / rounds, "dist_far_corner": far, "n": int(n),
+               "delta_sweep": sweep}
     return out
 
 
@@ -531,7 +554,7 @@ def aggregate_replicas(ms_total, e2e_ms, edges_per_step, steps, world, device):
     return ms_total, e2e_ms, value, e2e_value
 
 
-EXTRAS = ("config2", "serving", "grid_sssp_and_tc", "batching")
+EXTRAS = ("config2", "serving", "tc", "grid_sssp", "batching")
 
 
 def generate_extra_graphs(which):
@@ -550,8 +573,9 @@ def generate_extra_graphs(which):
         jobs = {}
         if "serving" in which:
             jobs["serve"] = pool.starmap_async(_serve_graph, serve_specs)
-        if "grid_sssp_and_tc" in which:
+        if "grid_sssp" in which:
             jobs["grid"] = pool.apply_async(_grid_weighted)
+        if "tc" in which:
             jobs["tc"] = pool.apply_async(_rmat_plain, (TC_SCALE, TC_EF, 2))
         if "batching" in which:
             jobs["big"] = pool.apply_async(_rmat_plain, (MS_SCALE, EDGE_FACTOR, 3))
@@ -705,8 +729,12 @@ def main():
                     help="run only these extras (repeatable; default all)")
     ap.add_argument("--tile", type=int, default=None, help="override the main workload's tile_dim")
     ap.add_argument("--schedule", type=int, default=None, help="override its SpMV schedule (1 staged, 2 direct)")
+    ap.add_argument("--permute", type=int, default=None,
+                    help="relabel the main workload's vertices by the random permutation of this seed")
     args = ap.parse_args()
-    global TILE, SCHEDULE
+    global TILE, SCHEDULE, PERMUTE
+    if args.permute is not None:
+        PERMUTE = args.permute
     if args.tile:
         TILE = args.tile
     if args.schedule:
@@ -880,6 +908,18 @@ def main():
         B.b2sr_timing_reset()
         extra["spmv_bool"] = {"tile_dim": TILE, "kernel_us": tb / nb * 1e3, "gteps": g.nnz / (tb / nb / 1e3) / 1e9,
                               "gbs": byb / nb / (tb / nb / 1e3) / 1e9, "frac": byb / nb / (tb / nb / 1e3) / 1e9 / peak}
+        # CSR -> B2SR alone: the rows as generated (column order: ranking
+        # conversion) and the same CSR with its longest row reversed (radix sort)
+        def convert(cd):
+            B.b2sr_from_csr(g.n, rp, cd, TILE).close()
+        ci_u = ci.clone()
+        ilong = int(torch.argmax(rp[1:] - rp[:-1]).item())
+        a0, a1 = int(rp[ilong].item()), int(rp[ilong + 1].item())
+        ci_u[a0:a1] = torch.flip(ci_u[a0:a1], [0])
+        extra["conversion"] = {"tile_dim": TILE, "sorted_rows_ms": _timed(lambda: convert(ci), reps=5),
+                               "one_row_reversed_ms": _timed(lambda: convert(ci_u), reps=5),
+                               "includes": "validation, keys in order, tiles, B2SR arrays, SpMV schedule"}
+        del ci_u
         # max-times (Table 4): the SpMV alone, then MIS and colouring by rounds of local maxima
         xf = torch.from_numpy(np.random.default_rng(37).normal(size=g.n).astype(np.float32)).to(dev)
         yf = torch.empty(g.n, dtype=torch.float32, device=dev)
@@ -960,7 +1000,8 @@ def main():
             extra["autotune_main"] = {"failed": repr(e)}
     if pre is not None:
         for name, fn in (("serving", lambda: serving_extra(B, dev, pre["serve"], t_gen)),
-                         ("grid_sssp_and_tc", lambda: grid_tc_extra(B, dev, pre["grid"], pre["tc"])),
+                         ("tc", lambda: tc_extra(B, dev, pre["tc"])),
+                         ("grid_sssp", lambda: grid_sssp_extra(B, dev, pre["grid"])),
                          ("batching", lambda: batching_extra(B, dev, pre["big"], pre["arena"],
                                                              f"{ARENA_SCALES[0]}..{ARENA_SCALES[1]} uniform, seed 23"))):
             if name not in which:

@@ -466,15 +466,26 @@ b2sr_status b2sr_sssp(b2sr_handle h, const float* weights, int32_t src, float* d
  *   dist       device float[n]: 0 at src, +inf if unreachable
  *   delta      > 0: the buckets of delta-stepping (Sec. V names it): a round
  *              relaxes only active vertices closer than a threshold, which
- *              starts at delta and grows by delta whenever a round has none;
+ *              starts at delta; vertices at or past it wait in a far set
+ *              that no round touches until the near set is empty, when the
+ *              threshold grows by delta (to the least waiting distance plus
+ *              delta, if that is further) and the far set becomes active;
  *              <= 0: every active vertex every round (Bellman-Ford frontier)
  * A round touches only the active tile-rows.  Distances are updated with
  * integer atomicMin on the float bits; the order of updates and delta change
  * the number of rounds, never the result (bit-exact).  Rounds run as a CUDA
- * graph of 32 gated rounds: one host synchronisation per 32 rounds.
- * B2SR_ERR_NOT_CONVERGED past max_iters rounds (<= 0: n). */
+ * graph of 32 gated rounds: one host synchronisation per 32 rounds, and one
+ * more at the end to read the round count.
+ * B2SR_ERR_NOT_CONVERGED past max_iters rounds (<= 0: n, or 4n + 4 with
+ * delta > 0). */
 b2sr_status b2sr_sssp_push(b2sr_handle hT, const float* weights_t, int32_t src, float* dist, float delta,
                            int max_iters, void* stream);
+
+/* The rounds (relaxation rounds, counting those that only moved the far set
+ * in) run by the most recent successful b2sr_sssp_push on the calling host
+ * thread; 0 before any, and after a failed call.  Host-only; a measurement
+ * aid with no counterpart in the paper (Sec. V reports SSSP times only). */
+b2sr_status b2sr_sssp_push_rounds(int64_t* rounds);
 
 /* PageRank (Sec. V PR): x^0 = 1/n, then `iters` steps of
  *   x_i <- (1-d) t_i + d * sum_{j: A_ij=1} x_j / outdeg(j)

@@ -4,12 +4,16 @@
 // derived arrays (SpMV chunk schedule, set-bit offsets, column counts).
 //
 // Conversion: every entry (i, j) becomes the 64-bit key
-//   (i/k) << (S+10) | (j/k) << 10 | ((i%k)*k + j%k)
-// with S the bit width of a tile index; a stable radix sort on the tile part
-// groups equal tiles in (tile-row, tile-column) order, run heads become the
-// tiles, and each entry ORs its bit into its tile.  This replaces the paper's
-// cusparseXcsr2bsrNnz / cusparseScsr2bsr + packing kernels (Sec. III-B) with
-// one sort that gives the same three arrays.
+//   (i/k) << (S+10) | (j/k) << 10 | ((j%k)*k + i%k)
+// with S the bit width of a tile index.  Once the keys are in order, equal
+// tiles are runs in (tile-row, tile-column) order, run heads become the tiles,
+// and each entry ORs its bit into its tile.  When every CSR row is already in
+// column order (the usual case) the k rows of a tile-row are k sorted runs and
+// the keys are put in order by ranking each entry among its tile-row's rows
+// (binary searches) and, at k = 16 and 32, merging groups of eight rows
+// pairwise; otherwise a radix sort on the tile part orders them.  Both replace
+// the paper's cusparseXcsr2bsrNnz / cusparseScsr2bsr + packing kernels
+// (Sec. III-B) and give the same three arrays.
 #include <algorithm>
 #include <mutex>
 
@@ -57,6 +61,10 @@ __device__ __forceinline__ int32_t row_of(const int32_t* __restrict__ rowptr, in
     return lo;
 }
 
+__device__ __forceinline__ uint64_t entry_key(int32_t i, int32_t j, int k, int sbits) {
+    return ((uint64_t)(i / k) << (sbits + 10)) | ((uint64_t)(j / k) << 10) | (uint64_t)((j % k) * k + (i % k));
+}
+
 __global__ void __launch_bounds__(kKeyThreads) make_keys_kernel(int32_t n, const int32_t* __restrict__ rowptr,
                                                                 const int32_t* __restrict__ colind,
                                                                 int64_t nnz, int k, int sbits,
@@ -71,10 +79,98 @@ __global__ void __launch_bounds__(kKeyThreads) make_keys_kernel(int32_t n, const
     int64_t e = b0 + threadIdx.x;
     if (e > b1) return;
     int32_t i = row_of(rowptr, range[0], range[1], e);
-    int32_t j = colind[e];
-    uint64_t key = ((uint64_t)(i / k) << (sbits + 10)) | ((uint64_t)(j / k) << 10) |
-                   (uint64_t)((i % k) * k + (j % k));
-    keys[e] = key;
+    keys[e] = entry_key(i, colind[e], k, sbits);
+}
+
+// Flags (bit 0 of *unsorted) a row whose columns decrease somewhere; repeated
+// columns keep a row sorted.
+__global__ void __launch_bounds__(kKeyThreads) sorted_rows_kernel(int32_t n, const int32_t* __restrict__ rowptr,
+                                                                  const int32_t* __restrict__ colind,
+                                                                  int64_t nnz, int* __restrict__ unsorted) {
+    __shared__ int32_t range[2];
+    int64_t b0 = (int64_t)blockIdx.x * kKeyThreads;
+    if (b0 >= nnz) return;
+    int64_t b1 = min(b0 + kKeyThreads, nnz) - 1;
+    if (threadIdx.x == 0) range[0] = row_of(rowptr, 0, n - 1, b0);
+    if (threadIdx.x == 1) range[1] = row_of(rowptr, 0, n - 1, b1);
+    __syncthreads();
+    int64_t e = b0 + threadIdx.x;
+    if (e > b1) return;
+    int32_t i = row_of(rowptr, range[0], range[1], e);
+    if (e > 0 && e > __ldg(rowptr + i) && __ldg(colind + e - 1) > __ldg(colind + e)) atomicOr(unsorted, 1);
+}
+
+// Entries of the same tile-row ahead of column j in row q: those with a
+// smaller column, and also those with column j when `ties` (q is an earlier
+// row).
+__device__ __forceinline__ int64_t count_before(const int32_t* __restrict__ colind, int64_t lo, int64_t hi,
+                                                int32_t j, bool ties) {
+    const int64_t base = lo;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        int32_t x = __ldg(colind + mid);
+        if (x < j || (ties && x == j)) lo = mid + 1; else hi = mid;
+    }
+    return lo - base;
+}
+
+// Sorted rows: writes every entry's key straight to its place in the order of
+// its group of G rows (G divides k, groups start at multiples of G).  The
+// place is the group's first CSR position, plus the entry's offset in its own
+// row, plus the entries of the group's other rows that come before it in
+// (column, row) order.
+template <int G>
+__global__ void __launch_bounds__(kKeyThreads) rank_keys_kernel(int32_t n, const int32_t* __restrict__ rowptr,
+                                                                const int32_t* __restrict__ colind,
+                                                                int64_t nnz, int k, int sbits,
+                                                                uint64_t* __restrict__ keys) {
+    __shared__ int32_t range[2];
+    int64_t b0 = (int64_t)blockIdx.x * kKeyThreads;
+    if (b0 >= nnz) return;
+    int64_t b1 = min(b0 + kKeyThreads, nnz) - 1;
+    if (threadIdx.x == 0) range[0] = row_of(rowptr, 0, n - 1, b0);
+    if (threadIdx.x == 1) range[1] = row_of(rowptr, 0, n - 1, b1);
+    __syncthreads();
+    int64_t e = b0 + threadIdx.x;
+    if (e > b1) return;
+    const int32_t i = row_of(rowptr, range[0], range[1], e);
+    const int32_t j = __ldg(colind + e);
+    const int rg = i % G;
+    const int32_t g0 = i - rg;
+    int64_t dest = (int64_t)__ldg(rowptr + g0) + (e - (int64_t)__ldg(rowptr + i));
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+        const int32_t iq = g0 + q;
+        if (q == rg || iq >= n) continue;
+        dest += count_before(colind, __ldg(rowptr + iq), __ldg(rowptr + iq + 1), j, q < rg);
+    }
+    keys[dest] = entry_key(i, j, k, sbits);
+}
+
+// One pairwise merge of sorted runs of `run` rows inside every tile-row (the
+// runs a sorted-row conversion leaves when k > 8): each key moves to its
+// offset in its own run plus the partner run's keys ahead of it (the left
+// run wins ties).
+__global__ void merge_runs_kernel(const uint64_t* __restrict__ src, uint64_t* __restrict__ dst, int64_t nnz,
+                                  const int32_t* __restrict__ rowptr, int32_t n, int k, int run, int sbits) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = src[e];
+        const int r = (int)(x & 1023u) % k;
+        const int64_t rowL = (int64_t)(x >> (sbits + 10)) * k + (r & ~(2 * run - 1));
+        const int64_t a0 = __ldg(rowptr + min(rowL, (int64_t)n));
+        const int64_t m = __ldg(rowptr + min(rowL + run, (int64_t)n));
+        const int64_t b1 = __ldg(rowptr + min(rowL + 2 * run, (int64_t)n));
+        const bool right = (r & run) != 0;
+        int64_t lo = right ? a0 : m, hi = right ? m : b1;
+        const int64_t base = lo;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            uint64_t y = src[mid];
+            if (y < x || (right && y == x)) lo = mid + 1; else hi = mid;
+        }
+        dst[a0 + (e - (right ? m : a0)) + (lo - base)] = x;
+    }
 }
 
 __global__ void mark_heads_kernel(const uint64_t* __restrict__ keys, int64_t N, int32_t* __restrict__ flag) {
@@ -98,7 +194,7 @@ __global__ void fill_tiles_kernel(const uint64_t* __restrict__ keys, const int32
             colind[t] = (int32_t)((key >> 10) & jmask);
             tilerow[t] = (int32_t)(key >> (sbits + 10));
         }
-        int r = p / k, c = p % k;
+        int r = p % k, c = p / k;
         int64_t byte = (t * k + r) * wb + (c >> 3);
         atomicOr(tiles32 + (byte >> 2), 1u << ((int)(byte & 3) * 8 + (c & 7)));
     }
@@ -515,29 +611,51 @@ extern "C" b2sr_status b2sr_from_csr(int32_t n, const int32_t* rowptr, const int
     const int sbits = bits_for(std::max<int64_t>(ntr, 2));
     if (2 * sbits + 10 > 64) return fail(B2SR_ERR_INVALID_ARG, "matrix too large");
 
-    // validate
+    // validate; note whether every row is in column order
+    bool sorted_rows = false;
     {
         DevBuf bad(s);
-        B2SR_TRY(bad.alloc(sizeof(int)));
-        B2SR_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+        B2SR_TRY(bad.alloc(2 * sizeof(int)));
+        B2SR_CUDA_TRY(cudaMemsetAsync(bad.p, 0, 2 * sizeof(int), s));
         B2SR_TRY(validate_csr_async(n, rowptr, colind, nnz, bad.as<int>(), s));
-        int hbad = 0;
-        B2SR_CUDA_TRY(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        if (nnz > 0 && n > 0) {
+            sorted_rows_kernel<<<(unsigned)ceil_div(nnz, kKeyThreads), kKeyThreads, 0, s>>>(n, rowptr, colind, nnz,
+                                                                                            bad.as<int>() + 1);
+            B2SR_LAUNCH_CHECK("sorted_rows_kernel");
+        }
+        int hbad[2] = {0, 0};
+        B2SR_CUDA_TRY(cudaMemcpyAsync(hbad, bad.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         B2SR_CUDA_TRY(cudaStreamSynchronize(s));
-        if (hbad) return fail(B2SR_ERR_INVALID_ARG, "malformed CSR (rowptr/colind/nnz inconsistent)");
+        if (hbad[0]) return fail(B2SR_ERR_INVALID_ARG, "malformed CSR (rowptr/colind/nnz inconsistent)");
+        sorted_rows = hbad[1] == 0;
     }
 
-    // keys -> sort -> heads -> tile index
+    // keys in (tile-row, tile-column) order -> heads -> tile index
     int64_t T = 0;
     DevBuf keys(s), ktmp(s), flag(s), tidx(s);
     uint64_t* sorted = nullptr;
     if (nnz > 0) {
         B2SR_TRY(keys.alloc(nnz * sizeof(uint64_t)));
         B2SR_TRY(ktmp.alloc(nnz * sizeof(uint64_t)));
-        make_keys_kernel<<<(unsigned)ceil_div(nnz, kKeyThreads), kKeyThreads, 0, s>>>(
-            n, rowptr, colind, nnz, k, sbits, keys.as<uint64_t>());
-        B2SR_LAUNCH_CHECK("make_keys_kernel");
-        B2SR_TRY(radix_sort_u64(keys.as<uint64_t>(), ktmp.as<uint64_t>(), nnz, 10, 10 + 2 * sbits, s, &sorted));
+        const unsigned blocks = (unsigned)ceil_div(nnz, kKeyThreads);
+        if (sorted_rows) {
+            const int G = std::min(k, 8);
+            if (G == 4) rank_keys_kernel<4><<<blocks, kKeyThreads, 0, s>>>(n, rowptr, colind, nnz, k, sbits, keys.as<uint64_t>());
+            else rank_keys_kernel<8><<<blocks, kKeyThreads, 0, s>>>(n, rowptr, colind, nnz, k, sbits, keys.as<uint64_t>());
+            B2SR_LAUNCH_CHECK("rank_keys_kernel");
+            uint64_t* cur = keys.as<uint64_t>();
+            uint64_t* oth = ktmp.as<uint64_t>();
+            for (int run = G; run < k; run *= 2) {
+                merge_runs_kernel<<<grid_wide(nnz), 256, 0, s>>>(cur, oth, nnz, rowptr, n, k, run, sbits);
+                B2SR_LAUNCH_CHECK("merge_runs_kernel");
+                std::swap(cur, oth);
+            }
+            sorted = cur;
+        } else {
+            make_keys_kernel<<<blocks, kKeyThreads, 0, s>>>(n, rowptr, colind, nnz, k, sbits, keys.as<uint64_t>());
+            B2SR_LAUNCH_CHECK("make_keys_kernel");
+            B2SR_TRY(radix_sort_u64(keys.as<uint64_t>(), ktmp.as<uint64_t>(), nnz, 10, 10 + 2 * sbits, s, &sorted));
+        }
         B2SR_TRY(flag.alloc(nnz * sizeof(int32_t)));
         B2SR_TRY(tidx.alloc(nnz * sizeof(int64_t)));
         mark_heads_kernel<<<grid_wide(nnz), 256, 0, s>>>(sorted, nnz, flag.as<int32_t>());

@@ -303,6 +303,42 @@ def test_sssp_push(B, k, gi):
                     np.testing.assert_array_equal(d.view(np.uint32), to_np(B.b2sr_sssp(m, src, wb)).view(np.uint32))
 
 
+@pytest.mark.parametrize("k", KS)
+def test_sssp_push_rounds_on_a_path(B, k):
+    """Unit weights on a path from one end: one round per hop, plus the round
+    that finds nothing left to improve."""
+    g = graphs.path(203)
+    rp, ci = csr_dev(g)
+    with B.b2sr_from_csr(g.n, rp, ci, k) as m:
+        d = to_np(B.b2sr_sssp_push(m, 0))
+        np.testing.assert_array_equal(d, np.arange(g.n, dtype=np.float32))
+        assert B.b2sr_sssp_push_rounds() == g.n
+        with pytest.raises(B.B2SRError):
+            B.b2sr_sssp_push(m, 0, max_iters=5)
+        assert B.b2sr_sssp_push_rounds() == 0
+
+
+@pytest.mark.parametrize("k", KS)
+def test_sssp_push_far_set(B, k):
+    """Thresholds from below the lightest edge to past the longest path: the
+    far set holds most of the graph for the small ones, none of it for the
+    large one; every delta gives the oracle's distances."""
+    g = graphs.grid2d(45, 38)
+    w = graphs.symmetric_weights(g, 5)
+    rp, ci = csr_dev(g)
+    want = oracle.sssp(g, 7, w)
+    with B.b2sr_from_csr(g.n, rp, ci, k) as m:
+        wb = B.b2sr_weights_from_csr(m, rp, ci, to_dev(w))
+        rounds = {}
+        for delta in (0.0, 0.75, 3.0, 40.0, 1e6):
+            d = to_np(B.b2sr_sssp_push(m, 7, wb, delta=delta))
+            np.testing.assert_array_equal(d.astype(np.float64), want)
+            rounds[delta] = B.b2sr_sssp_push_rounds()
+        # narrow buckets: more raises of the threshold, fewer rounds in each
+        assert rounds[0.75] > rounds[40.0]
+        assert max(rounds.values()) <= 4 * g.n + 4
+
+
 def test_sssp_push_symmetric_uses_own_handle(B):
     g = graphs.grid2d(60, 70)
     w = graphs.symmetric_weights(g, 3)

@@ -56,6 +56,53 @@ def test_duplicates_and_unsorted_rows_are_ored(B, k):
         assert m.nnz == g.nnz
 
 
+def _sort_rows(g):
+    """The same CSR with every row in column order (repeats kept)."""
+    ci = g.colind.copy()
+    for i in range(g.n):
+        ci[g.rowptr[i]:g.rowptr[i + 1]].sort()
+    return graphs.CSR(g.n, g.rowptr.copy(), ci, None, g.name + "-sorted")
+
+
+@pytest.mark.parametrize("k", KS)
+def test_sorted_rows_with_repeats_and_hubs(B, k):
+    """Column-ordered rows take the ranking conversion: repeated columns, a
+    hub row far longer than its tile-row's other rows, and n not a multiple
+    of k must still give the oracle's arrays."""
+    g = graphs.disjoint_union(graphs.star(2503), graphs.random_directed(203, 0.07, seed=5),
+                              graphs.rmat(9, 8, seed=3))
+    gs = _sort_rows(graphs.with_duplicates(g, seed=7))
+    assert all(np.all(np.diff(gs.colind[gs.rowptr[i]:gs.rowptr[i + 1]]) >= 0) for i in range(gs.n))
+    assert gs.nnz > g.nnz and gs.n % 4 != 0
+    rp, ci = csr_dev(gs)
+    with B.b2sr_from_csr(gs.n, rp, ci, k) as m:
+        trp, tci, tiles = _oracle_arrays(g, k)
+        grp, gci, gt = B.b2sr_export(m)
+        np.testing.assert_array_equal(to_np(grp), trp)
+        np.testing.assert_array_equal(to_np(gci), tci)
+        np.testing.assert_array_equal(to_np(gt), tiles)
+        assert m.nnz == g.nnz
+
+
+@pytest.mark.parametrize("k", KS)
+def test_one_unsorted_row_gives_the_same_arrays(B, k):
+    """One row out of column order sends the whole matrix down the sorting
+    conversion; its arrays equal the sorted input's."""
+    g = graphs.rmat(10, 8, seed=11)
+    ci = g.colind.copy()
+    i = int(np.argmax(np.diff(g.rowptr)))
+    ci[g.rowptr[i]:g.rowptr[i + 1]] = ci[g.rowptr[i]:g.rowptr[i + 1]][::-1]
+    gu = graphs.CSR(g.n, g.rowptr.copy(), ci, None, "rmat10-one-reversed")
+    trp, tci, tiles = _oracle_arrays(g, k)
+    for h in (g, gu):
+        rp, cd = csr_dev(h)
+        with B.b2sr_from_csr(h.n, rp, cd, k) as m:
+            grp, gci, gt = B.b2sr_export(m)
+            np.testing.assert_array_equal(to_np(grp), trp)
+            np.testing.assert_array_equal(to_np(gci), tci)
+            np.testing.assert_array_equal(to_np(gt), tiles)
+
+
 def test_mycielskian12_sizes_from_gpu(B):
     """The paper's Sec. III-C storage sizes, produced by the GPU conversion."""
     g = graphs.mycielski(12)
