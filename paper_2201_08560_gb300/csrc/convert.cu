@@ -38,6 +38,55 @@ __global__ void validate_csr_kernel(int32_t n, const int32_t* __restrict__ rowpt
     }
 }
 
+// The validation b2sr_from_csr runs, which also finds whether every row is
+// in column order.  Row pass: the rowptr checks of validate_csr_kernel, and
+// in `starts` (one bit per entry) the entries that begin a row.
+__global__ void validate_rows_kernel(int32_t n, const int32_t* __restrict__ rowptr, int64_t nnz,
+                                     int* __restrict__ bad, uint32_t* __restrict__ starts) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0 && (rowptr[0] != 0 || (int64_t)rowptr[n] != nnz)) atomicOr(bad, 1);
+    for (int64_t i = tid; i < n; i += stride) {
+        const int32_t a = rowptr[i], b = rowptr[i + 1];
+        if (b < a) atomicOr(bad, 2);
+        if (a >= 0 && a < nnz) atomicOr(starts + (a >> 5), 1u << (a & 31));
+    }
+}
+
+// Entry pass, four entries a step: every column in [0, n) (else bit 4 of
+// *bad), and *unsorted set if an entry that does not begin a row has a
+// smaller column than the entry before it.
+__global__ void validate_entries_kernel(int32_t n, const int32_t* __restrict__ colind, int64_t nnz,
+                                        const uint32_t* __restrict__ starts, int* __restrict__ bad,
+                                        int* __restrict__ unsorted) {
+    const int64_t groups = (nnz + 3) / 4;
+    const bool vec = (reinterpret_cast<uintptr_t>(colind) & 15u) == 0;
+    bool out = false, down = false;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < groups;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e0 = g * 4;
+        int32_t c[4];
+        if (vec && e0 + 4 <= nnz) {
+            const int4 v = __ldg(reinterpret_cast<const int4*>(colind) + g);
+            c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) c[q] = e0 + q < nnz ? __ldg(colind + e0 + q) : 0;
+        }
+        const uint32_t sw = __ldg(starts + (e0 >> 5)) >> (e0 & 31);  // e0 % 4 == 0: one word holds all four
+        int32_t prev = e0 > 0 ? __ldg(colind + e0 - 1) : 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (e0 + q >= nnz) break;
+            out |= c[q] < 0 || c[q] >= n;
+            down |= e0 + q > 0 && !((sw >> q) & 1u) && prev > c[q];
+            prev = c[q];
+        }
+    }
+    if (out) atomicOr(bad, 4);
+    if (down) atomicOr(unsorted, 1);
+}
+
 // Sets *bad (device) non-zero if the CSR is malformed; stream-ordered, no sync.
 b2sr_status validate_csr_async(int32_t n, const int32_t* rowptr, const int32_t* colind, int64_t nnz, int* bad,
                                cudaStream_t s) {
@@ -49,8 +98,6 @@ b2sr_status validate_csr_async(int32_t n, const int32_t* rowptr, const int32_t* 
 // ---------------------------------------------------------------------------
 // keys
 // ---------------------------------------------------------------------------
-constexpr int kKeyThreads = 256;
-
 // largest r in [lo, hi] with rowptr[r] <= e
 __device__ __forceinline__ int32_t row_of(const int32_t* __restrict__ rowptr, int32_t lo, int32_t hi,
                                           int64_t e) {
@@ -61,90 +108,171 @@ __device__ __forceinline__ int32_t row_of(const int32_t* __restrict__ rowptr, in
     return lo;
 }
 
-__device__ __forceinline__ uint64_t entry_key(int32_t i, int32_t j, int k, int sbits) {
-    return ((uint64_t)(i / k) << (sbits + 10)) | ((uint64_t)(j / k) << 10) | (uint64_t)((j % k) * k + (i % k));
+// The entry-parallel kernels below give each thread kRankPer consecutive CSR
+// entries.  A thread finds the row of its first entry by a binary search
+// between the rows of its block's first and last entries (brow), then walks
+// forward through rows as its entries cross them.
+constexpr int kRankThreads = 256;
+constexpr int kRankPer = 8;
+constexpr int kRankEntries = kRankThreads * kRankPer;
+
+// brow[b] = row of entry b * kRankEntries for every block b < nblocks, and
+// brow[nblocks] = row of the last entry: one independent search per block, so
+// that no block starts with a chain of dependent global loads.  The entries of
+// block b lie in rows brow[b] .. brow[b+1].
+__global__ void block_rows_kernel(int32_t n, const int32_t* __restrict__ rowptr, int64_t nnz, int64_t nblocks,
+                                  int32_t* __restrict__ brow) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= nblocks;
+         b += (int64_t)gridDim.x * blockDim.x)
+        brow[b] = row_of(rowptr, 0, n - 1, b < nblocks ? b * kRankEntries : nnz - 1);
 }
 
-__global__ void __launch_bounds__(kKeyThreads) make_keys_kernel(int32_t n, const int32_t* __restrict__ rowptr,
-                                                                const int32_t* __restrict__ colind,
-                                                                int64_t nnz, int k, int sbits,
-                                                                uint64_t* __restrict__ keys) {
-    __shared__ int32_t range[2];
-    int64_t b0 = (int64_t)blockIdx.x * kKeyThreads;
-    if (b0 >= nnz) return;
-    int64_t b1 = min(b0 + kKeyThreads, nnz) - 1;
-    if (threadIdx.x == 0) range[0] = row_of(rowptr, 0, n - 1, b0);
-    if (threadIdx.x == 1) range[1] = row_of(rowptr, 0, n - 1, b1);
-    __syncthreads();
-    int64_t e = b0 + threadIdx.x;
-    if (e > b1) return;
-    int32_t i = row_of(rowptr, range[0], range[1], e);
-    keys[e] = entry_key(i, colind[e], k, sbits);
-}
+// The thread's entries [e0, e1) and the row holding e0: rows i with
+// rowptr[i] <= e < rowptr[i+1] = re.  Returns false for a thread with none.
+struct EntryRun {  // positions fit int32: the conversion takes nnz < 2^31
+    int32_t e0, e1;
+    int32_t i;
+    int32_t rs, re;  // rowptr[i], rowptr[i+1]
+};
 
-// Flags (bit 0 of *unsorted) a row whose columns decrease somewhere; repeated
-// columns keep a row sorted.
-__global__ void __launch_bounds__(kKeyThreads) sorted_rows_kernel(int32_t n, const int32_t* __restrict__ rowptr,
-                                                                  const int32_t* __restrict__ colind,
-                                                                  int64_t nnz, int* __restrict__ unsorted) {
-    __shared__ int32_t range[2];
-    int64_t b0 = (int64_t)blockIdx.x * kKeyThreads;
-    if (b0 >= nnz) return;
-    int64_t b1 = min(b0 + kKeyThreads, nnz) - 1;
-    if (threadIdx.x == 0) range[0] = row_of(rowptr, 0, n - 1, b0);
-    if (threadIdx.x == 1) range[1] = row_of(rowptr, 0, n - 1, b1);
-    __syncthreads();
-    int64_t e = b0 + threadIdx.x;
-    if (e > b1) return;
-    int32_t i = row_of(rowptr, range[0], range[1], e);
-    if (e > 0 && e > __ldg(rowptr + i) && __ldg(colind + e - 1) > __ldg(colind + e)) atomicOr(unsorted, 1);
-}
-
-// Entries of the same tile-row ahead of column j in row q: those with a
-// smaller column, and also those with column j when `ties` (q is an earlier
-// row).
-__device__ __forceinline__ int64_t count_before(const int32_t* __restrict__ colind, int64_t lo, int64_t hi,
-                                                int32_t j, bool ties) {
-    const int64_t base = lo;
+// largest r in [lo, hi] with rowptr[r] <= e (int32 positions)
+__device__ __forceinline__ int32_t row_of32(const int32_t* __restrict__ rowptr, int32_t lo, int32_t hi, int32_t e) {
     while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        int32_t x = __ldg(colind + mid);
-        if (x < j || (ties && x == j)) lo = mid + 1; else hi = mid;
+        const int32_t mid = lo + (hi - lo + 1) / 2;
+        if (__ldg(rowptr + mid) <= e) lo = mid; else hi = mid - 1;
     }
-    return lo - base;
+    return lo;
+}
+
+__device__ __forceinline__ bool entry_run(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ brow,
+                                          int32_t n, int64_t nnz, EntryRun& u) {
+    const int64_t e0 = ((int64_t)blockIdx.x * kRankThreads + threadIdx.x) * kRankPer;
+    if (e0 >= nnz) return false;
+    u.e0 = (int32_t)e0;
+    u.e1 = (int32_t)min(e0 + kRankPer, nnz);
+    u.i = row_of32(rowptr, __ldg(brow + blockIdx.x), __ldg(brow + blockIdx.x + 1), u.e0);
+    u.rs = __ldg(rowptr + u.i);
+    u.re = __ldg(rowptr + u.i + 1);
+    return true;
+}
+
+// Moves u to the row holding entry e (e >= u.rs); true if the row changed.
+// Never passes row n-1 (for a valid CSR, e < nnz lies in a row below n).
+__device__ __forceinline__ bool advance_row(const int32_t* __restrict__ rowptr, int32_t n, int32_t e, EntryRun& u) {
+    bool moved = false;
+    while (e >= u.re && u.i + 1 < n) {
+        ++u.i;
+        u.rs = u.re;
+        u.re = __ldg(rowptr + u.i + 1);
+        moved = true;
+    }
+    return moved;
+}
+
+// k is a power of two: shifts and masks instead of divisions by a runtime k.
+__device__ __forceinline__ uint64_t entry_key(int32_t i, int32_t j, int k, int sbits) {
+    const int lk = __ffs(k) - 1;
+    return ((uint64_t)(i >> lk) << (sbits + 10)) | ((uint64_t)(j >> lk) << 10) |
+           (uint64_t)(((j & (k - 1)) << lk) | (i & (k - 1)));
+}
+
+__global__ void __launch_bounds__(kRankThreads) make_keys_kernel(int32_t n, const int32_t* __restrict__ rowptr,
+                                                                 const int32_t* __restrict__ brow,
+                                                                 const int32_t* __restrict__ colind,
+                                                                 int64_t nnz, int k, int sbits,
+                                                                 uint64_t* __restrict__ keys) {
+    EntryRun u;
+    if (!entry_run(rowptr, brow, n, nnz, u)) return;
+    for (int32_t e = u.e0; e < u.e1; ++e) {
+        advance_row(rowptr, n, e, u);
+        keys[e] = entry_key(u.i, __ldg(colind + e), k, sbits);
+    }
 }
 
 // Sorted rows: writes every entry's key straight to its place in the order of
 // its group of G rows (G divides k, groups start at multiples of G).  The
 // place is the group's first CSR position, plus the entry's offset in its own
-// row, plus the entries of the group's other rows that come before it in
-// (column, row) order.
+// row, plus, for every other row q of the group, the entries of q ahead of it
+// in (column, row) order: those with a smaller column, and those with the same
+// column when q is an earlier row.  A thread's first entry in a row finds
+// those counts by binary searches (advancing side by side, so that their loads
+// overlap); its later entries in the row have columns no smaller, so each
+// count moves forward from the last one by a galloping search.
 template <int G>
-__global__ void __launch_bounds__(kKeyThreads) rank_keys_kernel(int32_t n, const int32_t* __restrict__ rowptr,
-                                                                const int32_t* __restrict__ colind,
-                                                                int64_t nnz, int k, int sbits,
-                                                                uint64_t* __restrict__ keys) {
-    __shared__ int32_t range[2];
-    int64_t b0 = (int64_t)blockIdx.x * kKeyThreads;
-    if (b0 >= nnz) return;
-    int64_t b1 = min(b0 + kKeyThreads, nnz) - 1;
-    if (threadIdx.x == 0) range[0] = row_of(rowptr, 0, n - 1, b0);
-    if (threadIdx.x == 1) range[1] = row_of(rowptr, 0, n - 1, b1);
-    __syncthreads();
-    int64_t e = b0 + threadIdx.x;
-    if (e > b1) return;
-    const int32_t i = row_of(rowptr, range[0], range[1], e);
-    const int32_t j = __ldg(colind + e);
-    const int rg = i % G;
-    const int32_t g0 = i - rg;
-    int64_t dest = (int64_t)__ldg(rowptr + g0) + (e - (int64_t)__ldg(rowptr + i));
+__global__ void __launch_bounds__(kRankThreads) rank_keys_kernel(int32_t n, const int32_t* __restrict__ rowptr,
+                                                                 const int32_t* __restrict__ brow,
+                                                                 const int32_t* __restrict__ colind,
+                                                                 int64_t nnz, int k, int sbits,
+                                                                 uint64_t* __restrict__ keys) {
+    EntryRun u;
+    if (!entry_run(rowptr, brow, n, nnz, u)) return;
+    // pos[q]: entries of row q of the group ahead of the current entry (from
+    // base[q]); end[q]: the row's end.  The entry's own row keeps an empty
+    // range.  An entry x of row q is ahead of column j when x < j + tie[q]:
+    // the same column counts as ahead in an earlier row.
+    int32_t pos[G], end[G], base[G];
+    int tie[G];
+    int32_t gstart = 0;
+    bool fresh = true;
+    for (int32_t e = u.e0; e < u.e1; ++e) {
+        fresh |= advance_row(rowptr, n, e, u);
+        const int32_t j = __ldg(colind + e);
+        if (fresh) {
+            const int rg = u.i % G;
+            const int32_t g0 = u.i - rg;
+            gstart = __ldg(rowptr + g0);
+            int32_t hi[G];
 #pragma unroll
-    for (int q = 0; q < G; ++q) {
-        const int32_t iq = g0 + q;
-        if (q == rg || iq >= n) continue;
-        dest += count_before(colind, __ldg(rowptr + iq), __ldg(rowptr + iq + 1), j, q < rg);
+            for (int q = 0; q < G; ++q) {
+                const int32_t iq = g0 + q;
+                const bool live = q != rg && iq < n;
+                pos[q] = live ? __ldg(rowptr + iq) : 0;
+                end[q] = live ? __ldg(rowptr + iq + 1) : 0;
+                base[q] = pos[q];
+                hi[q] = end[q];
+                tie[q] = q < rg ? 1 : 0;
+            }
+            // binary searches, side by side
+            for (;;) {
+                bool more = false;
+#pragma unroll
+                for (int q = 0; q < G; ++q) {
+                    if (pos[q] < hi[q]) {
+                        const int32_t mid = pos[q] + ((hi[q] - pos[q]) >> 1);
+                        if (__ldg(colind + mid) < j + tie[q]) pos[q] = mid + 1; else hi[q] = mid;
+                        more = true;
+                    }
+                }
+                if (!more) break;
+            }
+            fresh = false;
+        } else {
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                const int32_t jq = j + tie[q];
+                int32_t lo = pos[q], hi = end[q];
+                if (lo >= hi || __ldg(colind + lo) >= jq) continue;  // nothing more of row q is ahead
+                // gallop: entry lo is ahead; double the step until an entry is not
+                int32_t step = 1, last = lo;
+                while (hi - last > step) {
+                    const int32_t probe = last + step;
+                    if (__ldg(colind + probe) >= jq) { hi = probe; break; }
+                    last = probe;
+                    step <<= 1;
+                }
+                lo = last + 1;
+                while (lo < hi) {
+                    const int32_t mid = lo + ((hi - lo) >> 1);
+                    if (__ldg(colind + mid) < jq) lo = mid + 1; else hi = mid;
+                }
+                pos[q] = lo;
+            }
+        }
+        int32_t dest = gstart + (e - u.rs);
+#pragma unroll
+        for (int q = 0; q < G; ++q) dest += pos[q] - base[q];
+        keys[dest] = entry_key(u.i, j, k, sbits);
     }
-    keys[dest] = entry_key(i, j, k, sbits);
 }
 
 // One pairwise merge of sorted runs of `run` rows inside every tile-row (the
@@ -156,7 +284,7 @@ __global__ void merge_runs_kernel(const uint64_t* __restrict__ src, uint64_t* __
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
          e += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t x = src[e];
-        const int r = (int)(x & 1023u) % k;
+        const int r = (int)(x & 1023u) & (k - 1);
         const int64_t rowL = (int64_t)(x >> (sbits + 10)) * k + (r & ~(2 * run - 1));
         const int64_t a0 = __ldg(rowptr + min(rowL, (int64_t)n));
         const int64_t m = __ldg(rowptr + min(rowL + run, (int64_t)n));
@@ -173,41 +301,249 @@ __global__ void merge_runs_kernel(const uint64_t* __restrict__ src, uint64_t* __
     }
 }
 
-__global__ void mark_heads_kernel(const uint64_t* __restrict__ keys, int64_t N, int32_t* __restrict__ flag) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N;
-         e += (int64_t)gridDim.x * blockDim.x)
-        flag[e] = (e == 0 || (keys[e] >> 10) != (keys[e - 1] >> 10)) ? 1 : 0;
-}
+// Keys in order -> tiles, in two passes over the keys.  A key whose tile
+// (its bits above the low 10) differs from the previous key's is a run head:
+// the first entry of a new tile.  Pass 1 counts the heads of every block of
+// kFillTile keys; after an exclusive scan of those counts, pass 2 gives each
+// key its tile index (the block's offset plus the heads before it), writes
+// the column index of every new tile, points rowptr at the first tile of
+// every tile-row that begins there, and ORs the bits of each run of keys that
+// fall in one 32-bit word of the tile array in one atomic.
+constexpr int kFillThreads = 256;
+constexpr int kFillItems = 8;  // consecutive keys per thread
+constexpr int kFillTile = kFillThreads * kFillItems;
 
-__global__ void fill_tiles_kernel(const uint64_t* __restrict__ keys, const int32_t* __restrict__ flag,
-                                  const int64_t* __restrict__ tidx, int64_t N, int k, int sbits,
-                                  int32_t* __restrict__ colind, int32_t* __restrict__ tilerow,
-                                  uint32_t* __restrict__ tiles32) {
-    const int wb = word_bytes(k);
-    const uint64_t jmask = (1ull << sbits) - 1ull;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t key = keys[e];
-        int64_t t = tidx[e] + flag[e] - 1;  // tile of this entry's run (tidx counts heads before e)
-        int p = (int)(key & 1023u);
-        if (flag[e]) {
-            colind[t] = (int32_t)((key >> 10) & jmask);
-            tilerow[t] = (int32_t)(key >> (sbits + 10));
+// Loads keys base .. base+kFillItems-1 (those below N) and the key before base.
+__device__ __forceinline__ void load_run(const uint64_t* __restrict__ keys, int64_t N, int64_t base,
+                                         uint64_t (&key)[kFillItems], uint64_t& before) {
+    before = base > 0 && base <= N ? __ldg(keys + base - 1) : 0ull;
+    if (base + kFillItems <= N) {
+        const ulonglong2* v = reinterpret_cast<const ulonglong2*>(keys + base);  // base is a multiple of 8 keys
+#pragma unroll
+        for (int q = 0; q < kFillItems / 2; ++q) {
+            const ulonglong2 x = __ldg(v + q);
+            key[2 * q] = x.x;
+            key[2 * q + 1] = x.y;
         }
-        int r = p % k, c = p / k;
-        int64_t byte = (t * k + r) * wb + (c >> 3);
-        atomicOr(tiles32 + (byte >> 2), 1u << ((int)(byte & 3) * 8 + (c & 7)));
+    } else {
+#pragma unroll
+        for (int q = 0; q < kFillItems; ++q) key[q] = base + q < N ? __ldg(keys + base + q) : 0ull;
     }
 }
 
-// rowptr[R] = first tile of tile-row R, for every R in [0, ntr]
-__global__ void build_rowptr_kernel(const int32_t* __restrict__ tilerow, int64_t T, int32_t ntr,
-                                    int32_t* __restrict__ rowptr) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= T;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        int32_t prev = t == 0 ? -1 : tilerow[t - 1];
-        int32_t cur = t == T ? ntr : tilerow[t];
-        for (int32_t R = prev + 1; R <= cur; ++R) rowptr[R] = (int32_t)t;
+// Bit q of the result: key q of the run is a head.
+__device__ __forceinline__ uint32_t run_heads(const uint64_t (&key)[kFillItems], uint64_t before, int64_t base,
+                                              int64_t N) {
+    uint32_t h = 0;
+#pragma unroll
+    for (int q = 0; q < kFillItems; ++q) {
+        const uint64_t prev = q == 0 ? before : key[q - 1];
+        if (base + q < N && (base + q == 0 || (key[q] >> 10) != (prev >> 10))) h |= 1u << q;
+    }
+    return h;
+}
+
+// Sum of v over the block; every thread gets it.  Also returns, in *excl,
+// the sum over the threads before this one.
+__device__ __forceinline__ int block_scan(int v, int* excl) {
+    __shared__ int warp_tot[kFillThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    int before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kFillThreads / 32; ++w) {
+        const int x = warp_tot[w];
+        before += w < wid ? x : 0;
+        total += x;
+    }
+    *excl = before + inc - v;
+    return total;
+}
+
+__global__ void __launch_bounds__(kFillThreads) count_heads_kernel(const uint64_t* __restrict__ keys, int64_t N,
+                                                                   int64_t* __restrict__ sums) {
+    const int64_t base = (int64_t)blockIdx.x * kFillTile + (int64_t)threadIdx.x * kFillItems;
+    uint64_t key[kFillItems], before;
+    load_run(keys, N, base, key, before);
+    int excl;
+    const int total = block_scan(__popc(run_heads(key, before, base, N)), &excl);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// Pass 2 for k <= 8, where a tile (one byte per row) is one 64-bit word:
+// the block's keys come in coalesced through shared memory, its tiles and
+// their column indices are built in shared memory and leave in coalesced
+// stores.  Only a tile whose run of keys crosses a block boundary is ORed
+// into global memory by atomics (from both sides).
+__device__ __forceinline__ int fill_slot(int i) { return i + (i >> 4); }  // padding: no bank conflicts
+
+__global__ void __launch_bounds__(kFillThreads) fill_small_tiles_kernel(const uint64_t* __restrict__ keys, int64_t N,
+                                                                        const int64_t* __restrict__ block_off,
+                                                                        int k, int sbits, int32_t ntr, int64_t T,
+                                                                        int32_t* __restrict__ colind,
+                                                                        int32_t* __restrict__ rowptr,
+                                                                        uint32_t* __restrict__ tiles32) {
+    __shared__ uint64_t s_key[kFillTile + kFillTile / 16];
+    __shared__ unsigned long long s_tile[kFillTile];
+    __shared__ int32_t s_col[kFillTile];
+    const int64_t b0 = (int64_t)blockIdx.x * kFillTile;
+    const int cnt = (int)min((int64_t)kFillTile, N - b0);
+    {
+        uint64_t v[kFillItems];  // all loads in flight before the first store
+#pragma unroll
+        for (int q = 0; q < kFillItems; ++q) {
+            const int i = q * kFillThreads + threadIdx.x;
+            v[q] = i < cnt ? __ldg(keys + b0 + i) : 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < kFillItems; ++q) {
+            const int i = q * kFillThreads + threadIdx.x;
+            s_key[fill_slot(i)] = v[q];
+            s_tile[i] = 0ull;
+        }
+    }
+    __syncthreads();
+    const int q0 = threadIdx.x * kFillItems;
+    uint64_t key[kFillItems];
+#pragma unroll
+    for (int q = 0; q < kFillItems; ++q) key[q] = s_key[fill_slot(q0 + q)];
+    const uint64_t before = threadIdx.x > 0 ? s_key[fill_slot(q0 - 1)] : (b0 > 0 ? __ldg(keys + b0 - 1) : 0ull);
+    const uint32_t h = run_heads(key, before, b0 + q0, N);
+    int excl;
+    const int heads = block_scan(__popc(h), &excl);
+    const int64_t boff = block_off[blockIdx.x];
+    const uint64_t jmask = (1ull << sbits) - 1ull;
+    const bool wide = k == 8;
+    int lt = excl - 1;  // block-local tile of the run in progress (-1: a tile begun in an earlier block)
+    uint64_t acc = 0;
+    auto flush = [&]() {
+        if (!acc) return;
+        if (lt >= 0) {
+            atomicOr(&s_tile[lt], (unsigned long long)acc);
+        } else if (wide) {
+            atomicOr(reinterpret_cast<unsigned long long*>(tiles32) + (boff - 1), (unsigned long long)acc);
+        } else {
+            atomicOr(tiles32 + (boff - 1), (uint32_t)acc);
+        }
+        acc = 0;
+    };
+#pragma unroll
+    for (int q = 0; q < kFillItems; ++q) {
+        if (q0 + q >= cnt) break;
+        const uint64_t x = key[q];
+        if ((h >> q) & 1u) {
+            flush();
+            ++lt;
+            s_col[lt] = (int32_t)((x >> 10) & jmask);
+            const int64_t I = (int64_t)(x >> (sbits + 10));
+            const int64_t Ip = b0 + q0 + q == 0 ? -1 : (int64_t)((q == 0 ? before : key[q - 1]) >> (sbits + 10));
+            for (int64_t R = Ip + 1; R <= I; ++R) rowptr[R] = (int32_t)(boff + lt);
+        }
+        const int p = (int)(x & 1023u);
+        acc |= 1ull << ((p & (k - 1)) * 8 + (p >> (__ffs(k) - 1)));
+        if (b0 + q0 + q == N - 1)  // tile-rows after the last entry's start at T
+            for (int64_t R = (int64_t)(x >> (sbits + 10)) + 1; R <= ntr; ++R) rowptr[R] = (int32_t)T;
+    }
+    flush();
+    __syncthreads();
+    // the block's last tile goes on into the next block unless the next key starts a tile
+    const bool cut = b0 + cnt < N && (__ldg(keys + b0 + cnt) >> 10) == (s_key[fill_slot(cnt - 1)] >> 10);
+    for (int i = threadIdx.x; i < heads; i += kFillThreads) {
+        const int64_t t = boff + i;
+        colind[t] = s_col[i];
+        const unsigned long long v = s_tile[i];
+        const bool shared_tile = cut && i == heads - 1;
+        if (wide) {
+            unsigned long long* t64 = reinterpret_cast<unsigned long long*>(tiles32);
+            if (shared_tile) atomicOr(t64 + t, v); else t64[t] = v;
+        } else {
+            if (shared_tile) atomicOr(tiles32 + t, (uint32_t)v); else tiles32[t] = (uint32_t)v;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kFillThreads, 4) fill_tiles_kernel(const uint64_t* __restrict__ keys, int64_t N,
+                                                                  const int64_t* __restrict__ block_off, int k,
+                                                                  int sbits, int32_t ntr, int64_t T,
+                                                                  int32_t* __restrict__ colind,
+                                                                  int32_t* __restrict__ rowptr,
+                                                                  uint32_t* __restrict__ tiles32) {
+    const int64_t base = (int64_t)blockIdx.x * kFillTile + (int64_t)threadIdx.x * kFillItems;
+    uint64_t key[kFillItems], before;
+    load_run(keys, N, base, key, before);
+    const uint32_t h = run_heads(key, before, base, N);
+    int excl;
+    block_scan(__popc(h), &excl);
+    const int wb = word_bytes(k);
+    const uint64_t jmask = (1ull << sbits) - 1ull;
+    int64_t t = block_off[blockIdx.x] + excl - 1;  // the tile of the run in progress
+    // k <= 8: a whole tile (one byte per row) fits one 64-bit register.  A tile
+    // whose run of keys begins and ends in this thread is stored outright;
+    // only the runs cut by a thread boundary need atomics.
+    const bool whole = k <= 8;
+    bool owned = false;  // the run in progress began in this thread
+    uint64_t tacc = 0;
+    int64_t accw = -1;
+    uint32_t acc = 0;
+    auto flush_tile = [&](bool cut) {
+        if (k == 4) {
+            if (owned && !cut) tiles32[t] = (uint32_t)tacc;
+            else atomicOr(tiles32 + t, (uint32_t)tacc);
+        } else {
+            unsigned long long* t64 = reinterpret_cast<unsigned long long*>(tiles32);
+            if (owned && !cut) t64[t] = tacc;
+            else atomicOr(t64 + t, (unsigned long long)tacc);
+        }
+    };
+    int last = -1;
+    uint64_t lastkey = 0;
+#pragma unroll
+    for (int q = 0; q < kFillItems; ++q) {
+        if (base + q >= N) break;
+        last = q;
+        const uint64_t x = key[q];
+        lastkey = x;
+        if ((h >> q) & 1u) {
+            if (whole && q > 0) flush_tile(false);
+            ++t;
+            owned = true;
+            tacc = 0;
+            colind[t] = (int32_t)((x >> 10) & jmask);
+            const int64_t I = (int64_t)(x >> (sbits + 10));
+            const int64_t Ip = base + q == 0 ? -1 : (int64_t)((q == 0 ? before : key[q - 1]) >> (sbits + 10));
+            for (int64_t R = Ip + 1; R <= I; ++R) rowptr[R] = (int32_t)t;
+        }
+        const int p = (int)(x & 1023u);
+        const int r = p & (k - 1), c = p >> (__ffs(k) - 1);
+        if (whole) {
+            tacc |= 1ull << (r * 8 + c);
+        } else {
+            const int64_t byte = (t * k + r) * wb + (c >> 3);
+            if ((byte >> 2) != accw) {
+                if (accw >= 0) atomicOr(tiles32 + accw, acc);
+                accw = byte >> 2;
+                acc = 0;
+            }
+            acc |= 1u << ((int)(byte & 3) * 8 + (c & 7));
+        }
+        if (base + q == N - 1)  // tile-rows after the last entry's start at T
+            for (int64_t R = (int64_t)(x >> (sbits + 10)) + 1; R <= ntr; ++R) rowptr[R] = (int32_t)T;
+    }
+    if (last < 0) return;
+    if (whole) {
+        // the last run goes on into the next thread unless the next key starts a tile
+        const int64_t nx = base + last + 1;
+        const bool cut = nx < N && (__ldg(keys + nx) >> 10) == (lastkey >> 10);
+        flush_tile(cut);
+    } else if (accw >= 0) {
+        atomicOr(tiles32 + accw, acc);
     }
 }
 
@@ -613,15 +949,22 @@ extern "C" b2sr_status b2sr_from_csr(int32_t n, const int32_t* rowptr, const int
 
     // validate; note whether every row is in column order
     bool sorted_rows = false;
+    const int64_t blocks = ceil_div(nnz, kRankEntries);
+    DevBuf brow(s);
     {
-        DevBuf bad(s);
+        DevBuf bad(s), starts(s);
+        const size_t start_words = (size_t)ceil_div(std::max<int64_t>(nnz, 1), 32);
         B2SR_TRY(bad.alloc(2 * sizeof(int)));
+        B2SR_TRY(starts.alloc(start_words * sizeof(uint32_t)));
         B2SR_CUDA_TRY(cudaMemsetAsync(bad.p, 0, 2 * sizeof(int), s));
-        B2SR_TRY(validate_csr_async(n, rowptr, colind, nnz, bad.as<int>(), s));
-        if (nnz > 0 && n > 0) {
-            sorted_rows_kernel<<<(unsigned)ceil_div(nnz, kKeyThreads), kKeyThreads, 0, s>>>(n, rowptr, colind, nnz,
-                                                                                            bad.as<int>() + 1);
-            B2SR_LAUNCH_CHECK("sorted_rows_kernel");
+        B2SR_CUDA_TRY(cudaMemsetAsync(starts.p, 0, start_words * sizeof(uint32_t), s));
+        validate_rows_kernel<<<grid_wide((int64_t)n + 1), 256, 0, s>>>(n, rowptr, nnz, bad.as<int>(),
+                                                                      starts.as<uint32_t>());
+        B2SR_LAUNCH_CHECK("validate_rows_kernel");
+        if (nnz > 0) {
+            validate_entries_kernel<<<grid_wide(ceil_div(nnz, 4)), 256, 0, s>>>(
+                n, colind, nnz, starts.as<uint32_t>(), bad.as<int>(), bad.as<int>() + 1);
+            B2SR_LAUNCH_CHECK("validate_entries_kernel");
         }
         int hbad[2] = {0, 0};
         B2SR_CUDA_TRY(cudaMemcpyAsync(hbad, bad.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -629,19 +972,29 @@ extern "C" b2sr_status b2sr_from_csr(int32_t n, const int32_t* rowptr, const int
         if (hbad[0]) return fail(B2SR_ERR_INVALID_ARG, "malformed CSR (rowptr/colind/nnz inconsistent)");
         sorted_rows = hbad[1] == 0;
     }
+    if (nnz > 0) {
+        B2SR_TRY(brow.alloc((size_t)(blocks + 1) * sizeof(int32_t)));
+        block_rows_kernel<<<grid_for(blocks + 1), 256, 0, s>>>(n, rowptr, nnz, blocks, brow.as<int32_t>());
+        B2SR_LAUNCH_CHECK("block_rows_kernel");
+    }
 
     // keys in (tile-row, tile-column) order -> heads -> tile index
     int64_t T = 0;
-    DevBuf keys(s), ktmp(s), flag(s), tidx(s);
+    DevBuf keys(s), ktmp(s), hsum(s), hoff(s);
+    const int64_t fill_blocks = ceil_div(nnz, kFillTile);
     uint64_t* sorted = nullptr;
     if (nnz > 0) {
         B2SR_TRY(keys.alloc(nnz * sizeof(uint64_t)));
         B2SR_TRY(ktmp.alloc(nnz * sizeof(uint64_t)));
-        const unsigned blocks = (unsigned)ceil_div(nnz, kKeyThreads);
+        const int32_t* br = brow.as<int32_t>();
         if (sorted_rows) {
             const int G = std::min(k, 8);
-            if (G == 4) rank_keys_kernel<4><<<blocks, kKeyThreads, 0, s>>>(n, rowptr, colind, nnz, k, sbits, keys.as<uint64_t>());
-            else rank_keys_kernel<8><<<blocks, kKeyThreads, 0, s>>>(n, rowptr, colind, nnz, k, sbits, keys.as<uint64_t>());
+            if (G == 4)
+                rank_keys_kernel<4><<<(unsigned)blocks, kRankThreads, 0, s>>>(n, rowptr, br, colind, nnz, k, sbits,
+                                                                            keys.as<uint64_t>());
+            else
+                rank_keys_kernel<8><<<(unsigned)blocks, kRankThreads, 0, s>>>(n, rowptr, br, colind, nnz, k, sbits,
+                                                                            keys.as<uint64_t>());
             B2SR_LAUNCH_CHECK("rank_keys_kernel");
             uint64_t* cur = keys.as<uint64_t>();
             uint64_t* oth = ktmp.as<uint64_t>();
@@ -652,21 +1005,23 @@ extern "C" b2sr_status b2sr_from_csr(int32_t n, const int32_t* rowptr, const int
             }
             sorted = cur;
         } else {
-            make_keys_kernel<<<blocks, kKeyThreads, 0, s>>>(n, rowptr, colind, nnz, k, sbits, keys.as<uint64_t>());
+            make_keys_kernel<<<(unsigned)blocks, kRankThreads, 0, s>>>(n, rowptr, br, colind, nnz, k, sbits,
+                                                                     keys.as<uint64_t>());
             B2SR_LAUNCH_CHECK("make_keys_kernel");
             B2SR_TRY(radix_sort_u64(keys.as<uint64_t>(), ktmp.as<uint64_t>(), nnz, 10, 10 + 2 * sbits, s, &sorted));
         }
-        B2SR_TRY(flag.alloc(nnz * sizeof(int32_t)));
-        B2SR_TRY(tidx.alloc(nnz * sizeof(int64_t)));
-        mark_heads_kernel<<<grid_wide(nnz), 256, 0, s>>>(sorted, nnz, flag.as<int32_t>());
-        B2SR_LAUNCH_CHECK("mark_heads_kernel");
-        B2SR_TRY(exclusive_scan_i32_to_i64(flag.as<int32_t>(), tidx.as<int64_t>(), nnz, s));
-        int64_t last = 0;
-        int32_t lastf = 0;
-        B2SR_CUDA_TRY(cudaMemcpyAsync(&last, tidx.as<int64_t>() + nnz - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        B2SR_CUDA_TRY(cudaMemcpyAsync(&lastf, flag.as<int32_t>() + nnz - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        B2SR_TRY(hsum.alloc(fill_blocks * sizeof(int64_t)));
+        B2SR_TRY(hoff.alloc(fill_blocks * sizeof(int64_t)));
+        count_heads_kernel<<<(unsigned)fill_blocks, kFillThreads, 0, s>>>(sorted, nnz, hsum.as<int64_t>());
+        B2SR_LAUNCH_CHECK("count_heads_kernel");
+        B2SR_TRY(exclusive_scan_i64(hsum.as<int64_t>(), hoff.as<int64_t>(), fill_blocks, s));
+        int64_t last[2] = {0, 0};
+        B2SR_CUDA_TRY(cudaMemcpyAsync(&last[0], hoff.as<int64_t>() + fill_blocks - 1, sizeof(int64_t),
+                                      cudaMemcpyDeviceToHost, s));
+        B2SR_CUDA_TRY(cudaMemcpyAsync(&last[1], hsum.as<int64_t>() + fill_blocks - 1, sizeof(int64_t),
+                                      cudaMemcpyDeviceToHost, s));
         B2SR_CUDA_TRY(cudaStreamSynchronize(s));
-        T = last + lastf;
+        T = last[0] + last[1];
     }
 
     // outputs
@@ -685,22 +1040,21 @@ extern "C" b2sr_status b2sr_from_csr(int32_t n, const int32_t* rowptr, const int
     cudaError_t e = cudaMemsetAsync(o_colind, 0, (size_t)cap * sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(o_tiles, 0, (size_t)cap * tile_bytes(k), s);
     if (e != cudaSuccess) return release(cuda_fail(e, "memset outputs"));
-    {
-        DevBuf tilerow(s);
-        st = tilerow.alloc(std::max<int64_t>(T, 1) * sizeof(int32_t));
-        if (st != B2SR_OK) return release(st);
-        if (nnz > 0) {
-            fill_tiles_kernel<<<grid_wide(nnz), 256, 0, s>>>(sorted, flag.as<int32_t>(), tidx.as<int64_t>(), nnz, k,
-                                                            sbits, o_colind, tilerow.as<int32_t>(),
-                                                            reinterpret_cast<uint32_t*>(o_tiles));
-            note_launch();
-            e = cudaGetLastError();
-            if (e != cudaSuccess) return release(cuda_fail(e, "fill_tiles_kernel"));
-        }
-        build_rowptr_kernel<<<grid_wide(T + 1), 256, 0, s>>>(tilerow.as<int32_t>(), T, ntr, o_rowptr);
+    if (nnz > 0) {
+        if (k <= 8)
+            fill_small_tiles_kernel<<<(unsigned)fill_blocks, kFillThreads, 0, s>>>(
+                sorted, nnz, hoff.as<int64_t>(), k, sbits, ntr, T, o_colind, o_rowptr,
+                reinterpret_cast<uint32_t*>(o_tiles));
+        else
+            fill_tiles_kernel<<<(unsigned)fill_blocks, kFillThreads, 0, s>>>(sorted, nnz, hoff.as<int64_t>(), k,
+                                                                             sbits, ntr, T, o_colind, o_rowptr,
+                                                                             reinterpret_cast<uint32_t*>(o_tiles));
         note_launch();
         e = cudaGetLastError();
-        if (e != cudaSuccess) return release(cuda_fail(e, "build_rowptr_kernel"));
+        if (e != cudaSuccess) return release(cuda_fail(e, "fill_tiles_kernel"));
+    } else {
+        e = cudaMemsetAsync(o_rowptr, 0, ((size_t)ntr + 1) * sizeof(int32_t), s);
+        if (e != cudaSuccess) return release(cuda_fail(e, "memset rowptr"));
     }
     b2sr_matrix* h = nullptr;
     st = new_handle_from_tiles(n, k, T, o_rowptr, o_colind, o_tiles, cap, s, &h);

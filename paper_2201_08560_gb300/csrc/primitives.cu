@@ -120,24 +120,29 @@ __global__ void __launch_bounds__(kScanThreads) scan_block_sums(const TIn* __res
     }
 }
 
+// Shared-memory slot of tile item i: one pad word per 16 keeps both the
+// striped (item j * kScanThreads + t) and the blocked (item t * kScanItems + j)
+// accesses of 64-bit words free of bank conflicts.
+__device__ __forceinline__ int scan_slot(int i) { return i + (i >> 4); }
+
 // Exclusive scan of one tile of kScanTile items, plus a per-block offset.
 template <class TIn>
 __global__ void __launch_bounds__(kScanThreads) scan_tiles(const TIn* __restrict__ in, int64_t n,
                                                            int64_t* __restrict__ out,
                                                            const int64_t* __restrict__ block_off) {
-    __shared__ int64_t sm[kScanTile];
+    __shared__ int64_t sm[kScanTile + kScanTile / 16];
     __shared__ int64_t warp_tot[kScanThreads / 32];
     int64_t base = (int64_t)blockIdx.x * kScanTile;
     for (int j = 0; j < kScanItems; ++j) {
         int64_t i = base + j * kScanThreads + threadIdx.x;
-        sm[j * kScanThreads + threadIdx.x] = i < n ? (int64_t)in[i] : 0;
+        sm[scan_slot(j * kScanThreads + threadIdx.x)] = i < n ? (int64_t)in[i] : 0;
     }
     __syncthreads();
     int64_t v[kScanItems];
     int64_t run = 0;
     for (int j = 0; j < kScanItems; ++j) {
         v[j] = run;
-        run += sm[threadIdx.x * kScanItems + j];
+        run += sm[scan_slot(threadIdx.x * kScanItems + j)];
     }
     // warp inclusive scan of per-thread totals
     int64_t inc = run;
@@ -158,11 +163,11 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles(const TIn* __restrict
     }
     __syncthreads();
     int64_t off = (block_off ? block_off[blockIdx.x] : 0) + warp_tot[threadIdx.x >> 5] + (inc - run);
-    for (int j = 0; j < kScanItems; ++j) sm[threadIdx.x * kScanItems + j] = v[j] + off;
+    for (int j = 0; j < kScanItems; ++j) sm[scan_slot(threadIdx.x * kScanItems + j)] = v[j] + off;
     __syncthreads();
     for (int j = 0; j < kScanItems; ++j) {
         int64_t i = base + j * kScanThreads + threadIdx.x;
-        if (i < n) out[i] = sm[j * kScanThreads + threadIdx.x];
+        if (i < n) out[i] = sm[scan_slot(j * kScanThreads + threadIdx.x)];
     }
 }
 

@@ -2,6 +2,7 @@
 and the weight side array, element by element against the CPU oracle."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 from paper_2201_08560_gb300 import graphs
@@ -101,6 +102,23 @@ def test_one_unsorted_row_gives_the_same_arrays(B, k):
             np.testing.assert_array_equal(to_np(grp), trp)
             np.testing.assert_array_equal(to_np(gci), tci)
             np.testing.assert_array_equal(to_np(gt), tiles)
+
+
+@pytest.mark.parametrize("k", [4, 8])
+def test_column_array_off_a_16_byte_boundary(B, k):
+    """colind that starts 4 bytes past an aligned address (a view into a
+    larger buffer): the validation's vector loads must not be used on it."""
+    g = graphs.rmat(9, 8, seed=21)
+    rp, ci = csr_dev(g)
+    buf = torch.zeros(ci.numel() + 1, dtype=torch.int32, device=ci.device)
+    buf[1:] = ci
+    view = buf[1:]
+    assert view.data_ptr() % 16 != 0
+    trp, tci, tiles = _oracle_arrays(g, k)
+    with B.b2sr_from_csr(g.n, rp, view, k) as m:
+        grp, gci, gt = B.b2sr_export(m)
+        np.testing.assert_array_equal(to_np(gci), tci)
+        np.testing.assert_array_equal(to_np(gt), tiles)
 
 
 def test_mycielskian12_sizes_from_gpu(B):
