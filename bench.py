@@ -437,14 +437,20 @@ def batching_extra(B, dev, big, arena_gs, arena_scales):
                                "speedup": t_plain / t_multi, "nnz": int(ci.size),
                                "batched_gteps": MS_SOURCES * ci.size / (t_multi / 1e3) / 1e9}
     del rp_d, ci_d
+    # the arena and the separate graphs run at the tile size and schedule the
+    # autotuner chose above for the same scheme (Boolean BFS) on R-MAT graphs
+    a_tile, a_sched = int(rep["tile_dim"]), int(rep["schedule"])
     gs = arena_gs
     csrs = [(gn, torch.from_numpy(grp).to(dev), torch.from_numpy(gci).to(dev)) for gn, grp, gci in gs]
-    arena, bases = B.b2sr_from_csr_batch(csrs, EXTRA_TILE)
+    arena, bases = B.b2sr_from_csr_batch(csrs, a_tile)
+    B.b2sr_set_schedule(arena, a_sched)
     srcs_a = [int(bases[i]) for i in range(len(gs))]  # vertex 0 of every graph (its hub)
     with arena:
         lva = torch.empty(arena.n, dtype=torch.int32, device=dev)
         t_arena = _timed(lambda: B.b2sr_bfs_sources(arena, srcs_a, lva))
-        mats = [B.b2sr_from_csr(gn, grp, gci, EXTRA_TILE) for gn, grp, gci in csrs]
+        mats = [B.b2sr_from_csr(gn, grp, gci, a_tile) for gn, grp, gci in csrs]
+        for mm in mats:
+            B.b2sr_set_schedule(mm, a_sched)
         outs = [torch.empty(gn, dtype=torch.int32, device=dev) for gn, _, _ in csrs]
 
         def per_graph():
@@ -456,6 +462,7 @@ def batching_extra(B, dev, big, arena_gs, arena_scales):
         for mm in mats:
             mm.close()
         out["arena_256_graphs"] = {"graphs": len(gs), "scales": arena_scales, "arena_n": int(arena.n),
+                                   "tile_dim": a_tile, "schedule": a_sched,
                                    "arena_ms": t_arena, "per_graph_ms": t_each,
                                    "graphs_per_s_arena": len(gs) / (t_arena / 1e3),
                                    "graphs_per_s_per_graph": len(gs) / (t_each / 1e3),
@@ -521,9 +528,14 @@ class ClockSampler:
 # our arm
 # ---------------------------------------------------------------------------
 
-def traffic_for(family, tile, kname):
+def traffic_key(permute):
+    """Names the graph a traffic figure was taken on."""
+    return f"rmat{SCALE}" + ("" if permute is None else f"_perm{permute}")
+
+
+def traffic_for(family, tile, kname, graph):
     """dram bytes per launch from the committed ncu summary, if it was taken on
-    the same kernel, tile_dim and kernel source (else None)."""
+    the same kernel, tile_dim, graph and kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2201_08560_gb300", "csrc", "spmv.cu")
     try:
@@ -531,7 +543,7 @@ def traffic_for(family, tile, kname):
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
         for ent in rec.values():
             if (ent.get("family") == family and ent.get("tile_dim") == tile and ent.get("kernel", "").startswith(kname)
-                    and ent.get("kernel_source_sha256") == sha):
+                    and ent.get("graph") == graph and ent.get("kernel_source_sha256") == sha):
                 return float(ent["dram_bytes_per_launch"]), ent
     except Exception:
         pass
@@ -631,7 +643,7 @@ def timed_steps(B, step, args, barrier, uuid=None):
     return ev0.elapsed_time(ev1), fam, launches, (clk.summary() if clk is not None else None)
 
 
-def roofline_of(fam, ms_total, peak, peak_src, tile, schedule):
+def roofline_of(fam, ms_total, peak, peak_src, tile, schedule, graph):
     """Roofline entry of the family with the most device time in a timed
     region: algorithmic bytes per launch over its average CUDA-event launch
     time, against the measured copy bandwidth."""
@@ -641,7 +653,7 @@ def roofline_of(fam, ms_total, peak, peak_src, tile, schedule):
     d = fam[dom]
     achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
     kname = spmv_kernel_name(dom, tile, schedule)
-    traffic, _ = traffic_for(dom, tile, kname)
+    traffic, _ = traffic_for(dom, tile, kname, graph)
     return {"bound": "hbm", "kernel": f"{kname} ({dom}, k={tile})", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
             "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
@@ -861,7 +873,7 @@ def main():
         return 0
 
     peak, peak_src = measured_peak()
-    roofline = roofline_of(fam, ms_total, peak, peak_src, TILE, SCHEDULE)
+    roofline = roofline_of(fam, ms_total, peak, peak_src, TILE, SCHEDULE, traffic_key(PERMUTE))
     extra = {}
 
     # ---- extras: batched vs plain BFS, Boolean SpMV alone ----
@@ -978,7 +990,8 @@ def main():
             "workload": f"R-MAT scale {SCALE} ef{EDGE_FACTOR} seed {SEED}, ids permuted (seed {PERM_SEED}); "
                         f"the same step, tile_dim {TILE}", "nnz": int(pci.size),
             "gteps": QUERIES_PER_STEP * int(pci.size) * args.steps / (pms / 1e3) / 1e9,
-            "ms_per_step": pms / args.steps, "roofline": roofline_of(pfam, pms, peak, peak_src, TILE, SCHEDULE),
+            "ms_per_step": pms / args.steps, "roofline": roofline_of(pfam, pms, peak, peak_src, TILE, SCHEDULE,
+                                                                 traffic_key(PERM_SEED)),
             "kernel_breakdown_ms_per_step": {f: pfam[f]["ms"] / args.steps for f in pfam}}
         del plev
         # config 2's tile_dim sweep of the Boolean and plus-times SpMVs, unpermuted and permuted

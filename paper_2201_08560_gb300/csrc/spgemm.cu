@@ -35,9 +35,11 @@ __device__ __forceinline__ uint64_t tile_word64(const uint8_t* __restrict__ tile
     return __ldg(reinterpret_cast<const uint32_t*>(tiles) + t);
 }
 
-__device__ __forceinline__ int64_t lower_bound_i32(const int32_t* __restrict__ a, int64_t lo, int64_t hi, int32_t v) {
+// Tile positions fit int32 (a handle holds fewer than 2^31 tiles), which keeps
+// the searches' arithmetic 32-bit.
+__device__ __forceinline__ int32_t lower_bound_i32(const int32_t* __restrict__ a, int32_t lo, int32_t hi, int32_t v) {
     while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
+        const int32_t mid = lo + ((hi - lo) >> 1);
         if (__ldg(a + mid) < v) lo = mid + 1; else hi = mid;
     }
     return lo;
@@ -87,19 +89,19 @@ __global__ void masked_count_kernel(MatView A, MatView B, MatView M, unsigned lo
 #pragma unroll
             for (int r = 0; r < K; ++r) mrow[r] = gword<K>(M.tiles, mt, r);
         }
-        const int64_t a0 = __ldg(A.rowptr + I), a1 = __ldg(A.rowptr + I + 1);
-        const int64_t b0 = __ldg(B.rowptr + J), b1 = __ldg(B.rowptr + J + 1);
+        const int32_t a0 = __ldg(A.rowptr + I), a1 = __ldg(A.rowptr + I + 1);
+        const int32_t b0 = __ldg(B.rowptr + J), b1 = __ldg(B.rowptr + J + 1);
         const bool a_short = (a1 - a0) <= (b1 - b0);
-        const int64_t s0 = a_short ? a0 : b0, s1 = a_short ? a1 : b1;
-        const int64_t l0 = a_short ? b0 : a0, l1 = a_short ? b1 : a1;
+        const int32_t s0 = a_short ? a0 : b0, s1 = a_short ? a1 : b1;
+        const int32_t l0 = a_short ? b0 : a0, l1 = a_short ? b1 : a1;
         const int32_t* scol = a_short ? A.colind : B.colind;
         const int32_t* lcol = a_short ? B.colind : A.colind;
-        for (int64_t p = s0 + lane; p < s1; p += 32) {
+        for (int32_t p = s0 + lane; p < s1; p += 32) {
             const int32_t Kc = __ldg(scol + p);
-            const int64_t q = lower_bound_i32(lcol, l0, l1, Kc);
+            const int32_t q = lower_bound_i32(lcol, l0, l1, Kc);
             if (q >= l1 || __ldg(lcol + q) != Kc) continue;
-            const int64_t ta = a_short ? p : q;  // tile A_IK
-            const int64_t tb = a_short ? q : p;  // tile B_JK
+            const int32_t ta = a_short ? p : q;  // tile A_IK
+            const int32_t tb = a_short ? q : p;  // tile B_JK
             if constexpr (K <= 8) {
                 const uint64_t aw = tile_word64<K>(A.tiles, ta), bw = tile_word64<K>(B.tiles, tb);
                 uint64_t m = mw;
