@@ -709,6 +709,28 @@ __global__ void i64_to_i32_kernel(const int64_t* __restrict__ in, int64_t n, int
         out[i] = (int32_t)in[i];
 }
 
+// k = 4: four tiles (16 bytes of words, 16 of column indices) per thread and
+// step; the padding after T is zero, so whole groups of four can be read.
+// Column c of a tile word (row r in byte r) counts popc(w & (0x01010101 << c)).
+__global__ void col_count4_kernel(const int32_t* __restrict__ colind, const uint8_t* __restrict__ tiles,
+                                  int64_t groups, int32_t* __restrict__ deg) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < groups;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4*>(tiles) + g);
+        const int4 J = __ldg(reinterpret_cast<const int4*>(colind) + g);
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+        const int32_t js[4] = {J.x, J.y, J.z, J.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int v = __popc(ws[q] & (0x01010101u << c));
+                if (v) atomicAdd(deg + (int64_t)js[q] * 4 + c, v);
+            }
+        }
+    }
+}
+
 template <int K>
 __global__ void col_count_kernel(const int32_t* __restrict__ colind, const uint8_t* __restrict__ tiles,
                                  int64_t T, int32_t n, int32_t* __restrict__ deg) {
@@ -781,7 +803,10 @@ b2sr_status ensure_outdeg(b2sr_matrix* h, cudaStream_t s) {
     if (e != cudaSuccess) { dfree(deg, s); return cuda_fail(e, "memset outdeg"); }
     b2sr_status st = with_tile(h->k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
-        if (h->T > 0) col_count_kernel<K><<<grid_wide(h->T), 256, 0, s>>>(h->colind, h->tiles, h->T, h->n, deg);
+        if (h->T > 0 && K == 4)  // cap is a multiple of 512 tiles: groups of four stay inside the arrays
+            col_count4_kernel<<<grid_wide(ceil_div(h->T, 4)), 256, 0, s>>>(h->colind, h->tiles, ceil_div(h->T, 4), deg);
+        else if (h->T > 0)
+            col_count_kernel<K><<<grid_wide(h->T), 256, 0, s>>>(h->colind, h->tiles, h->T, h->n, deg);
         B2SR_LAUNCH_CHECK("col_count_kernel");
         return B2SR_OK;
     });

@@ -797,6 +797,22 @@ __device__ __forceinline__ void close_chunk(const SEM& sem, Partials<typename SE
     if (close_here) sem.store(first_row, F);
 }
 
+// 16 / 8 bytes of the tile stream in one load, not allocated in L1: each tile
+// is read once, and L1 is left to the input-vector gathers.
+__device__ __forceinline__ uint4 ld16_stream(const void* p) {
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];\n"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint2 ld8_stream(const void* p) {
+    uint2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];\n" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+
 template <int K>
 __device__ __forceinline__ void load_lane_tiles(const SpmvGeom& g, int32_t tl, uint4 (&tv)[ChunkShape<K>::TILE_V4],
                                                 int32_t (&col)[ChunkShape<K>::P]) {
@@ -804,20 +820,21 @@ __device__ __forceinline__ void load_lane_tiles(const SpmvGeom& g, int32_t tl, u
     constexpr int P = S::P;
     const uint4* src = reinterpret_cast<const uint4*>(g.tiles + (int64_t)tl * S::TB);
 #pragma unroll
-    for (int q = 0; q < S::TILE_V4; ++q) tv[q] = __ldg(src + q);
+    for (int q = 0; q < S::TILE_V4; ++q) tv[q] = ld16_stream(src + q);
     if constexpr (P % 4 == 0) {
-        const int4* cs = reinterpret_cast<const int4*>(g.colind + tl);
+        const uint4* cs = reinterpret_cast<const uint4*>(g.colind + tl);
 #pragma unroll
         for (int q = 0; q < P / 4; ++q) {
-            int4 v = __ldg(cs + q);
-            col[4 * q] = v.x; col[4 * q + 1] = v.y; col[4 * q + 2] = v.z; col[4 * q + 3] = v.w;
+            const uint4 v = ld16_stream(cs + q);
+            col[4 * q] = (int32_t)v.x; col[4 * q + 1] = (int32_t)v.y; col[4 * q + 2] = (int32_t)v.z;
+            col[4 * q + 3] = (int32_t)v.w;
         }
     } else {
-        const int2* cs = reinterpret_cast<const int2*>(g.colind + tl);
+        const uint2* cs = reinterpret_cast<const uint2*>(g.colind + tl);
 #pragma unroll
         for (int q = 0; q < P / 2; ++q) {
-            int2 v = __ldg(cs + q);
-            col[2 * q] = v.x; col[2 * q + 1] = v.y;
+            const uint2 v = ld8_stream(cs + q);
+            col[2 * q] = (int32_t)v.x; col[2 * q + 1] = (int32_t)v.y;
         }
     }
 }
