@@ -96,9 +96,11 @@ __global__ void masked_count_kernel(MatView A, MatView B, MatView M, unsigned lo
         const int32_t l0 = a_short ? b0 : a0, l1 = a_short ? b1 : a1;
         const int32_t* scol = a_short ? A.colind : B.colind;
         const int32_t* lcol = a_short ? B.colind : A.colind;
+        int32_t from = l0;  // a lane's entries rise, so each search starts where its last one ended
         for (int32_t p = s0 + lane; p < s1; p += 32) {
             const int32_t Kc = __ldg(scol + p);
-            const int32_t q = lower_bound_i32(lcol, l0, l1, Kc);
+            const int32_t q = lower_bound_i32(lcol, from, l1, Kc);
+            from = q;
             if (q >= l1 || __ldg(lcol + q) != Kc) continue;
             const int32_t ta = a_short ? p : q;  // tile A_IK
             const int32_t tb = a_short ? q : p;  // tile B_JK

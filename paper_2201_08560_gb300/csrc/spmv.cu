@@ -797,8 +797,25 @@ __device__ __forceinline__ void close_chunk(const SEM& sem, Partials<typename SE
     if (close_here) sem.store(first_row, F);
 }
 
-// 16 / 8 bytes of the tile stream in one load, not allocated in L1: each tile
-// is read once, and L1 is left to the input-vector gathers.
+// 32 bytes from global memory in one load, not allocated in L1: each tile
+// is read once, and L1 is left to the input-vector gathers.  A whole 32-byte
+// sector per instruction: narrower no-allocate loads would fetch a sector
+// again for every part of it.
+__device__ __forceinline__ void ld32_stream(const void* p, uint32_t (&v)[8]) {
+    asm volatile("ld.global.nc.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "l"(p));
+}
+
+// The same load without `volatile`: the compiler may schedule it with the
+// other loads of the lane (the data is read-only while a kernel runs).
+__device__ __forceinline__ void ld32_stream_free(const void* p, uint32_t (&v)[8]) {
+    asm("ld.global.nc.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+        : "l"(p));
+}
+
+// 16 bytes, not allocated in L1.
 __device__ __forceinline__ uint4 ld16_stream(const void* p) {
     uint4 v;
     asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];\n"
@@ -807,34 +824,50 @@ __device__ __forceinline__ uint4 ld16_stream(const void* p) {
     return v;
 }
 
-__device__ __forceinline__ uint2 ld8_stream(const void* p) {
-    uint2 v;
-    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];\n" : "=r"(v.x), "=r"(v.y) : "l"(p));
-    return v;
-}
-
 template <int K>
 __device__ __forceinline__ void load_lane_tiles(const SpmvGeom& g, int32_t tl, uint4 (&tv)[ChunkShape<K>::TILE_V4],
                                                 int32_t (&col)[ChunkShape<K>::P]) {
     using S = ChunkShape<K>;
     constexpr int P = S::P;
-    const uint4* src = reinterpret_cast<const uint4*>(g.tiles + (int64_t)tl * S::TB);
+    // a lane's P tiles are P * TB = 32, 64, 128 or 256 bytes, 32-byte aligned (tl is a multiple of P)
+    static_assert(S::TILE_V4 % 2 == 0, "whole 32-byte sectors of tiles per lane");
+    const uint8_t* src = g.tiles + (int64_t)tl * S::TB;
+    if constexpr (K == 4) {
+        // k = 4 (32 bytes of tiles and of columns a lane): two 16-byte loads
+        // each measured faster here than one 32-byte load (161 against 166 us
+        // for the plus-times SpMV on R-MAT 20); from k = 8 the 32-byte load wins
 #pragma unroll
-    for (int q = 0; q < S::TILE_V4; ++q) tv[q] = ld16_stream(src + q);
-    if constexpr (P % 4 == 0) {
-        const uint4* cs = reinterpret_cast<const uint4*>(g.colind + tl);
+        for (int q = 0; q < S::TILE_V4; ++q) tv[q] = ld16_stream(src + 16 * q);
+        const uint4 c0 = ld16_stream(g.colind + tl), c1 = ld16_stream(g.colind + tl + 4);
+        col[0] = (int32_t)c0.x; col[1] = (int32_t)c0.y; col[2] = (int32_t)c0.z; col[3] = (int32_t)c0.w;
+        col[4] = (int32_t)c1.x; col[5] = (int32_t)c1.y; col[6] = (int32_t)c1.z; col[7] = (int32_t)c1.w;
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < S::TILE_V4 / 2; ++q) {
+        uint32_t v[8];
+        ld32_stream_free(src + 32 * q, v);
+        tv[2 * q] = make_uint4(v[0], v[1], v[2], v[3]);
+        tv[2 * q + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+    }
+    if constexpr (P == 8) {  // 32 bytes of column indices: one sector
+        uint32_t v[8];
+        ld32_stream_free(g.colind + tl, v);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) col[i] = (int32_t)v[i];
+    } else if constexpr (P % 4 == 0) {  // lanes share sectors: cached loads
+        const int4* cs = reinterpret_cast<const int4*>(g.colind + tl);
 #pragma unroll
         for (int q = 0; q < P / 4; ++q) {
-            const uint4 v = ld16_stream(cs + q);
-            col[4 * q] = (int32_t)v.x; col[4 * q + 1] = (int32_t)v.y; col[4 * q + 2] = (int32_t)v.z;
-            col[4 * q + 3] = (int32_t)v.w;
+            int4 v = __ldg(cs + q);
+            col[4 * q] = v.x; col[4 * q + 1] = v.y; col[4 * q + 2] = v.z; col[4 * q + 3] = v.w;
         }
     } else {
-        const uint2* cs = reinterpret_cast<const uint2*>(g.colind + tl);
+        const int2* cs = reinterpret_cast<const int2*>(g.colind + tl);
 #pragma unroll
         for (int q = 0; q < P / 2; ++q) {
-            const uint2 v = ld8_stream(cs + q);
-            col[2 * q] = (int32_t)v.x; col[2 * q + 1] = (int32_t)v.y;
+            int2 v = __ldg(cs + q);
+            col[2 * q] = v.x; col[2 * q + 1] = v.y;
         }
     }
 }
@@ -954,12 +987,6 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
 // two chunks' tile words and columns)
 constexpr int kK4MinBlocks = 4;
 
-// 32 bytes from global memory in one load, not allocated in L1
-__device__ __forceinline__ void ld32_stream(const void* p, uint32_t (&v)[8]) {
-    asm volatile("ld.global.nc.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                 : "l"(p));
-}
 
 // The tile stream of one chunk as a lane holds it: the chunk's first and last
 // tile-rows and their row pointers (lane j: rowptr[ra + j]), whether every
