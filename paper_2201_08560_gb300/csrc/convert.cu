@@ -709,11 +709,26 @@ __global__ void i64_to_i32_kernel(const int64_t* __restrict__ in, int64_t n, int
         out[i] = (int32_t)in[i];
 }
 
+// Column counts go to `copies` copies of the count array (warp w adds into
+// copy w % copies), summed at the end: the hub columns' atomics spread over
+// several addresses, and so over several L2 slices, instead of queueing on one.
+constexpr int kDegCopies = 8;
+
+__global__ void deg_sum_kernel(const int32_t* __restrict__ sub, int64_t stride, int copies, int64_t len,
+                               int32_t* __restrict__ deg) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v = 0;
+        for (int c = 0; c < copies; ++c) v += __ldg(sub + c * stride + i);
+        deg[i] = v;
+    }
+}
+
 // k = 4: four tiles (16 bytes of words, 16 of column indices) per thread and
 // step; the padding after T is zero, so whole groups of four can be read.
 // Column c of a tile word (row r in byte r) counts popc(w & (0x01010101 << c)).
 __global__ void col_count4_kernel(const int32_t* __restrict__ colind, const uint8_t* __restrict__ tiles,
-                                  int64_t groups, int32_t* __restrict__ deg) {
+                                  int64_t groups, int32_t* __restrict__ sub, int64_t stride, int copies) {
+    int32_t* __restrict__ deg = sub + (int64_t)((threadIdx.x >> 5) % copies) * stride;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < groups;
          g += (int64_t)gridDim.x * blockDim.x) {
         const uint4 w = __ldg(reinterpret_cast<const uint4*>(tiles) + g);
@@ -733,7 +748,8 @@ __global__ void col_count4_kernel(const int32_t* __restrict__ colind, const uint
 
 template <int K>
 __global__ void col_count_kernel(const int32_t* __restrict__ colind, const uint8_t* __restrict__ tiles,
-                                 int64_t T, int32_t n, int32_t* __restrict__ deg) {
+                                 int64_t T, int32_t* __restrict__ sub, int64_t stride, int copies) {
+    int32_t* __restrict__ deg = sub + (int64_t)((threadIdx.x >> 5) % copies) * stride;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
          t += (int64_t)gridDim.x * blockDim.x) {
         int64_t J = colind[t];
@@ -797,17 +813,27 @@ b2sr_status ensure_voff(b2sr_matrix* h, cudaStream_t s) {
 b2sr_status ensure_outdeg(b2sr_matrix* h, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(*static_cast<std::mutex*>(h->mtx));
     if (h->outdeg) return B2SR_OK;
+    const int64_t len = (int64_t)h->ntr * h->k;
     int32_t* deg = nullptr;
-    B2SR_TRY(dalloc(&deg, (size_t)h->ntr * h->k, s));
-    cudaError_t e = cudaMemsetAsync(deg, 0, (size_t)h->ntr * h->k * sizeof(int32_t), s);
+    B2SR_TRY(dalloc(&deg, (size_t)len, s));
+    // copies while they stay under 1 GiB in all
+    const int copies = (int)std::max<int64_t>(1, std::min<int64_t>(kDegCopies, (int64_t(1) << 30) / (len * 4 + 1)));
+    DevBuf sub(s);
+    b2sr_status st = sub.alloc((size_t)copies * len * sizeof(int32_t));
+    if (st != B2SR_OK) { dfree(deg, s); return st; }
+    cudaError_t e = cudaMemsetAsync(sub.p, 0, (size_t)copies * len * sizeof(int32_t), s);
     if (e != cudaSuccess) { dfree(deg, s); return cuda_fail(e, "memset outdeg"); }
-    b2sr_status st = with_tile(h->k, [&](auto kc) -> b2sr_status {
+    st = with_tile(h->k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
         if (h->T > 0 && K == 4)  // cap is a multiple of 512 tiles: groups of four stay inside the arrays
-            col_count4_kernel<<<grid_wide(ceil_div(h->T, 4)), 256, 0, s>>>(h->colind, h->tiles, ceil_div(h->T, 4), deg);
+            col_count4_kernel<<<grid_wide(ceil_div(h->T, 4)), 256, 0, s>>>(h->colind, h->tiles, ceil_div(h->T, 4),
+                                                                          sub.as<int32_t>(), len, copies);
         else if (h->T > 0)
-            col_count_kernel<K><<<grid_wide(h->T), 256, 0, s>>>(h->colind, h->tiles, h->T, h->n, deg);
+            col_count_kernel<K><<<grid_wide(h->T), 256, 0, s>>>(h->colind, h->tiles, h->T, sub.as<int32_t>(), len,
+                                                                copies);
         B2SR_LAUNCH_CHECK("col_count_kernel");
+        deg_sum_kernel<<<grid_wide(len), 256, 0, s>>>(sub.as<int32_t>(), len, copies, len, deg);
+        B2SR_LAUNCH_CHECK("deg_sum_kernel");
         return B2SR_OK;
     });
     if (st == B2SR_OK) {
