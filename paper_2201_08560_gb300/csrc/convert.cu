@@ -892,57 +892,70 @@ __device__ __forceinline__ uint32_t strict_lower_mask(int r) {  // columns c < r
     return r == 0 ? 0u : ((r >= 32) ? 0xffffffffu : ((1u << r) - 1u));
 }
 
+// A tile-row's tiles are in column order, so those strictly left of the
+// diagonal are a prefix, found by one binary search; the diagonal tile, if
+// present, follows it and keeps only its bits below the diagonal.
 template <int K>
-__global__ void lower_count_kernel(const int32_t* __restrict__ trp, const int32_t* __restrict__ tci,
-                                   const uint8_t* __restrict__ tiles, int32_t ntr, int32_t* __restrict__ cnt) {
-    for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < ntr;
-         I += (int64_t)gridDim.x * blockDim.x) {
-        int c = 0;
-        for (int64_t t = trp[I]; t < trp[I + 1]; ++t) {
-            int32_t J = tci[t];
-            if (J < I) { ++c; continue; }
-            if (J > I) break;
-            uint32_t any = 0;
+__device__ __forceinline__ bool diag_has_lower(const uint8_t* __restrict__ tiles, int64_t t) {
+    uint32_t any = 0;
 #pragma unroll
-            for (int r = 0; r < K; ++r) any |= tile_word<K>(tiles, t, r) & strict_lower_mask<K>(r);
-            c += any ? 1 : 0;
-        }
-        cnt[I] = c;
-    }
+    for (int r = 0; r < K; ++r) any |= tile_word<K>(tiles, t, r) & strict_lower_mask<K>(r);
+    return any != 0;
 }
 
 template <int K>
-__global__ void lower_fill_kernel(const int32_t* __restrict__ trp, const int32_t* __restrict__ tci,
-                                  const uint8_t* __restrict__ tiles, int32_t ntr,
-                                  const int64_t* __restrict__ off, int32_t* __restrict__ lrp,
-                                  int32_t* __restrict__ lci, uint8_t* __restrict__ ltiles) {
-    constexpr int WB = K <= 8 ? 1 : (K == 16 ? 2 : 4);
-    for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I <= ntr;
+__global__ void lower_count_kernel(const int32_t* __restrict__ trp, const int32_t* __restrict__ tci,
+                                   const uint8_t* __restrict__ tiles, int32_t ntr, int32_t* __restrict__ cnt,
+                                   int32_t* __restrict__ pre) {
+    for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < ntr;
          I += (int64_t)gridDim.x * blockDim.x) {
-        lrp[I] = (int32_t)off[I];
+        const int32_t t0 = __ldg(trp + I), t1 = __ldg(trp + I + 1);
+        int32_t lo = t0, hi = t1;  // first tile with column >= I
+        while (lo < hi) {
+            const int32_t mid = lo + ((hi - lo) >> 1);
+            if (__ldg(tci + mid) < I) lo = mid + 1; else hi = mid;
+        }
+        pre[I] = lo - t0;
+        cnt[I] = lo - t0 + ((lo < t1 && __ldg(tci + lo) == I && diag_has_lower<K>(tiles, lo)) ? 1 : 0);
+    }
+}
+
+// A warp per tile-row: the lanes copy the prefix tile by tile (coalesced),
+// then lane 0 writes the masked diagonal tile.
+template <int K>
+__global__ void lower_fill_kernel(const int32_t* __restrict__ trp, const int32_t* __restrict__ tci,
+                                  const uint8_t* __restrict__ tiles, int32_t ntr, const int64_t* __restrict__ off,
+                                  const int32_t* __restrict__ pre, int32_t* __restrict__ lrp,
+                                  int32_t* __restrict__ lci, uint8_t* __restrict__ ltiles) {
+    constexpr int TB = K * (K <= 8 ? 1 : (K == 16 ? 2 : 4));  // bytes per tile
+    constexpr int TW = (TB + 3) / 4;                            // 32-bit words per tile
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t I = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; I <= ntr; I += warps) {
+        const int64_t o = off[I];
+        if (lane == 0) lrp[I] = (int32_t)o;
         if (I == ntr) continue;
-        int64_t w = off[I];
-        for (int64_t t = trp[I]; t < trp[I + 1]; ++t) {
-            int32_t J = tci[t];
-            if (J > I) break;
-            uint32_t rows[K];
-            uint32_t any = 0;
+        const int32_t t0 = __ldg(trp + I), t1 = __ldg(trp + I + 1), np = pre[I];
+        for (int32_t q = lane; q < np; q += 32) {
+            lci[o + q] = __ldg(tci + t0 + q);
+            if (TB >= 4) {
+                const uint32_t* src = reinterpret_cast<const uint32_t*>(tiles) + (int64_t)(t0 + q) * TW;
+                uint32_t* dst = reinterpret_cast<uint32_t*>(ltiles) + (o + q) * TW;
+#pragma unroll
+                for (int w = 0; w < TW; ++w) dst[w] = __ldg(src + w);
+            }
+        }
+        const int32_t d = t0 + np;
+        if (lane == 0 && d < t1 && __ldg(tci + d) == I && diag_has_lower<K>(tiles, d)) {
+            const int64_t w = o + np;
+            lci[w] = (int32_t)I;
 #pragma unroll
             for (int r = 0; r < K; ++r) {
-                uint32_t v = tile_word<K>(tiles, t, r);
-                if (J == I) v &= strict_lower_mask<K>(r);
-                rows[r] = v;
-                any |= v;
+                const uint32_t v = tile_word<K>(tiles, d, r) & strict_lower_mask<K>(r);
+                if (K <= 8) ltiles[w * K + r] = (uint8_t)v;
+                else if (K == 16) reinterpret_cast<uint16_t*>(ltiles)[w * K + r] = (uint16_t)v;
+                else reinterpret_cast<uint32_t*>(ltiles)[w * K + r] = v;
             }
-            if (!any) continue;
-            lci[w] = J;
-#pragma unroll
-            for (int r = 0; r < K; ++r) {
-                if (WB == 1) ltiles[w * K + r] = (uint8_t)rows[r];
-                else if (WB == 2) reinterpret_cast<uint16_t*>(ltiles)[w * K + r] = (uint16_t)rows[r];
-                else reinterpret_cast<uint32_t*>(ltiles)[w * K + r] = rows[r];
-            }
-            ++w;
         }
     }
 }
@@ -1150,14 +1163,17 @@ extern "C" b2sr_status b2sr_lower(b2sr_handle h, void* stream, b2sr_handle* out)
     cudaStream_t s = to_stream(stream);
     const int k = h->k;
     const int32_t ntr = h->ntr;
-    DevBuf cnt(s), off(s);
+    DevBuf cnt(s), off(s), pre(s);
     B2SR_TRY(cnt.alloc(((size_t)ntr + 1) * sizeof(int32_t)));
     B2SR_TRY(off.alloc(((size_t)ntr + 1) * sizeof(int64_t)));
+    B2SR_TRY(pre.alloc(((size_t)ntr + 1) * sizeof(int32_t)));
     B2SR_CUDA_TRY(cudaMemsetAsync(cnt.as<int32_t>() + ntr, 0, sizeof(int32_t), s));
     int64_t T = 0;
     B2SR_TRY(with_tile(k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
-        if (ntr > 0) lower_count_kernel<K><<<grid_wide(ntr), 256, 0, s>>>(h->rowptr, h->colind, h->tiles, ntr, cnt.as<int32_t>());
+        if (ntr > 0)
+            lower_count_kernel<K><<<grid_wide(ntr), 256, 0, s>>>(h->rowptr, h->colind, h->tiles, ntr, cnt.as<int32_t>(),
+                                                                 pre.as<int32_t>());
         B2SR_LAUNCH_CHECK("lower_count_kernel");
         return B2SR_OK;
     }));
@@ -1181,8 +1197,10 @@ extern "C" b2sr_status b2sr_lower(b2sr_handle h, void* stream, b2sr_handle* out)
     if (e != cudaSuccess) return release(cuda_fail(e, "memset lower"));
     st = with_tile(k, [&](auto kc) -> b2sr_status {
         constexpr int K = decltype(kc)::value;
-        lower_fill_kernel<K><<<grid_wide((int64_t)ntr + 1), 256, 0, s>>>(h->rowptr, h->colind, h->tiles, ntr,
-                                                                       off.as<int64_t>(), lrp, lci, lt);
+        lower_fill_kernel<K><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)ntr + 1, 8),
+                                                                                   (int64_t)sm_count() * 16)),
+                               256, 0, s>>>(h->rowptr, h->colind, h->tiles, ntr, off.as<int64_t>(), pre.as<int32_t>(),
+                                            lrp, lci, lt);
         B2SR_LAUNCH_CHECK("lower_fill_kernel");
         return B2SR_OK;
     });
