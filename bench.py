@@ -663,11 +663,13 @@ def roofline_of(fam, ms_total, peak, peak_src, tile, schedule, graph):
 
 def spmv_kernel_name(family, tile, schedule):
     """The SpMV kernel a family runs at this tile_dim and schedule (the
-    library's dispatch: the tile_dim-4 kernel for the bit-vector schemes at
-    k = 4, the staged gather kernel for the value schemes under the staged
-    schedule at k <= 16, the chunk kernel otherwise)."""
+    library's dispatch: at k = 4 the tile_dim-4 kernel for the bit-vector
+    schemes and, under the direct schedule, for the unweighted 4-byte value
+    schemes; the staged gather kernel for the value schemes under the staged
+    schedule at k <= 16; the chunk kernel otherwise)."""
     bits = family in ("spmv_bool", "spmv_count")
-    if tile == 4 and bits:
+    k4_values = family in ("spmv_plus", "spmv_min_i32", "spmv_max")
+    if tile == 4 and (bits or (k4_values and schedule == 2)):
         return "spmv_k4_kernel"
     if not bits and tile <= 16 and schedule != 2:
         return "spmv_gather_kernel"

@@ -972,8 +972,9 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_chunks_kernel(SpmvGeom g, S
 
 // ---------------------------------------------------------------------------
 // tile_dim-4 chunk kernel for the bit-vector schemes (Boolean and count
-// SpMVs).  At k = 4 a tile is 4 bytes, so the tile stream is tiny per tile and
-// the kernel is shaped by per-tile latency:
+// SpMVs) and the unweighted 4-byte value schemes (plus-times, label min, fp32
+// max: one gather per set bit).  At k = 4 a tile is 4 bytes, so the tile
+// stream is tiny per tile and the kernel is shaped by per-tile latency:
 //   * persistent warps: warp gw takes chunks gw, gw + W, ... and loads the
 //     next chunk's tile stream (8 tile words and 8 tile columns a lane, one
 //     32-byte load each, marked not to be kept in L1, plus the chunk's row
@@ -1017,6 +1018,28 @@ __device__ __forceinline__ void k4_load(const SpmvGeom& g, const SEM& sem, int32
     }
 }
 
+// The set bits of one k = 4 tile (row r in byte r) gather their inputs and
+// add them to the lane's row accumulators (value schemes).
+template <class SEM, class Acc>
+__device__ __forceinline__ void k4_gather_tile(const SEM& sem, Acc& acc, uint32_t w, int32_t J) {
+    using G = typename SEM::G;
+    using V = typename SEM::V;
+    const G* xt = sem.src() + (int64_t)J * 4;
+    while (w) {
+        const int bit = __ffs(w) - 1;
+        w &= w - 1;
+        const int r = bit >> 3;
+        const G xv = __ldg(xt + (bit & 7));
+        if constexpr (sizeof(V) == 8) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+                if (v == r) acc.set(v, sem.apply(acc.get(v), xv, 1.0f));
+        } else {
+            acc.set(r, sem.apply(acc.get(r), xv, 1.0f));
+        }
+    }
+}
+
 // One chunk from its loaded tile stream.
 template <class SEM>
 __device__ __forceinline__ void k4_chunk(const SpmvGeom& g, const SEM& sem, Partials<typename SEM::V> part, int32_t c,
@@ -1025,19 +1048,21 @@ __device__ __forceinline__ void k4_chunk(const SpmvGeom& g, const SEM& sem, Part
     using V = typename SEM::V;
     constexpr int NV = SEM::NV;
     constexpr int P = S::P;
-    static_assert(P == 8 && S::TW == 1 && !SEM::kGather, "eight one-word tiles a lane, bit-vector schemes");
+    static_assert(P == 8 && S::TW == 1, "eight one-word tiles a lane");
     LaneSpan ls;
     ls.cs = c * S::CT;
     ls.ce = min(ls.cs + S::CT, (int32_t)g.T);
     ls.tl = ls.cs + lane * P;
     ls.cnt = max(0, min(P, ls.ce - ls.tl));
     const int32_t ra = t.ra, rb = t.rb;
-    // the 4-bit input segment under each tile
-    uint32_t xs[P];
+    // the 4-bit input segment under each tile (bit-vector schemes)
+    uint32_t xs[SEM::kGather ? 1 : P];
+    if constexpr (!SEM::kGather) {
 #pragma unroll
-    for (int i = 0; i < P; ++i) {
-        const bool ok = i < ls.cnt && t.w[i] != 0u;
-        xs[i] = ok ? sem.xseg((int32_t)t.cu[i]) : 0u;
+        for (int i = 0; i < P; ++i) {
+            const bool ok = i < ls.cnt && t.w[i] != 0u;
+            xs[i] = ok ? sem.xseg((int32_t)t.cu[i]) : 0u;
+        }
     }
     RegAcc<V, NV> acc, F, idv;
 #pragma unroll
@@ -1049,8 +1074,12 @@ __device__ __forceinline__ void k4_chunk(const SpmvGeom& g, const SEM& sem, Part
         // scan is needed -- one fixed-order butterfly joins the lanes.
         const int32_t row_start = __shfl_sync(0xffffffffu, t.win, 0);
 #pragma unroll
-        for (int i = 0; i < P; ++i)
-            if (i < ls.cnt) sem.tile(acc, t.w + i, xs[i]);
+        for (int i = 0; i < P; ++i) {
+            if (i < ls.cnt) {
+                if constexpr (SEM::kGather) k4_gather_tile(sem, acc, t.w[i], (int32_t)t.cu[i]);
+                else sem.tile(acc, t.w + i, xs[i]);
+            }
+        }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
 #pragma unroll
@@ -1085,7 +1114,8 @@ __device__ __forceinline__ void k4_chunk(const SpmvGeom& g, const SEM& sem, Part
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             if (i < ls.cnt) {
-                sem.tile(acc, t.w + i, xs[i]);
+                if constexpr (SEM::kGather) k4_gather_tile(sem, acc, t.w[i], (int32_t)t.cu[i]);
+                else sem.tile(acc, t.w + i, xs[i]);
                 wk.end_tile(g, sem, acc, F, ls.tl + i, i, ls.cnt, idv);
             }
         }
@@ -1542,9 +1572,14 @@ static double spmv_bytes(const b2sr_matrix* h, double vec_bytes) {
     return 4.0 * ((double)h->ntr + 1.0) + (double)h->T * (4.0 + tile_bytes(h->k)) + vec_bytes;
 }
 
-// The tile_dim-4 kernel serves the bit-vector schemes at k = 4.
+// The tile_dim-4 kernel serves, at k = 4, the bit-vector schemes and the
+// unweighted value schemes with 4-byte values (plus-times, the label min, fp32
+// max); 8-byte values would not fit its registers without spilling.
 template <int K, class SEM>
-constexpr bool use_k4() { return K == 4 && !SEM::kGather; }
+constexpr bool use_k4() {
+    if constexpr (!SEM::kGather) return K == 4;
+    else return K == 4 && !SEM::kMayWeight && sizeof(typename SEM::V) == 4;
+}
 
 // The direct chunk kernel: the tile_dim-4 one where it serves, else the
 // general one.
