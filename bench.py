@@ -41,8 +41,8 @@ EXTRA_TILE = 8           # tile_dim of the grid SSSP, triangle-count and arena e
 NSRC, PR_ITERS, DAMP = 16, 50, 0.85
 QUERIES_PER_STEP = 1 + NSRC + PR_ITERS + 1  # edge passes counted per step (x nnz)
 PERMUTE = None           # seed of a vertex relabelling of the main workload (None: R-MAT's own ids)
-FAMILIES = ["spmv_bool", "spmv_count", "spmv_plus", "spmv_minplus", "spmv_min_i32", "spmm_or64", "spmm_plus4",
-            "spmv_max", "spmv_maxkey"]
+FAMILIES = ["spmv_bool", "spmv_count", "spmv_plus", "spmv_minplus", "spmv_min_i32", "spmm_or64", "spmm_or32",
+            "spmm_plus4", "spmv_max", "spmv_maxkey"]
 
 
 def ids_desc():
@@ -668,7 +668,7 @@ def spmv_kernel_name(family, tile, schedule):
     schemes; the staged gather kernel for the value schemes under the staged
     schedule at k <= 16; the chunk kernel otherwise)."""
     bits = family in ("spmv_bool", "spmv_count")
-    k4_values = family in ("spmv_plus", "spmv_min_i32", "spmv_max")
+    k4_values = family in ("spmv_plus", "spmv_min_i32", "spmv_max", "spmm_or32")
     if tile == 4 and (bits or (k4_values and schedule == 2)):
         return "spmv_k4_kernel"
     if not bits and tile <= 16 and schedule != 2:

@@ -440,7 +440,8 @@ b2sr_status b2sr_bfs_diropt(b2sr_handle h, b2sr_handle hT, int32_t src, int32_t*
                             void* stream);
 
 /* Multi-source BFS: up to 64 BFS runs of Sec. V advance together, their
- * frontiers packed as one uint64 per vertex (b2sr_spmm_bits64).
+ * frontiers packed as one uint64 per vertex (b2sr_spmm_bits64), or, for at
+ * most 32 sources, one uint32 (half the bytes per step; same levels).
  *   srcs_host host int32[nsrc], 1 <= nsrc <= 64
  *   levels    device int32[nsrc * n]: row s holds the levels of srcs_host[s] */
 b2sr_status b2sr_bfs_multi(b2sr_handle h, const int32_t* srcs_host, int nsrc, int32_t* levels,
@@ -558,8 +559,10 @@ int64_t b2sr_launch_count(void);
  * paper) on (1) or off (0).  While
  * on, every such launch is bracketed by two events on its own stream and
  * recorded under its family: "spmv_bool", "spmv_count", "spmv_plus",
- * "spmv_minplus", "spmv_min_i32", "spmm_or64" or "spgemm_masked" (the
- * masked-count SpGEMM kernel; its bytes are the three matrices' arrays). */
+ * "spmv_minplus", "spmv_min_i32", "spmv_max", "spmv_maxkey", "spmm_or64",
+ * "spmm_or32" (the batched BFS with at most 32 sources), "spmm_plus4" or
+ * "spgemm_masked" (the masked-count SpGEMM kernel; its bytes are the three
+ * matrices' arrays). */
 void b2sr_timing_enable(int on);
 
 /* Timing read-out (no counterpart in the paper).

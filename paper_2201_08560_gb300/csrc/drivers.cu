@@ -120,42 +120,48 @@ b2sr_status bfs_sources(b2sr_matrix* h, const int32_t* srcs_host, int nsrc, int3
 // ---------------------------------------------------------------------------
 // multi-source BFS, 64 frontiers per vertex
 // ---------------------------------------------------------------------------
-__global__ void msbfs_init_kernel(int32_t* levels, int32_t n, int nsrc, unsigned long long* X,
-                                  unsigned long long* vis) {
+// The lane word: 64 frontiers (uint64) or, for at most 32 sources, 32 (uint32:
+// half the bytes per gather, and the SpMV takes the tile_dim-4 kernel).
+__device__ __forceinline__ int lowest_lane(unsigned long long b) { return __ffsll((long long)b) - 1; }
+__device__ __forceinline__ int lowest_lane(uint32_t b) { return __ffs(b) - 1; }
+
+template <class W>
+__global__ void msbfs_init_kernel(int32_t* levels, int32_t n, int nsrc, W* X, W* vis) {
+    constexpr int BITS = 8 * (int)sizeof(W);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)n * nsrc || i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (i < (int64_t)n * nsrc) levels[i] = -1;
         // unused lanes count as visited, so a vertex every source has reached is
         // all ones in the mask and the SpMM can skip its rows
-        if (i < n) { X[i] = 0ull; vis[i] = nsrc < 64 ? ~((1ull << nsrc) - 1ull) : 0ull; }
+        if (i < n) { X[i] = (W)0; vis[i] = nsrc < BITS ? (W)~(((W)1 << nsrc) - (W)1) : (W)0; }
     }
 }
 
-__global__ void msbfs_seed_kernel(const int32_t* srcs, int nsrc, int32_t n, int32_t* levels, unsigned long long* X,
-                                  unsigned long long* vis) {
+template <class W>
+__global__ void msbfs_seed_kernel(const int32_t* srcs, int nsrc, int32_t n, int32_t* levels, W* X, W* vis) {
     int s = threadIdx.x;
     if (s < nsrc) {
         int32_t v = srcs[s];
         levels[(int64_t)s * n + v] = 0;
-        atomicOr(X + v, 1ull << s);
-        atomicOr(vis + v, 1ull << s);
+        atomicOr(X + v, (W)1 << s);
+        atomicOr(vis + v, (W)1 << s);
     }
 }
 
-__global__ void msbfs_update_kernel(const unsigned long long* __restrict__ Y, unsigned long long* __restrict__ vis,
-                                    int32_t* __restrict__ levels, int32_t n, const int32_t* level,
-                                    const int32_t* gate, int32_t* found) {
+template <class W>
+__global__ void msbfs_update_kernel(const W* __restrict__ Y, W* __restrict__ vis, int32_t* __restrict__ levels,
+                                    int32_t n, const int32_t* level, const int32_t* gate, int32_t* found) {
     if (gate_closed(gate)) return;
     const int32_t lv = *level + 1;
     int any = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long b = Y[v];
+        W b = Y[v];
         if (!b) continue;
         any = 1;
         vis[v] |= b;
         while (b) {
-            int s = __ffsll((long long)b) - 1;
+            int s = lowest_lane(b);
             b &= b - 1;
             levels[(int64_t)s * n + v] = lv;
         }
@@ -163,20 +169,34 @@ __global__ void msbfs_update_kernel(const unsigned long long* __restrict__ Y, un
     if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(found, 1);
 }
 
-b2sr_status bfs_multi(b2sr_matrix* h, const int32_t* srcs_host, int nsrc, int32_t* levels, int max_iters,
-                      cudaStream_t s) {
+b2sr_status spmm32_dispatch(b2sr_matrix* h, const uint32_t* X, uint32_t* Y, const uint32_t* M, int comp,
+                            cudaStream_t s, const int32_t* gate);
+
+static b2sr_status spmm_lanes(b2sr_matrix* h, const unsigned long long* X, unsigned long long* Y,
+                              const unsigned long long* M, cudaStream_t s, const int32_t* gate) {
+    return spmm64_dispatch(h, reinterpret_cast<const uint64_t*>(X), reinterpret_cast<uint64_t*>(Y),
+                           reinterpret_cast<const uint64_t*>(M), 1, s, gate);
+}
+static b2sr_status spmm_lanes(b2sr_matrix* h, const uint32_t* X, uint32_t* Y, const uint32_t* M, cudaStream_t s,
+                              const int32_t* gate) {
+    return spmm32_dispatch(h, X, Y, M, 1, s, gate);
+}
+
+template <class W>
+static b2sr_status bfs_multi_lanes(b2sr_matrix* h, const int32_t* srcs_host, int nsrc, int32_t* levels,
+                                   int max_iters, cudaStream_t s) {
     const int32_t n = h->n;
     DevBuf buf(s);
-    B2SR_TRY(buf.alloc(3 * (size_t)n * sizeof(uint64_t) + 72 * sizeof(int32_t)));
-    unsigned long long* X = buf.as<unsigned long long>();
-    unsigned long long* Yb = X + n;
-    unsigned long long* vis = Yb + n;
-    int32_t* dsrc = reinterpret_cast<int32_t*>(vis + n);
+    B2SR_TRY(buf.alloc(3 * round_up((size_t)n * sizeof(W), 256) + 72 * sizeof(int32_t)));
+    W* X = buf.as<W>();
+    W* Yb = reinterpret_cast<W*>(buf.as<char>() + round_up((size_t)n * sizeof(W), 256));
+    W* vis = reinterpret_cast<W*>(buf.as<char>() + 2 * round_up((size_t)n * sizeof(W), 256));
+    int32_t* dsrc = reinterpret_cast<int32_t*>(buf.as<char>() + 3 * round_up((size_t)n * sizeof(W), 256));
     int32_t* flags = dsrc + 64;  // active, found, level
     B2SR_CUDA_TRY(cudaMemcpyAsync(dsrc, srcs_host, nsrc * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    msbfs_init_kernel<<<grid_for((int64_t)n * nsrc), 256, 0, s>>>(levels, n, nsrc, X, vis);
+    msbfs_init_kernel<W><<<grid_for((int64_t)n * nsrc), 256, 0, s>>>(levels, n, nsrc, X, vis);
     B2SR_LAUNCH_CHECK("msbfs_init_kernel");
-    msbfs_seed_kernel<<<1, 64, 0, s>>>(dsrc, nsrc, n, levels, X, vis);
+    msbfs_seed_kernel<W><<<1, 64, 0, s>>>(dsrc, nsrc, n, levels, X, vis);
     B2SR_LAUNCH_CHECK("msbfs_seed_kernel");
     const int32_t init[3] = {1, 0, 0};
     B2SR_CUDA_TRY(cudaMemcpyAsync(flags, init, sizeof(init), cudaMemcpyHostToDevice, s));
@@ -187,18 +207,24 @@ b2sr_status bfs_multi(b2sr_matrix* h, const int32_t* srcs_host, int nsrc, int32_
     int64_t rounds = 0;
     return run_captured(s, 4, cap + 1, active,
                         [&](cudaStream_t cs, int r) -> b2sr_status {
-                            unsigned long long* cur = (r & 1) ? Yb : X;
-                            unsigned long long* nxt = (r & 1) ? X : Yb;
-                            B2SR_TRY(spmm64_dispatch(h, reinterpret_cast<uint64_t*>(cur), reinterpret_cast<uint64_t*>(nxt),
-                                                     reinterpret_cast<uint64_t*>(vis), 1, cs, active));
+                            W* cur = (r & 1) ? Yb : X;
+                            W* nxt = (r & 1) ? X : Yb;
+                            B2SR_TRY(spmm_lanes(h, cur, nxt, vis, cs, active));
                             B2SR_CUDA_TRY(cudaMemsetAsync(found, 0, sizeof(int32_t), cs));
-                            msbfs_update_kernel<<<grid_for(n), 256, 0, cs>>>(nxt, vis, levels, n, level, active, found);
+                            msbfs_update_kernel<W><<<grid_for(n), 256, 0, cs>>>(nxt, vis, levels, n, level, active,
+                                                                               found);
                             B2SR_LAUNCH_CHECK("msbfs_update_kernel");
                             advance_kernel<<<1, 32, 0, cs>>>(active, found, level);
                             B2SR_LAUNCH_CHECK("advance_kernel");
                             return B2SR_OK;
                         },
                         &rounds);
+}
+
+b2sr_status bfs_multi(b2sr_matrix* h, const int32_t* srcs_host, int nsrc, int32_t* levels, int max_iters,
+                      cudaStream_t s) {
+    if (nsrc <= 32) return bfs_multi_lanes<uint32_t>(h, srcs_host, nsrc, levels, max_iters, s);
+    return bfs_multi_lanes<unsigned long long>(h, srcs_host, nsrc, levels, max_iters, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -536,25 +536,26 @@ struct SemMaxKey {
     }
 };
 
-// 64 Boolean frontiers per vertex: Y_i = OR_j X_j, masked by M_i or ~M_i
-template <int K>
-struct SemOr64 {
-    using V = unsigned long long;
-    using G = unsigned long long;
-    using J = unsigned long long;
+// Boolean frontiers packed in one word per vertex (lane b of X_j: vertex j is
+// in frontier b): Y_i = OR_j X_j, masked by M_i or ~M_i
+template <int K, class W>
+struct SemOrLanes {
+    using V = W;
+    using G = W;
+    using J = W;
     static constexpr int NV = K;
     static constexpr bool kGather = true;
     static constexpr bool kMayWeight = false;
     static constexpr bool weighted = false;
-    const unsigned long long* x;
-    unsigned long long* y;
-    const unsigned long long* mask;
+    const W* x;
+    W* y;
+    const W* mask;
     int comp;
     int32_t n;
-    __device__ const unsigned long long* src() const { return x; }
+    __device__ const W* src() const { return x; }
     __device__ const float* wts() const { return nullptr; }
     __device__ const int32_t* voffs() const { return nullptr; }
-    __device__ V ident() const { return 0ull; }
+    __device__ V ident() const { return (W)0; }
     __device__ V comb(V a, V b) const { return a | b; }
     __device__ J jcomb(J a, J b) const { return a | b; }
     __device__ V apply(V acc, G xv, float) const { return acc | xv; }
@@ -565,7 +566,7 @@ struct SemOr64 {
         if (!mask || !comp || r1 - r0 > 9 * K) return false;  // up to nine tile-rows
         r1 = min(r1, (int64_t)n);
         bool ok = true;
-        for (int64_t i = r0 + lane_id(); i < r1; i += 32) ok &= __ldg(mask + i) == ~0ull;
+        for (int64_t i = r0 + lane_id(); i < r1; i += 32) ok &= __ldg(mask + i) == (W)~(W)0;
         return __all_sync(0xffffffffu, ok);
     }
     __device__ void store_row(int32_t R, int r, V v) const {
@@ -581,6 +582,13 @@ struct SemOr64 {
         for (int r = 0; r < K; ++r) store_row(R, r, acc.get(r));
     }
 };
+
+// 64 and 32 lanes: the batched BFS packs up to 64 (or, for at most 32
+// sources, 32) frontiers into one word per vertex.
+template <int K>
+using SemOr64 = SemOrLanes<K, unsigned long long>;
+template <int K>
+using SemOr32 = SemOrLanes<K, uint32_t>;
 
 // ---------------------------------------------------------------------------
 // kernel arguments and shared-memory layout
@@ -1709,6 +1717,17 @@ b2sr_status spmm64_dispatch(b2sr_matrix* h, const uint64_t* X, uint64_t* Y, cons
         SemOr64<K> sem{reinterpret_cast<const unsigned long long*>(X), reinterpret_cast<unsigned long long*>(Y),
                        reinterpret_cast<const unsigned long long*>(M), comp ? 1 : 0, h->n};
         return run_spmv<K>(h, sem, nullptr, s, "spmm_or64", (M ? 24.0 : 16.0) * h->n, gate);
+    });
+}
+
+// The same over 32-lane words (at most 32 frontiers): half the bytes per
+// gather and 4-byte accumulators, which the tile_dim-4 kernel takes.
+b2sr_status spmm32_dispatch(b2sr_matrix* h, const uint32_t* X, uint32_t* Y, const uint32_t* M, int comp,
+                            cudaStream_t s, const int32_t* gate) {
+    return with_tile(h->k, [&](auto kc) -> b2sr_status {
+        constexpr int K = decltype(kc)::value;
+        SemOr32<K> sem{X, Y, M, comp ? 1 : 0, h->n};
+        return run_spmv<K>(h, sem, nullptr, s, "spmm_or32", (M ? 12.0 : 8.0) * h->n, gate);
     });
 }
 
