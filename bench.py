@@ -388,7 +388,7 @@ def grid_sssp_extra(B, dev, grid):
         # push rounds over the frontier (the grid is symmetric: the handle is its own transpose),
         # delta-stepping buckets of 4x the largest weight
         ms = _timed(lambda: B.b2sr_sssp_push(m, 0, wb, dist, delta=SSSP_DELTA), reps=3)
-        rounds = B.b2sr_sssp_push_rounds()
+        rounds, rows = B.b2sr_sssp_push_rounds(with_rows=True)
         far = float(dist[-1].item())
         sweep = {}
         for delta in SSSP_DELTA_SWEEP:
@@ -397,7 +397,8 @@ def grid_sssp_extra(B, dev, grid):
             sweep[str(delta)] = {"ms": t, "rounds": r, "us_per_round": t * 1e3 / r}
         out = {"driver": "b2sr_sssp_push", "delta": SSSP_DELTA, "ms": ms, "nnz": int(ci.size),
                "gteps": ci.size / (ms / 1e3) / 1e9, "rounds": rounds,
-               "us_per_round": ms * 1e3 / rounds, "dist_far_corner": far, "n": int(n),
+               "us_per_round": ms * 1e3 / rounds, "active_tile_rows_per_round": rows / rounds,
+               "dist_far_corner": far, "n": int(n),
                "delta_sweep": sweep}
     return out
 

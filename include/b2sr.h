@@ -484,9 +484,11 @@ b2sr_status b2sr_sssp_push(b2sr_handle hT, const float* weights_t, int32_t src, 
 
 /* The rounds (relaxation rounds, counting those that only moved the far set
  * in) run by the most recent successful b2sr_sssp_push on the calling host
- * thread; 0 before any, and after a failed call.  Host-only; a measurement
- * aid with no counterpart in the paper (Sec. V reports SSSP times only). */
-b2sr_status b2sr_sssp_push_rounds(int64_t* rounds);
+ * thread, and, if active_tile_rows is not NULL, the active tile-rows those
+ * rounds took summed over the rounds; 0 before any call and after a failed
+ * one.  Host-only; a measurement aid with no counterpart in the paper (Sec. V
+ * reports SSSP times only). */
+b2sr_status b2sr_sssp_push_rounds(int64_t* rounds, int64_t* active_tile_rows);
 
 /* PageRank (Sec. V PR): x^0 = 1/n, then `iters` steps of
  *   x_i <- (1-d) t_i + d * sum_{j: A_ij=1} x_j / outdeg(j)

@@ -93,7 +93,7 @@ def _load() -> ctypes.CDLL:
         "b2sr_from_csr_batch": (c_int, [c_int, p, p, p, p, c_int, p, pp, p]),
         "b2sr_sssp": (c_int, [p, p, i32, p, c_int, p]),
         "b2sr_sssp_push": (c_int, [p, p, i32, p, f32, c_int, p]),
-        "b2sr_sssp_push_rounds": (c_int, [p]),
+        "b2sr_sssp_push_rounds": (c_int, [p, p]),
         "b2sr_pagerank": (c_int, [p, f32, c_int, p, p, p]),
         "b2sr_cc": (c_int, [p, p, c_int, p]),
         "b2sr_mis": (c_int, [p, p, p, c_int, p]),
@@ -481,11 +481,13 @@ def b2sr_sssp_push(mT: Matrix, src: int, weights_t: Optional[torch.Tensor] = Non
     return dist[: mT.n]
 
 
-def b2sr_sssp_push_rounds() -> int:
-    """Rounds run by this thread's most recent b2sr_sssp_push."""
+def b2sr_sssp_push_rounds(with_rows: bool = False):
+    """Rounds run by this thread's most recent b2sr_sssp_push; with
+    with_rows, (rounds, active tile-rows summed over the rounds)."""
     r = ctypes.c_int64(0)
-    _check(lib.b2sr_sssp_push_rounds(ctypes.byref(r)))
-    return int(r.value)
+    a = ctypes.c_int64(0)
+    _check(lib.b2sr_sssp_push_rounds(ctypes.byref(r), ctypes.byref(a)))
+    return (int(r.value), int(a.value)) if with_rows else int(r.value)
 
 
 def b2sr_tc(m: Matrix, count: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:

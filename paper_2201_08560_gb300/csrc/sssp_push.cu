@@ -173,6 +173,7 @@ struct PushCtl {
     int32_t* drain;   // far entries the drain kernel moves into the next set
     float* theta;     // threshold (nullptr: no buckets)
     int* farmin;      // least distance (float bits) that entered the far set since it was last moved
+    unsigned long long* worked;  // active tile-rows summed over the rounds
 };
 
 // After a round: the next round reads `nxt`, and the list it builds starts
@@ -185,6 +186,7 @@ struct PushCtl {
 __global__ void push_advance_kernel(int32_t* cur_count, int32_t* next_count, int32_t* far_count, PushCtl c,
                                     float delta) {
     if (threadIdx.x != 0 || blockIdx.x != 0 || !*c.active) return;
+    *c.worked += (unsigned long long)*reinterpret_cast<volatile int32_t*>(cur_count);
     *reinterpret_cast<volatile int32_t*>(cur_count) = 0;
     int32_t nn = *reinterpret_cast<volatile int32_t*>(next_count);
     int32_t dn = 0;
@@ -227,10 +229,12 @@ __global__ void push_init_kernel(float* dist, int32_t n, int32_t src) {
 }
 
 thread_local int64_t g_last_push_rounds = 0;
+thread_local int64_t g_last_push_rows = 0;
 
 b2sr_status sssp_push(b2sr_matrix* hT, const float* w, int32_t src, float* dist, float delta, int max_iters,
                       cudaStream_t s) {
     g_last_push_rounds = 0;
+    g_last_push_rows = 0;
     const int32_t n = hT->n;
     const int32_t ntr = hT->ntr;
     if (w) B2SR_TRY(ensure_voff(hT, s));  // before capture: capture must not allocate for the handle
@@ -241,14 +245,16 @@ b2sr_status sssp_push(b2sr_matrix* hT, const float* w, int32_t src, float* dist,
     B2SR_TRY(buf.alloc(total));
     char* base = buf.as<char>();
     int32_t* ctl = reinterpret_cast<int32_t*>(base + 3 * bw + 5 * lw);
-    // ctl: countA, countB, countFar, active, rounds, drain, theta (float), farmin (float bits)
+    // ctl: countA, countB, countFar, active, rounds, drain, theta (float), farmin (float bits), -,
+    // worked (8 bytes at ctl + 10: ctl is 256-byte aligned)
     PushSide A{reinterpret_cast<uint32_t*>(base), reinterpret_cast<int32_t*>(base + 3 * bw), ctl};
     PushSide Bs{reinterpret_cast<uint32_t*>(base + bw), reinterpret_cast<int32_t*>(base + 3 * bw + lw), ctl + 1};
     PushSide F{reinterpret_cast<uint32_t*>(base + 2 * bw), reinterpret_cast<int32_t*>(base + 3 * bw + 2 * lw),
                ctl + 2};
     int32_t* flag = reinterpret_cast<int32_t*>(base + 3 * bw + 3 * lw);
     int32_t* farflag = reinterpret_cast<int32_t*>(base + 3 * bw + 4 * lw);
-    PushCtl c{ctl + 3, ctl + 4, ctl + 5, delta > 0.0f ? reinterpret_cast<float*>(ctl + 6) : nullptr, ctl + 7};
+    PushCtl c{ctl + 3, ctl + 4, ctl + 5, delta > 0.0f ? reinterpret_cast<float*>(ctl + 6) : nullptr, ctl + 7,
+              reinterpret_cast<unsigned long long*>(ctl + 10)};
     B2SR_CUDA_TRY(cudaMemsetAsync(base, 0, total, s));
     push_init_kernel<<<grid_for(n), 256, 0, s>>>(dist, n, src);
     B2SR_LAUNCH_CHECK("push_init_kernel");
@@ -296,9 +302,12 @@ b2sr_status sssp_push(b2sr_matrix* hT, const float* w, int32_t src, float* dist,
     });
     if (st != B2SR_OK) return st;
     int32_t r = 0;
+    unsigned long long rows = 0;
     B2SR_CUDA_TRY(cudaMemcpyAsync(&r, c.rounds, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    B2SR_CUDA_TRY(cudaMemcpyAsync(&rows, c.worked, sizeof(rows), cudaMemcpyDeviceToHost, s));
     B2SR_CUDA_TRY(cudaStreamSynchronize(s));
     g_last_push_rounds = r;
+    g_last_push_rows = (int64_t)rows;
     return B2SR_OK;
 }
 
@@ -316,9 +325,10 @@ extern "C" b2sr_status b2sr_sssp_push(b2sr_handle hT, const float* weights_t, in
     return sssp_push(hT, weights_t, src, dist, delta, max_iters, to_stream(stream));
 }
 
-extern "C" b2sr_status b2sr_sssp_push_rounds(int64_t* rounds) {
+extern "C" b2sr_status b2sr_sssp_push_rounds(int64_t* rounds, int64_t* active_tile_rows) {
     clear_error();
     if (!rounds) return fail(B2SR_ERR_INVALID_ARG, "rounds is NULL");
     *rounds = g_last_push_rounds;
+    if (active_tile_rows) *active_tile_rows = g_last_push_rows;
     return B2SR_OK;
 }

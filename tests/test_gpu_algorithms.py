@@ -315,6 +315,8 @@ def test_sssp_push_rounds_on_a_path(B, k):
         d = to_np(B.b2sr_sssp_push(m, 0))
         np.testing.assert_array_equal(d, np.arange(g.n, dtype=np.float32))
         assert B.b2sr_sssp_push_rounds() == g.n
+        # one active vertex, hence one active tile-row, in each of the n rounds
+        assert B.b2sr_sssp_push_rounds(with_rows=True) == (g.n, g.n)
         with pytest.raises(B.B2SRError):
             B.b2sr_sssp_push(m, 0, max_iters=5)
         assert B.b2sr_sssp_push_rounds() == 0
