@@ -1,7 +1,11 @@
-"""GPU parity at tile_dim 4, where the Boolean and count SpMVs run on their
-own persistent kernel (each warp prefetches its next chunk's tiles; a chunk
-inside one tile-row is joined by a butterfly instead of the row walk) and the
-value schemes on the general chunk kernel.
+"""GPU parity at tile_dim 4, where the Boolean and count SpMVs and, under the
+direct schedule, the unweighted 4-byte value schemes (plus-times, label min,
+fp32 max) run on their own persistent kernel (each warp prefetches its next
+chunk's tiles; a chunk inside one tile-row is joined by a butterfly instead of
+the row walk), and the other value schemes on the general chunk kernel.  The
+butterfly pairs lanes exactly as the chunk kernel's scan does, so the
+four-column block (chunk kernel) still equals the single-column SpMV (tile_dim-4
+kernel) bit for bit.
 
 Every scheme is compared with the oracle on graphs with the tile patterns the
 kernels treat apart: dense tiles (all sixteen bits set), short tile-rows of
