@@ -3,17 +3,19 @@
 
 One step is one pass of the hot path over the workload: CSR -> B2SR
 conversion (tile_dim 4, direct SpMV schedule: the autotuner's choice for
-the step's dominant scheme on this graph), one Boolean SpMV, BFS from 16 seeded sources (one
-batched 64-lane launch sequence), PageRank (fp32, d = 0.85, 50 iterations)
-and connected components.  Throughput is GTEPS: the edges the step's queries
-must touch -- nnz for the SpMV, nnz per BFS source, nnz per PageRank
-iteration and nnz for CC, i.e. 68 * nnz per step -- divided by the step time.
+the step's dominant scheme on this graph), one Boolean SpMV, BFS from 16
+seeded sources (one batched sequence over 32-lane frontier words), PageRank
+(fp32, d = 0.85, 50 iterations) and connected components.  Throughput is
+GTEPS: the edges the step's queries must touch -- nnz for the SpMV, nnz per
+BFS source, nnz per PageRank iteration and nnz for CC, i.e. 68 * nnz per
+step -- divided by the step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--extra NAME ...] [--no-extras] [--permute SEED]
 
 N > 1 runs under torchrun, one replica per GPU (the path has no exchange
-step); rank 0 prints one JSON line.  --impl reference times the CPU oracle on
-a bounded sample of the same step (rank 0 only).
+step); rank 0 prints one JSON line.  --impl reference times whole steps of
+the same workload on the CPU oracle, on all host cores (rank 0 only).
 """
 from __future__ import annotations
 
