@@ -152,7 +152,7 @@ def run_reference(args):
 SERVE_GRAPHS, SERVE_SCALES = 32, (14, 20)
 SERVE_QUERIES, SERVE_RATE, SERVE_PR_ITERS = 10000, 2000.0, 20
 SERVE_BUDGET = 64 << 30
-SERVE_BASELINE_QUERIES = 300
+SERVE_SOLO_QUERIES = 300
 SERVE_FIFO_QUERIES = 1000
 
 
@@ -254,7 +254,7 @@ def serving_extra(B, dev, gs, t_gen):
                                       "p99_ms": float(lat_ms[int(np.ceil(0.99 * nf)) - 1]),
                                       "note": f"the first {nf} queries of the same Poisson stream, one driver call each"}
     # one query per driver call, same mix
-    base = plan[:SERVE_BASELINE_QUERIES]
+    base = plan[:SERVE_SOLO_QUERIES]
     for kind, gi, src in base[:20]:   # warm-up
         if kind == "bfs":
             B.b2sr_bfs(mats[gi], src, outs_i[0])
@@ -276,7 +276,7 @@ def serving_extra(B, dev, gs, t_gen):
     torch.cuda.synchronize()
     base_wall = time.perf_counter() - t0
     t0 = time.perf_counter()
-    bq = [q for q in plan if q[0] == "bfs"][:SERVE_BASELINE_QUERIES]
+    bq = [q for q in plan if q[0] == "bfs"][:SERVE_SOLO_QUERIES]
     for i, (kind, gi, src) in enumerate(bq):
         B.b2sr_bfs(mats[gi], src, outs_i[i])
     torch.cuda.synchronize()
