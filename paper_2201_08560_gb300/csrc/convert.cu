@@ -423,10 +423,15 @@ __global__ void __launch_bounds__(kFillThreads) fill_small_tiles_kernel(const ui
     const bool wide = k == 8;
     int lt = excl - 1;  // block-local tile of the run in progress (-1: a tile begun in an earlier block)
     uint64_t acc = 0;
-    auto flush = [&]() {
+    // A run that begins and ends among this thread's keys owns its tile: a
+    // plain shared-memory store.  Runs cut by a thread boundary are ORed in.
+    bool owned = false;
+    uint64_t lastkey = 0;
+    auto flush = [&](bool cut) {
         if (!acc) return;
         if (lt >= 0) {
-            atomicOr(&s_tile[lt], (unsigned long long)acc);
+            if (owned && !cut) s_tile[lt] = acc;
+            else atomicOr(&s_tile[lt], (unsigned long long)acc);
         } else if (wide) {
             atomicOr(reinterpret_cast<unsigned long long*>(tiles32) + (boff - 1), (unsigned long long)acc);
         } else {
@@ -438,9 +443,11 @@ __global__ void __launch_bounds__(kFillThreads) fill_small_tiles_kernel(const ui
     for (int q = 0; q < kFillItems; ++q) {
         if (q0 + q >= cnt) break;
         const uint64_t x = key[q];
+        lastkey = x;
         if ((h >> q) & 1u) {
-            flush();
+            flush(false);
             ++lt;
+            owned = true;
             s_col[lt] = (int32_t)((x >> 10) & jmask);
             const int64_t I = (int64_t)(x >> (sbits + 10));
             const int64_t Ip = b0 + q0 + q == 0 ? -1 : (int64_t)((q == 0 ? before : key[q - 1]) >> (sbits + 10));
@@ -451,7 +458,17 @@ __global__ void __launch_bounds__(kFillThreads) fill_small_tiles_kernel(const ui
         if (b0 + q0 + q == N - 1)  // tile-rows after the last entry's start at T
             for (int64_t R = (int64_t)(x >> (sbits + 10)) + 1; R <= ntr; ++R) rowptr[R] = (int32_t)T;
     }
-    flush();
+    {
+        // the last run goes on past this thread unless the next key starts a tile
+        const int nq = q0 + kFillItems;
+        const int last = min(kFillItems, cnt - q0) - 1;
+        bool cut = false;
+        if (last >= 0 && b0 + q0 + last + 1 < N) {
+            const uint64_t nk = nq < cnt ? s_key[fill_slot(nq)] : __ldg(keys + b0 + q0 + last + 1);
+            cut = (nk >> 10) == (lastkey >> 10);
+        }
+        flush(cut);
+    }
     __syncthreads();
     // the block's last tile goes on into the next block unless the next key starts a tile
     const bool cut = b0 + cnt < N && (__ldg(keys + b0 + cnt) >> 10) == (s_key[fill_slot(cnt - 1)] >> 10);
