@@ -142,3 +142,32 @@ def test_k4_masked_level_loop_skips_saturated_chunks(B):
             ref = oracle.bfs(cg, s)
             np.testing.assert_array_equal(lv[i], ref)
             np.testing.assert_array_equal(B.b2sr_bfs(m, s).cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=IDS)
+def test_k4_value_schemes_with_masks(B, gi):
+    """The value schemes the tile_dim-4 kernel runs (plus-times, fp32 max,
+    label min) with a bit mask and its complement: masked-out rows get the
+    semiring's identity, the others the unmasked result."""
+    name, g = GRAPHS[gi]
+    rp, ci = csr_dev(g)
+    cg = oracle.canonicalize(g)
+    n = g.n
+    rng = np.random.default_rng(31)
+    mask = graphs.random_bits(n, 0.4, seed=9)
+    xf = rng.random(n).astype(np.float32)
+    xl = rng.permutation(n).astype(np.int32)
+    with B.b2sr_from_csr(n, rp, ci, 4) as m:
+        B.b2sr_set_schedule(m, 2)  # DIRECT: the tile_dim-4 kernel
+        y = torch.empty(max(n, 1), dtype=torch.float32, device="cuda")
+        yi = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        for comp in (False, True):
+            B.b2sr_spmv(m, B.PLUS_TIMES, B.VEC_F32, to_dev(xf), B.VEC_F32, y, to_dev(mask), comp)
+            ref = oracle.spmv_plus(cg, xf.astype(np.float64), mask, comp)
+            got = to_np(y)[:n]
+            np.testing.assert_array_less(np.abs(got - ref), RTOL_F32 * np.abs(ref) + 1e-30)
+            B.b2sr_spmv(m, B.MAX_TIMES, B.VEC_F32, to_dev(xf), B.VEC_F32, y, to_dev(mask), comp)
+            np.testing.assert_array_equal(to_np(y)[:n],
+                                          oracle.spmv_max(cg, xf.astype(np.float64), mask, comp).astype(np.float32))
+            B.b2sr_spmv(m, B.MIN_PLUS, B.VEC_I32, to_dev(xl), B.VEC_I32, yi, to_dev(mask), comp)
+            np.testing.assert_array_equal(to_np(yi)[:n], oracle.spmv_min_i32(cg, xl, mask, comp))
